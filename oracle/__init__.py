@@ -1,0 +1,318 @@
+"""CPU oracle (FP64) for the periodic neighbor query, RDF and Steinhardt q_l.
+
+TEST INFRASTRUCTURE: only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg
+of `bench.py` may import this package.  It shares no code with the CUDA library
+(`paper_1906_06317_gb300`) and never imports it.
+
+The arithmetic lives in `oracle.c` (plain loops, one query at a time); this module only
+marshals numpy arrays through ctypes and splits query ranges over host threads (ctypes
+releases the GIL during the call, so the threads run the C loops in parallel).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_BOX_TOO_SMALL, ERR_OOM = 0, -1, -2, -3
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int
+_D = ctypes.c_double
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_box_widths.argtypes = [_P, _P]
+        L.orc_min_image.argtypes = [_P, _P, _P, _P, _P]
+        L.orc_cells_dims.argtypes = [_P, _D, _P]
+        L.orc_cells_build.argtypes = [_P, _P, _I64, _P, _P, _P]
+        L.orc_ball_query.argtypes = [_P, _P, _I64, _P, _P, _P, _P, _I64, _I64, _D, _I32, _P, _P, _P, _P]
+        L.orc_knn.argtypes = [_P, _P, _I64, _P, _P, _P, _P, _I64, _I64, _I32, _I32, _P, _P, _P]
+        L.orc_rdf_edges.argtypes = [_I32, _D, _D, _P]
+        L.orc_rdf.argtypes = [_P, _P, _I64, _P, _P, _P, _P, _I64, _I64, _I32, _D, _D, _I32, _P]
+        L.orc_ylm.argtypes = [_I32, _I32, _D, _D, _D, _P, _P]
+        L.orc_steinhardt_ylm.argtypes = [_P, _P, _I64, _P, _P, _I32, _P, _I64, _P, _P]
+        L.orc_steinhardt_legendre.argtypes = [_P, _P, _I64, _P, _P, _I32, _P, _I64, _P]
+        L.orc_q_grad.argtypes = [_P, _P, _I64, _P, _P, _I32, _P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(code, what):
+    if code != OK:
+        raise OracleError(code, what)
+
+
+def _box(box) -> np.ndarray:
+    b = np.asarray(box.params() if hasattr(box, "params") else box, dtype=np.float64)
+    assert b.shape == (6,)
+    return np.ascontiguousarray(b)
+
+
+def _pts(x) -> np.ndarray:
+    x = np.asarray(x)
+    assert x.ndim == 2 and x.shape[1] == 3
+    return np.ascontiguousarray(x.astype(np.float64))
+
+
+def default_threads() -> int:
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def _ranges(n, threads, min_chunk=256):
+    chunks = max(1, min(threads * 4, (n + min_chunk - 1) // min_chunk))
+    edges = np.linspace(0, n, chunks + 1).astype(np.int64)
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+def box_widths(box) -> np.ndarray:
+    w = np.zeros(3)
+    lib().orc_box_widths(_ptr(_box(box)), _ptr(w))
+    return w
+
+
+def min_image(box, xi, xj):
+    """Minimum-image displacement x_j - x_i (exact FP64 sequence) and its length."""
+    d = np.zeros(3)
+    r = np.zeros(1)
+    lib().orc_min_image(_ptr(_box(box)), _ptr(np.asarray(xi, np.float64)), _ptr(np.asarray(xj, np.float64)),
+                        _ptr(d), _ptr(r))
+    return d, float(r[0])
+
+
+class Cells:
+    """Cell list used by the oracle only to prune candidates."""
+
+    def __init__(self, box, points, r_cell: float):
+        self.b = _box(box)
+        self.pts = _pts(points)
+        self.nc = np.zeros(3, dtype=np.int32)
+        _check(lib().orc_cells_dims(_ptr(self.b), float(r_cell), _ptr(self.nc)), "cells_dims")
+        ncell = int(np.prod(self.nc.astype(np.int64)))
+        self.cell_start = np.zeros(ncell + 1, dtype=np.int64)
+        self.order = np.zeros(max(1, len(self.pts)), dtype=np.int64)
+        _check(lib().orc_cells_build(_ptr(self.b), _ptr(self.pts), len(self.pts), _ptr(self.nc),
+                                     _ptr(self.cell_start), _ptr(self.order)), "cells_build")
+
+
+def _setup(box, points, r_cell, brute, query_points):
+    b = _box(box)
+    pts = _pts(points)
+    qpts = pts if query_points is None else _pts(query_points)
+    cells = None if brute else Cells(b, pts, r_cell)
+    return b, pts, qpts, cells
+
+
+def _cargs(cells):
+    if cells is None:
+        return None, None, None
+    return _ptr(cells.nc), _ptr(cells.cell_start), _ptr(cells.order)
+
+
+def ball_query(box, points, r_max, exclude_ii=True, query_points=None, brute=False, queries=None,
+               threads=None):
+    """Neighbor list of a ball query.
+
+    Returns (counts, offsets, point_indices, distances) for the queries in
+    `queries` = (q0, q1) (default all): segment t = offsets[t]..offsets[t+1] holds the
+    neighbors of query q0+t sorted by point index.
+    """
+    b, pts, qpts, cells = _setup(box, points, r_max, brute, query_points)
+    q0, q1 = (0, len(qpts)) if queries is None else queries
+    nq = q1 - q0
+    threads = threads or default_threads()
+    counts = np.zeros(nq, dtype=np.int64)
+    L = lib()
+    nc, cs, od = _cargs(cells)
+
+    def count(rg):
+        a, z = rg
+        return L.orc_ball_query(_ptr(b), _ptr(pts), len(pts), nc, cs, od, _ptr(qpts), q0 + a, q0 + z,
+                                float(r_max), int(exclude_ii), _ptr(counts[a:z]), None, None, None)
+
+    rgs = _ranges(nq, threads)
+    with ThreadPoolExecutor(threads) as ex:
+        for st in ex.map(count, rgs):
+            _check(st, "ball_query(count)")
+    offsets = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    pj = np.zeros(max(1, offsets[-1]), dtype=np.int64)
+    dist = np.zeros(max(1, offsets[-1]), dtype=np.float64)
+
+    def fill(rg):
+        a, z = rg
+        rel = np.ascontiguousarray(offsets[a:z])
+        return L.orc_ball_query(_ptr(b), _ptr(pts), len(pts), nc, cs, od, _ptr(qpts), q0 + a, q0 + z,
+                                float(r_max), int(exclude_ii), None, _ptr(rel), _ptr(pj), _ptr(dist))
+
+    with ThreadPoolExecutor(threads) as ex:
+        for st in ex.map(fill, rgs):
+            _check(st, "ball_query(fill)")
+    m = int(offsets[-1])
+    return counts, offsets, pj[:m], dist[:m]
+
+
+def knn(box, points, k, exclude_ii=True, query_points=None, brute=False, queries=None, threads=None,
+        r_cell=None):
+    """k nearest neighbors ordered by (r2, index).  Returns (n_found, idx (nq,k), dist (nq,k))."""
+    b = _box(box)
+    pts = _pts(points)
+    qpts = pts if query_points is None else _pts(query_points)
+    cells = None
+    if not brute:
+        if r_cell is None:
+            vol = abs(np.prod(b[:3]))
+            r_cell = 1.2 * (3.0 * (k + 1) * vol / (4.0 * math.pi * max(1, len(pts)))) ** (1.0 / 3.0)
+        cells = Cells(b, pts, r_cell)
+    q0, q1 = (0, len(qpts)) if queries is None else queries
+    nq = q1 - q0
+    threads = threads or default_threads()
+    out_j = np.full((nq, k), -1, dtype=np.int64)
+    out_r = np.zeros((nq, k), dtype=np.float64)
+    out_n = np.zeros(nq, dtype=np.int64)
+    L = lib()
+    nc, cs, od = _cargs(cells)
+
+    def run(rg):
+        a, z = rg
+        oj = np.zeros((z - a, k), dtype=np.int64)
+        orr = np.zeros((z - a, k), dtype=np.float64)
+        on = np.zeros(z - a, dtype=np.int64)
+        st = L.orc_knn(_ptr(b), _ptr(pts), len(pts), nc, cs, od, _ptr(qpts), q0 + a, q0 + z, int(k),
+                       int(exclude_ii), _ptr(oj), _ptr(orr), _ptr(on))
+        out_j[a:z], out_r[a:z], out_n[a:z] = oj, orr, on
+        return st
+
+    with ThreadPoolExecutor(threads) as ex:
+        for st in ex.map(run, _ranges(nq, threads, 64)):
+            _check(st, "knn")
+    for t in range(nq):
+        out_j[t, out_n[t]:] = -1
+    return out_n, out_j, out_r
+
+
+def rdf_edges(bins, r_min, r_max) -> np.ndarray:
+    e = np.zeros(bins + 1)
+    _check(lib().orc_rdf_edges(int(bins), float(r_min), float(r_max), _ptr(e)), "rdf_edges")
+    return e
+
+
+def rdf_counts(box, points, bins, r_max, r_min=0.0, exclude_ii=True, query_points=None, brute=False,
+               queries=None, threads=None) -> np.ndarray:
+    """Ordered-pair histogram counts (uint64) over bins of [r_min, r_max)."""
+    b, pts, qpts, cells = _setup(box, points, r_max, brute, query_points)
+    q0, q1 = (0, len(qpts)) if queries is None else queries
+    threads = threads or default_threads()
+    L = lib()
+    nc, cs, od = _cargs(cells)
+
+    def run(rg):
+        a, z = rg
+        c = np.zeros(bins, dtype=np.uint64)
+        st = L.orc_rdf(_ptr(b), _ptr(pts), len(pts), nc, cs, od, _ptr(qpts), q0 + a, q0 + z, int(bins),
+                       float(r_min), float(r_max), int(exclude_ii), _ptr(c))
+        _check(st, "rdf")
+        return c
+
+    total = np.zeros(bins, dtype=np.uint64)
+    with ThreadPoolExecutor(threads) as ex:
+        for c in ex.map(run, _ranges(q1 - q0, threads)):
+            total += c
+    return total
+
+
+def rdf_normalize(counts, n_query, n_points, volume, bins, r_min, r_max):
+    """g_b = counts_b / (N_q (N_p / V) (4 pi / 3)(R_{b+1}^3 - R_b^3)) and the bin centres
+    r_min + (b + 1/2) (r_max - r_min)/bins.  With several frames accumulated, pass
+    n_query * n_points / volume summed over frames as `n_query` and n_points = volume = 1."""
+    e = rdf_edges(bins, r_min, r_max)
+    shell = 4.0 / 3.0 * math.pi * (e[1:] ** 3 - e[:-1] ** 3)
+    g = np.asarray(counts, dtype=np.float64) / (n_query * (n_points / volume) * shell)
+    delta = (r_max - r_min) / bins
+    centers = r_min + (np.arange(bins) + 0.5) * delta
+    return g, centers
+
+
+def ylm(l, m, v):
+    re = np.zeros(1)
+    im = np.zeros(1)
+    _check(lib().orc_ylm(int(l), int(m), float(v[0]), float(v[1]), float(v[2]), _ptr(re), _ptr(im)), "ylm")
+    return complex(re[0], im[0])
+
+
+def _nl(offsets, pj):
+    return np.ascontiguousarray(np.asarray(offsets, np.int64)), np.ascontiguousarray(np.asarray(pj, np.int64))
+
+
+def steinhardt(box, points, offsets, pj, l, which=None, with_qlm=False, threads=None):
+    """q_l per particle from the spherical-harmonic definition (optionally Q_lm, m = 0..l)."""
+    b = _box(box)
+    pts = _pts(points)
+    off, j = _nl(offsets, pj)
+    idx = np.arange(len(pts), dtype=np.int64) if which is None else np.ascontiguousarray(np.asarray(which, np.int64))
+    q = np.zeros(len(idx))
+    Q = np.zeros((len(idx), l + 1, 2)) if with_qlm else None
+    threads = threads or default_threads()
+    L = lib()
+
+    def run(rg):
+        a, z = rg
+        sub = np.ascontiguousarray(idx[a:z])
+        qq = np.zeros(z - a)
+        QQ = np.zeros((z - a, l + 1, 2)) if with_qlm else None
+        st = L.orc_steinhardt_ylm(_ptr(b), _ptr(pts), len(pts), _ptr(off), _ptr(j), int(l), _ptr(sub), z - a,
+                                  _ptr(qq), _ptr(QQ))
+        _check(st, "steinhardt")
+        q[a:z] = qq
+        if with_qlm:
+            Q[a:z] = QQ
+        return st
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, _ranges(len(idx), threads, 64)))
+    if with_qlm:
+        return q, Q[..., 0] + 1j * Q[..., 1]
+    return q
+
+
+def steinhardt_legendre(box, points, offsets, pj, l, which=None):
+    """q_l per particle through the Legendre addition theorem (independent second form)."""
+    b = _box(box)
+    pts = _pts(points)
+    off, j = _nl(offsets, pj)
+    idx = np.arange(len(pts), dtype=np.int64) if which is None else np.ascontiguousarray(np.asarray(which, np.int64))
+    q = np.zeros(len(idx))
+    _check(lib().orc_steinhardt_legendre(_ptr(b), _ptr(pts), len(pts), _ptr(off), _ptr(j), int(l), _ptr(idx),
+                                         len(idx), _ptr(q)), "steinhardt_legendre")
+    return q
+
+
+def q_grad(box, points, offsets, pj, l):
+    """dQ/dx for Q = mean_i q_l(i), neighbor list fixed; (N, 3) float64."""
+    b = _box(box)
+    pts = _pts(points)
+    off, j = _nl(offsets, pj)
+    g = np.zeros((len(pts), 3))
+    _check(lib().orc_q_grad(_ptr(b), _ptr(pts), len(pts), _ptr(off), _ptr(j), int(l), _ptr(g)), "q_grad")
+    return g

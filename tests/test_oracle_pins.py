@@ -1,0 +1,306 @@
+"""Pins of the CPU oracle against facts fixed outside it (CPU only).
+
+Each check is chosen so a plausible slip in the oracle (dropped image term, wrong tilt
+index, off-by-one bin, sign of a spherical-harmonic phase, missing Legendre term,
+transposed gradient) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.special import sph_harm_y
+
+import oracle
+import workloads as W
+from tests.helpers import image_distances, legendre_p, nl_sets, q_from_bonds
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+BOXES = [
+    W.Box.cube(10.0),
+    W.Box(11.0, 9.5, 10.5, 0.1, 0.05, 0.0),
+    W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15),
+    W.Box(10.0, 10.0, 10.0, 0.2, -0.2, -0.2),
+]
+
+
+def _pairs(offsets, pj):
+    qi = np.repeat(np.arange(len(offsets) - 1), np.diff(offsets))
+    return qi, pj
+
+
+@pytest.mark.parametrize("bi", range(len(BOXES)))
+def test_min_image_is_true_nearest_image(bi):
+    b = BOXES[bi]
+    rng = np.random.default_rng(10 + bi)
+    x = W.uniform_points(rng, b, 60).astype(np.float64)
+    x[:10] += 3.0 * rng.normal(size=(10, 3))          # some points outside the box
+    ref = image_distances(b, x, x, reach=3)
+    wmin = oracle.box_widths(b).min()
+    for i in range(0, 60, 7):
+        for j in range(60):
+            d, r = oracle.min_image(b, x[i], x[j])
+            if ref[i, j] < 0.5 * wmin:
+                assert r == pytest.approx(ref[i, j], rel=1e-12, abs=1e-12)
+            else:
+                assert r >= ref[i, j] - 1e-12
+
+
+def test_box_widths_closed_form():
+    b = W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15)
+    M = np.array([[12.0, -2.0, 2.2], [0.0, 10.0, 1.65], [0.0, 0.0, 11.0]])
+    inv = np.linalg.inv(M)
+    w = 1.0 / np.linalg.norm(inv, axis=1)              # plane spacing = 1/|reciprocal row|
+    assert np.allclose(oracle.box_widths(b), w, rtol=1e-14)
+
+
+@pytest.mark.parametrize("bi", range(len(BOXES)))
+@pytest.mark.parametrize("r_max", [1.1, 2.3, 4.3])
+def test_ball_cells_equal_brute(bi, r_max):
+    b = BOXES[bi]
+    x = W.small_random(20 + bi, 1200, b)
+    c1, o1, p1, d1 = oracle.ball_query(b, x, r_max, brute=True)
+    c2, o2, p2, d2 = oracle.ball_query(b, x, r_max)
+    assert np.array_equal(o1, o2) and np.array_equal(p1, p2) and np.array_equal(d1, d2)
+    assert all(np.all(np.diff(p1[o1[i]:o1[i + 1]]) > 0) for i in range(len(x)))
+
+
+@pytest.mark.parametrize("bi", range(len(BOXES)))
+def test_ball_matches_image_enumeration(bi):
+    b = BOXES[bi]
+    x = W.small_random(30 + bi, 400, b)
+    r_max = 2.7
+    ref = image_distances(b, x, x)
+    np.fill_diagonal(ref, np.inf)
+    _, o, pj, dist = oracle.ball_query(b, x, r_max)
+    got = nl_sets(o, pj)
+    margin = 1e-9
+    for i in range(len(x)):
+        sure = set(np.nonzero(ref[i] < r_max - margin)[0].tolist())
+        maybe = set(np.nonzero(ref[i] < r_max + margin)[0].tolist())
+        assert sure <= got[i] <= maybe
+        assert np.allclose(dist[o[i]:o[i + 1]], ref[i, pj[o[i]:o[i + 1]]], rtol=1e-12)
+
+
+def test_ball_matches_ckdtree_cubic():
+    L = 12.0
+    b = W.Box.cube(L)
+    x = W.small_random(40, 3000, b).astype(np.float64)
+    r_max = 1.7
+    tree = cKDTree(x + L / 2, boxsize=L)
+    ref = tree.query_pairs(r_max - 1e-9, output_type="ndarray")
+    ref_hi = tree.query_pairs(r_max + 1e-9, output_type="ndarray")
+    _, o, pj, _ = oracle.ball_query(b, x.astype(np.float32), r_max)
+    qi, _ = _pairs(o, pj)
+    got = {(int(a), int(c)) for a, c in zip(qi, pj) if a < c}
+    lo = {(int(a), int(c)) for a, c in ref}
+    hi = {(int(a), int(c)) for a, c in ref_hi}
+    assert lo <= got <= hi and len(got) > 1000
+
+
+def test_fcc_shell_counts():
+    g = json.load(open(os.path.join(GOLDEN, "fcc_shells.json")))
+    a = 1.5874
+    n = 4
+    b = W.Box.cube(n * a)
+    x = W.lattice_points(None, b, n)
+    radii = [a * s for s in g["shell_radius_over_a"]] + [1e9]
+    for t, want in enumerate(g["cumulative_counts"]):
+        r_max = 0.5 * (radii[t] + radii[t + 1]) if t + 1 < len(g["cumulative_counts"]) else radii[t] + 0.05
+        c, *_ = oracle.ball_query(b, x, r_max)
+        assert np.all(c == want), (t, np.unique(c))
+
+
+def test_neighbor_list_symmetry_and_translation():
+    b = W.Box(10.0, 10.0, 10.0, 0.15, -0.1, 0.05)
+    x = W.small_random(50, 1500, b)
+    _, o, pj, _ = oracle.ball_query(b, x, 2.2)
+    qi, _ = _pairs(o, pj)
+    fwd = set(zip(qi.tolist(), pj.tolist()))
+    assert fwd == {(j, i) for i, j in fwd}
+    # translation by whole box vectors is exact in FP64 here, so sets and order are identical
+    M = W.Box(10.0, 10.0, 10.0, 0.15, -0.1, 0.05).matrix()
+    rng = np.random.default_rng(0)
+    xs = x.astype(np.float64) + (rng.integers(-2, 3, size=(len(x), 3)) @ M.T)
+    _, o2, pj2, d2 = oracle.ball_query(b, xs, 2.2)
+    assert np.array_equal(o, o2) and np.array_equal(pj, pj2)
+
+
+@pytest.mark.parametrize("bi", [0, 2])
+def test_knn_equals_full_sort(bi):
+    b = BOXES[bi]
+    x = W.small_random(60 + bi, 700, b)
+    k = 12
+    n1, j1, r1 = oracle.knn(b, x, k, brute=True)
+    n2, j2, r2 = oracle.knn(b, x, k)
+    assert np.array_equal(n1, n2) and np.array_equal(j1, j2) and np.array_equal(r1, r2)
+    ref = image_distances(b, x, x)
+    np.fill_diagonal(ref, np.inf)
+    order = np.lexsort((np.broadcast_to(np.arange(len(x)), ref.shape), ref), axis=1)[:, :k]
+    gaps = np.diff(np.sort(ref, axis=1)[:, : k + 1], axis=1).min(axis=1)
+    clear = gaps > 1e-9                                  # no near-tie anywhere in the first k+1
+    assert clear.mean() > 0.95
+    assert np.array_equal(j1[clear], order[clear])
+    assert np.allclose(r1, np.take_along_axis(ref, j1, axis=1), rtol=1e-12)
+
+
+def test_knn_small_n_and_box_limits():
+    b = W.Box.cube(20.0)
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 3.5]], np.float32)
+    n, j, r = oracle.knn(b, x, 12)
+    assert np.all(n == 3)
+    assert j[0, :3].tolist() == [1, 2, 3] and np.allclose(r[0, :3], [1.0, 2.0, 3.5])
+    n, j, r = oracle.knn(b, x[:1], 12)
+    assert n[0] == 0
+    far = np.array([[0.0, 0.0, 0.0], [9.9, 9.9, 9.9]], np.float32)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.knn(b, far, 1)
+    assert e.value.code == oracle.ERR_BOX_TOO_SMALL
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ball_query(b, x, 10.0)
+    assert e.value.code == oracle.ERR_BOX_TOO_SMALL
+
+
+def test_rdf_histogram_against_numpy():
+    b = W.Box(9.0, 10.0, 11.0, 0.1, 0.0, -0.1)
+    x = W.small_random(70, 800, b)
+    bins, r_min, r_max = 37, 0.3, 4.1
+    ref = image_distances(b, x, x)
+    np.fill_diagonal(ref, np.inf)
+    delta = (r_max - r_min) / bins
+    edges = np.array([r_min + k * delta for k in range(bins)] + [r_max])
+    assert np.array_equal(edges, oracle.rdf_edges(bins, r_min, r_max))
+    r = ref[np.isfinite(ref)]
+    r = r[(r >= r_min) & (r < r_max)]
+    want = np.histogram(r, bins=edges)[0]
+    got = oracle.rdf_counts(b, x, bins, r_max, r_min)
+    assert np.array_equal(got, want.astype(np.uint64))
+    assert np.array_equal(oracle.rdf_counts(b, x, bins, r_max, r_min, brute=True), got)
+
+
+def test_rdf_total_equals_neighbor_count():
+    b = W.Box.cube(16.0)
+    x = W.c1().points[:2048]
+    c, *_ = oracle.ball_query(b, x, 4.0)
+    h = oracle.rdf_counts(b, x, 100, 4.0)
+    assert int(h.sum()) == int(c.sum())
+
+
+def test_rdf_ideal_gas():
+    w = W.c1()
+    p = w.params
+    counts = oracle.rdf_counts(w.box, w.points, p["rdf_bins"], p["rdf_r_max"])
+    n = len(w.points)
+    g, centers = oracle.rdf_normalize(counts, n, n, w.box.volume, p["rdf_bins"], 0.0, p["rdf_r_max"])
+    e = oracle.rdf_edges(p["rdf_bins"], 0.0, p["rdf_r_max"])
+    expect = n * (n - 1) / w.box.volume * 4.0 / 3.0 * math.pi * (e[1:] ** 3 - e[:-1] ** 3)
+    ok = expect > 200
+    sigma = np.sqrt(2.0 / expect[ok])
+    assert np.all(np.abs(g[ok] - (1.0 - 1.0 / n)) < 5.0 * sigma)
+    assert centers[0] == pytest.approx(0.02) and centers[-1] == pytest.approx(3.98)
+
+
+def test_ylm_matches_scipy():
+    rng = np.random.default_rng(80)
+    for _ in range(20):
+        v = rng.normal(size=3)
+        th = math.acos(v[2] / np.linalg.norm(v))
+        ph = math.atan2(v[1], v[0])
+        for l in (0, 1, 2, 4, 6, 8, 12):
+            for m in range(-l, l + 1):
+                assert oracle.ylm(l, m, v) == pytest.approx(complex(sph_harm_y(l, m, th, ph)), abs=1e-12)
+
+
+def _lattice_q(basis, nn, l):
+    b = W.Box.cube(6.0)
+    x = W.lattice_points(None, b, 6, basis=basis)
+    shells = image_distances(b, x[:1], x)[0]
+    r_first = np.sort(shells)[1]
+    r_max = r_first * 1.05
+    _, o, pj, _ = oracle.ball_query(b, x, r_max)
+    assert np.all(np.diff(o) == nn)
+    return oracle.steinhardt(b, x, o, pj, l), oracle.steinhardt_legendre(b, x, o, pj, l)
+
+
+@pytest.mark.parametrize("name,basis,nn", [("fcc_12", W.FCC_BASIS, 12), ("bcc_8", W.BCC_BASIS, 8),
+                                            ("sc_6", W.SC_BASIS, 6)])
+def test_steinhardt_perfect_lattices(name, basis, nn):
+    g = json.load(open(os.path.join(GOLDEN, "steinhardt_lattices.json")))[name]
+    for l in (4, 6):
+        q1, q2 = _lattice_q(basis, nn, l)
+        assert np.allclose(q1, g[f"q{l}"], atol=g["tol"])
+        assert np.allclose(q1, q2, atol=1e-12)
+
+
+def test_steinhardt_closed_forms_numpy():
+    # SC: dot products 1 (x6), -1 (x6), 0 (x24): q_l = sqrt(6 P(1) + 6 P(-1) + 24 P(0)) / 6
+    for l in (4, 6):
+        S = 6 * legendre_p(l, 1.0) + 6 * legendre_p(l, -1.0) + 24 * legendre_p(l, 0.0)
+        sc = math.sqrt(S) / 6
+        q1, _ = _lattice_q(W.SC_BASIS, 6, l)
+        assert np.allclose(q1, sc, atol=1e-12)
+    fcc_bonds = np.array([[a, b_, 0] for a in (1, -1) for b_ in (1, -1)] + [[a, 0, b_] for a in (1, -1) for b_ in (1, -1)]
+                         + [[0, a, b_] for a in (1, -1) for b_ in (1, -1)], np.float64)
+    for l in (4, 6):
+        q1, _ = _lattice_q(W.FCC_BASIS, 12, l)
+        assert np.allclose(q1, q_from_bonds(fcc_bonds, l), atol=1e-12)
+
+
+def test_steinhardt_single_neighbor_and_empty():
+    b = W.Box.cube(10.0)
+    x = np.array([[0.0, 0.0, 0.0], [0.3, 1.1, -0.4], [4.0, 4.0, 4.0]], np.float64)
+    off = np.array([0, 1, 2, 2])
+    pj = np.array([1, 0])
+    for l in (2, 4, 6, 8):
+        q = oracle.steinhardt(b, x, off, pj, l)
+        assert q[0] == pytest.approx(1.0, abs=1e-13) and q[1] == pytest.approx(1.0, abs=1e-13) and q[2] == 0.0
+        assert np.allclose(oracle.steinhardt_legendre(b, x, off, pj, l), q, atol=1e-13)
+
+
+def test_steinhardt_forms_agree_and_rotation_invariant():
+    w = W.c2(n_cells=4)
+    _, o, pj, _ = oracle.ball_query(w.box, w.points, 1.3)
+    for l in (4, 6):
+        q1 = oracle.steinhardt(w.box, w.points, o, pj, l)
+        q2 = oracle.steinhardt_legendre(w.box, w.points, o, pj, l)
+        assert np.allclose(q1, q2, atol=1e-12)
+    # an isolated cluster in a big box: rotating it leaves q_l unchanged
+    rng = np.random.default_rng(81)
+    cl = rng.normal(size=(14, 3))
+    big = W.Box.cube(100.0)
+    off = np.array([0, 13] + [13] * 13)
+    pj = np.arange(1, 14)
+    R = W.random_rotation(rng)
+    for l in (3, 4, 6, 10):
+        a = oracle.steinhardt(big, cl, off, pj, l)[0]
+        c = oracle.steinhardt(big, cl @ R.T, off, pj, l)[0]
+        assert a == pytest.approx(c, abs=1e-12)
+        assert a == pytest.approx(q_from_bonds(cl[1:] - cl[0], l), abs=1e-12)
+
+
+def test_q_gradient_finite_differences():
+    w = W.c4(n_cells=4)
+    x = w.points.astype(np.float64)
+    l = 6
+    _, o, pj, _ = oracle.ball_query(w.box, w.points, 1.3)
+    g = oracle.q_grad(w.box, x, o, pj, l)
+    assert np.allclose(g.sum(axis=0), 0.0, atol=1e-14)
+    n = len(x)
+    h = 1e-3
+    rng = np.random.default_rng(82)
+    picks = rng.choice(n, 40, replace=False)
+    for k in picks:
+        affected = np.unique(np.concatenate([[k], pj[o[k]:o[k + 1]]]))
+        for c in range(3):
+            xp = x.copy()
+            xm = x.copy()
+            xp[k, c] += h
+            xm[k, c] -= h
+            # only k and its neighbors change; the other terms of the mean cancel
+            fp = oracle.steinhardt(w.box, xp, o, pj, l, which=affected).sum() / n
+            fm = oracle.steinhardt(w.box, xm, o, pj, l, which=affected).sum() / n
+            fd = (fp - fm) / (2 * h)
+            assert fd == pytest.approx(g[k, c], rel=1e-4, abs=1e-4 * np.abs(g).max())
