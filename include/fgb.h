@@ -1,0 +1,263 @@
+/*
+ * fgb: periodic neighbor query, radial distribution function and Steinhardt order
+ * parameters on one GB300 GPU (sm_103a).  C ABI of libfgb.so.
+ *
+ * The operations follow freud (arXiv 1906.06317):
+ *   - Box and NeighborQuery: Section "Implementation" (a triclinic box with three
+ *     linearly independent vectors, centred on the origin; a NeighborQuery built from
+ *     (box, points) answers queries by cutoff r_max or by neighbor count, with
+ *     exclude_ii), and Section "General Utilities" (cell-list subclass, periodicity at
+ *     the lowest level, NeighborList as stored query results).
+ *   - RDF: the density module ("Analysis Modules"), histogram accumulated over frames
+ *     with reset=False ("Implementation", Compute classes).
+ *   - Steinhardt q_l: the order module ("Analysis Modules", bond-orientational order
+ *     parameters of Steinhardt et al. 1983).
+ *
+ * Conventions for every call:
+ *   - Box params (Lx, Ly, Lz, xy, xz, yz): a1 = (Lx,0,0), a2 = (xy Ly, Ly, 0),
+ *     a3 = (xz Lz, yz Lz, Lz); the box spans M (s - 1/2) for s in [0,1)^3.
+ *   - Points are device pointers to float32 arrays of shape (n, 3), row-major
+ *     (x0 y0 z0 x1 ...), owned by the caller; they must stay valid and unchanged for
+ *     the lifetime of any handle built from them.  Points may lie outside the box.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work on
+ *     it; a call that must return a size to the host (fgb_nq_query) synchronises it.
+ *   - Handles own the device memory they allocate (stream-ordered allocations on the
+ *     stream of the call that made them); *_destroy frees it and accepts NULL.
+ *   - Every call returns FGB_OK (0) or a negative FGB_ERR_* code and records a message
+ *     for fgb_last_error() (thread-local).  No C++ exception crosses this boundary.
+ *   - Distances use the minimum image; a pair (i, j) is a neighbor when its distance r
+ *     satisfies r < r_max (strict).  r is defined by one fixed FP64 sequence: d = x_j - x_i
+ *     reduced along a3, a2, a1 by rint(component / box length), r = sqrt((dx dx + dy dy)
+ *     + dz dz).  Kernels decide in FP32 and re-decide every pair within a proven
+ *     error band of an edge with that FP64 sequence, so neighbor sets and histogram
+ *     counts are exact with respect to it.
+ */
+#ifndef FGB_H
+#define FGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGB_OK 0
+#define FGB_ERR_INVALID_ARG (-1)   /* bad pointer, size or parameter */
+#define FGB_ERR_BOX_TOO_SMALL (-2) /* r_max (or the k-th neighbor distance) >= half the smallest box width */
+#define FGB_ERR_OOM (-3)           /* device allocation failed */
+#define FGB_ERR_CUDA (-4)          /* a CUDA runtime call or kernel launch failed */
+#define FGB_ERR_UNSUPPORTED (-5)   /* valid request outside what this build implements */
+#define FGB_ERR_CAPACITY (-6)      /* a documented size limit was exceeded */
+
+typedef struct fgb_box {
+    double Lx, Ly, Lz, xy, xz, yz;
+} fgb_box;
+
+/* Query arguments (freud's query dict): exactly one of r_max > 0 (ball query) or
+ * num_neighbors > 0 (k nearest) is set.  exclude_ii drops pairs whose query index equals
+ * the point index. */
+typedef struct fgb_query_args {
+    double r_max;
+    int32_t num_neighbors;
+    int32_t exclude_ii;
+} fgb_query_args;
+
+typedef struct fgb_nq fgb_nq;
+typedef struct fgb_nlist fgb_nlist;
+typedef struct fgb_rdf fgb_rdf;
+typedef struct fgb_steinhardt fgb_steinhardt;
+typedef struct fgb_batch fgb_batch;
+
+/* ------------------------------------------------------------- library state */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *fgb_last_error(void);
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int32_t fgb_version(void);
+
+/* --------------------------------------------------------- NeighborQuery (cell list) */
+
+/*
+ * Builds a cell-list NeighborQuery over `n` points (Section "General Utilities": the
+ * cell-list NeighborQuery subclass).  Work on `stream`: box wrap and fractional
+ * transform, cell index per point, stable radix sort by cell index, cell start offsets.
+ * Cells are at least `r_cell` wide along every reciprocal axis; any later query with
+ * r_max > r_cell widens its stencil instead of failing.
+ * n may be 0.  Errors: INVALID_ARG (n < 0, points NULL with n > 0, r_cell <= 0,
+ * degenerate box), OOM, CUDA.
+ */
+int fgb_nq_create(const fgb_box *box, const float *points, int64_t n, double r_cell, void *stream,
+                  fgb_nq **out);
+void fgb_nq_destroy(fgb_nq *nq);
+
+/* Cell grid of a NeighborQuery: cells per axis (x, y, z) and number of points. */
+int fgb_nq_dims(const fgb_nq *nq, int32_t ncell[3], int64_t *n_points);
+
+/*
+ * Device views of the cell list (owned by nq, valid until fgb_nq_destroy):
+ *   sorted      (n, 4) float32: cell-local x, y, z and the original point index stored
+ *               as the bit pattern of the 4th float, in (cell, index) order;
+ *   sorted_cell (n) uint32: cell index of each sorted entry;
+ *   cell_start  (ncells + 1) uint32: entries of cell c are cell_start[c] .. cell_start[c+1].
+ * Cell index = (cz * ny + cy) * nx + cx.
+ */
+int fgb_nq_cells(const fgb_nq *nq, const float **sorted, const uint32_t **sorted_cell,
+                 const uint32_t **cell_start);
+
+/*
+ * Query (Section "Implementation": queries by cutoff distance or by number of
+ * neighbors) producing a NeighborList sorted by (query index, point index) for ball
+ * queries and by (query index, distance, point index) for k-nearest queries.
+ * query_points == NULL queries the NeighborQuery's own points (n_query ignored).
+ * Ball query: count pass, exclusive scan into int64 segment offsets, write pass; the
+ * call synchronises `stream` once to size the output.  kNN: min(k, available)
+ * neighbors per query; FGB_ERR_BOX_TOO_SMALL if a selected neighbor is at distance
+ * >= w_min/2 (the minimum image would be ambiguous) or if r_max >= w_min/2.
+ */
+int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
+                 void *stream, fgb_nlist **out);
+
+/* --------------------------------------------------------------- NeighborList */
+
+int fgb_nlist_size(const fgb_nlist *nl, int64_t *n_pairs, int64_t *n_query);
+
+/*
+ * Device arrays of a NeighborList (owned by nl; any pointer argument may be NULL):
+ *   query_point_indices, point_indices: int32 (n_pairs);  distances: float32 (n_pairs);
+ *   segments: int64 (n_query + 1), pairs of query i are segments[i] .. segments[i+1];
+ *   counts: int32 (n_query).
+ */
+int fgb_nlist_arrays(const fgb_nlist *nl, const int32_t **query_point_indices, const int32_t **point_indices,
+                     const float **distances, const int64_t **segments, const int32_t **counts);
+
+/* Number of pair decisions that fell inside the FP32 error band and were re-decided in
+ * FP64 while building this list (a diagnostic). */
+int fgb_nlist_escalations(const fgb_nlist *nl, int64_t *n);
+
+/*
+ * NeighborList from caller arrays (device; query_point_indices must be non-decreasing;
+ * distances may be NULL).  The arrays are copied.  symmetric != 0 promises that (j, i) is
+ * present whenever (i, j) is (a self ball query), which lets the Steinhardt backward use
+ * its deterministic gather form.
+ */
+int fgb_nlist_from_arrays(int64_t n_query, int64_t n_points, const int32_t *query_point_indices,
+                          const int32_t *point_indices, const float *distances, int64_t n_pairs,
+                          int32_t symmetric, void *stream, fgb_nlist **out);
+void fgb_nlist_destroy(fgb_nlist *nl);
+
+/* ------------------------------------------------------------------------ RDF */
+
+/*
+ * Radial distribution function (density module; Section "Potentials of Mean Force and
+ * Torque" relates g(r) = exp(-beta F(r))).  Bin b holds R_b <= r < R_{b+1},
+ * R_b = r_min + b ((r_max - r_min)/bins), R_bins = r_max.  Errors: INVALID_ARG for
+ * bins <= 0, r_min < 0, r_max <= r_min.
+ */
+int fgb_rdf_create(int32_t bins, double r_max, double r_min, fgb_rdf **out);
+void fgb_rdf_destroy(fgb_rdf *rdf);
+
+/*
+ * Adds the ordered-pair distance histogram of one frame to the accumulator (reset != 0
+ * clears it first: freud's compute(..., reset=False) accumulation).
+ * nlist == NULL: fused cell-list query; pairs are never stored; query_points == NULL
+ * means the NeighborQuery's own points with exclude_ii (each unordered pair is visited
+ * once and counted twice).  nlist != NULL: histogram of the list's pairs (distances
+ * recomputed and decided exactly).  Asynchronous on `stream`.
+ */
+int fgb_rdf_compute(fgb_rdf *rdf, fgb_nq *nq, const float *query_points, int64_t n_query,
+                    const fgb_nlist *nlist, int32_t reset, void *stream);
+
+/*
+ * Copies the accumulated counts (uint64, bins), g(r) (float64, bins; counts divided by
+ * sum over frames of N_query (N_points / V) (4 pi/3)(R_{b+1}^3 - R_b^3)) and bin centres
+ * r_min + (b + 1/2) (r_max - r_min)/bins to host arrays (any may be NULL).  Synchronises
+ * `stream`.
+ */
+int fgb_rdf_result(fgb_rdf *rdf, uint64_t *counts, double *rdf_values, double *bin_centers, void *stream);
+
+/* Device pointer of the uint64 accumulator (bins entries), for graph-captured use. */
+int fgb_rdf_counts_device(const fgb_rdf *rdf, const uint64_t **counts);
+
+/* Number of pairs re-decided in FP64 by the last compute (synchronises `stream`). */
+int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
+
+/* ----------------------------------------------------------------- Steinhardt */
+
+/*
+ * Steinhardt q_l (order module): Q_lm(i) = (1/n_i) sum_j Y_lm(u_ij),
+ * q_l(i) = sqrt(4 pi/(2l+1) sum_m |Q_lm(i)|^2); q_l = 0 for a particle without
+ * neighbors.  0 <= l <= 12.
+ */
+int fgb_steinhardt_create(int32_t l, fgb_steinhardt **out);
+void fgb_steinhardt_destroy(fgb_steinhardt *st);
+
+/*
+ * q_out: device float32 (n points).  Neighbors come from `nlist` when it is not NULL
+ * (its query indices address nq's points), otherwise from a fused self ball query with
+ * qargs->r_max (no list is stored).  Keeps Q_lm (m = 0..l) and the neighbor counts for
+ * fgb_steinhardt_backward.  Asynchronous on `stream`.
+ */
+int fgb_steinhardt_compute(fgb_steinhardt *st, fgb_nq *nq, const fgb_nlist *nlist, const fgb_query_args *qargs,
+                           float *q_out, void *stream);
+
+/* Device views of the last compute: Q_lm as float32 (n, l+1, 2) (re, im) and int32
+ * neighbor counts (n). */
+int fgb_steinhardt_state(const fgb_steinhardt *st, const float **qlm, const int32_t **n_neighbors);
+
+/*
+ * Gradient of Q = (1/n) sum_i q_l(i) times `upstream` with respect to the positions,
+ * neighbor list fixed (requires the nlist used by the last compute; q from that
+ * compute).  grad_out: device float32 (n, 3), overwritten.  A symmetric list (self ball
+ * query) uses a deterministic gather over each particle's neighbors; other lists use
+ * a scatter with float atomics.
+ */
+int fgb_steinhardt_backward(fgb_steinhardt *st, fgb_nq *nq, const fgb_nlist *nlist, const float *q,
+                            float upstream, float *grad_out, void *stream);
+
+/* -------------------------------------------------------------- batched frames */
+
+typedef struct fgb_batch_params {
+    double r_max;        /* ball query radius feeding q_l */
+    int32_t l;           /* Steinhardt l (0..12), or -1 for none */
+    int32_t rdf_bins;    /* RDF bins (0 for none) */
+    double rdf_r_max;
+    double rdf_r_min;
+    int32_t cell_div;    /* cells per r_max along each axis: 1 or 2; 0 = autotune */
+    int32_t block;       /* threads per block of the persistent kernel: 64..512; 0 = autotune */
+    int32_t hist_copies; /* shared histogram copies per block: 1, 2 or 4; 0 = autotune */
+    int32_t reserved;
+} fgb_batch_params;
+
+/*
+ * Many frames of uneven size and different boxes analysed together (the per-frame
+ * trajectory loops of the paper's listings).  frame_offsets (host, n_frames + 1): frame f
+ * owns points frame_offsets[f] .. frame_offsets[f+1] of the packed (total, 3) array.
+ * All device buffers are allocated here, so fgb_batch_run enqueues a fixed sequence of
+ * kernels with no allocation and no host synchronisation (it can be captured in a CUDA
+ * graph; fgb_batch_run_graph does that itself).
+ */
+int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, const fgb_box *boxes,
+                     const fgb_batch_params *params, void *stream, fgb_batch **out);
+void fgb_batch_destroy(fgb_batch *b);
+
+/* One pass over all frames: per-frame binning, one sort over all frames, and one
+ * persistent kernel that computes every frame's RDF counts and q_l. */
+int fgb_batch_run(fgb_batch *b, const float *points, void *stream);
+
+/* Same work replayed from a CUDA graph captured on the first call for this `points`
+ * pointer (recaptured when it changes). */
+int fgb_batch_run_graph(fgb_batch *b, const float *points, void *stream);
+
+/* Times the candidate (cell_div, block, hist_copies) settings on `points` and keeps the
+ * fastest (the parameters set to 0 at create).  Synchronises `stream`. */
+int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, fgb_batch_params *chosen);
+
+/* Device outputs: RDF counts uint64 (n_frames, bins), q_l float32 (total points, in
+ * input order), neighbor counts int32 (total). */
+int fgb_batch_outputs(const fgb_batch *b, const uint64_t **rdf_counts, const float **q,
+                      const int32_t **n_neighbors);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGB_H */

@@ -1,0 +1,173 @@
+// Internal declarations shared by the libfgb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "fgb.h"
+
+namespace fgb {
+
+// ------------------------------------------------------------------ errors
+
+int fail(int code, const char *fmt, ...);
+void clear_error();
+
+#define FGB_CUDA(expr)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t fgb_e_ = (expr);                                                                     \
+        if (fgb_e_ != cudaSuccess)                                                                       \
+            return ::fgb::fail(FGB_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(fgb_e_), \
+                               __FILE__, __LINE__);                                                      \
+    } while (0)
+
+#define FGB_LAUNCH_CHECK() FGB_CUDA(cudaGetLastError())
+
+#define FGB_TRY(expr)              \
+    do {                           \
+        int fgb_s_ = (expr);       \
+        if (fgb_s_ != FGB_OK)      \
+            return fgb_s_;         \
+    } while (0)
+
+// Stream-ordered device allocation (the device's default memory pool).
+int dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+template <class T>
+int dalloc_n(T **p, size_t n, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void **>(p), n * sizeof(T), s);
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+int num_sms();
+
+// ------------------------------------------------------------------ box
+
+// FP32 view of the box for the fast paths.  Box vectors a1 = (Lx,0,0),
+// a2 = (a2x, Ly, 0), a3 = (a3x, a3y, Lz).  *_hi + *_lo splits carry the FP64 value to
+// about 48 bits so a reduction by a whole box vector loses no accuracy.
+struct BoxF {
+    float L[3];
+    float a2x, a3x, a3y;
+    float inv00, inv01, inv02, inv11, inv12, inv22;  // upper-triangular M^-1
+    float invL[3];
+    float Lhi[3], Llo[3];
+    float a2x_hi, a2x_lo, a3x_hi, a3x_lo, a3y_hi, a3y_lo;
+};
+
+// FP64 view for the exact decision sequence (identical operations to the definition).
+struct BoxD {
+    double L[3];
+    double invL[3];
+    double a2x, a3x, a3y;
+};
+
+struct BoxHost {
+    double p[6];  // Lx Ly Lz xy xz yz
+    double M[3][3];
+    double Minv[3][3];
+    double w[3];  // perpendicular widths
+    double wmin;
+    BoxF f;
+    BoxD d;
+};
+
+int make_box(const fgb_box *in, BoxHost *out);
+
+// Smallest double t with sqrt(t) >= R (IEEE sqrt, round to nearest): r >= R <=> r2 >= T(R).
+double sqrt_threshold(double R);
+
+// ------------------------------------------------------------------ cell grid
+
+constexpr double kCellMargin = 1.0 / 256.0;  // relative slack between cell width and r_cell
+constexpr int kMaxStencil = 8;               // largest stencil half-width
+
+struct GridHost {
+    int nc[3];
+    int64_t ncell;
+    double wc[3];        // perpendicular cell widths w_k / nc_k
+    double ext;          // bound on |component| of a cell-local coordinate
+    double origin_extent;
+};
+
+// Device tables of cell-corner origins along each axis, FP64 split in hi/lo floats:
+// O_x = Tx[cx] + Txy[cy] + Txz[cz], O_y = Ty[cy] + Tyz[cz], O_z = Tz[cz].
+struct OriginTables {
+    const float2 *Tx, *Txy, *Txz, *Ty, *Tyz, *Tz;
+};
+
+}  // namespace fgb
+
+// ------------------------------------------------------------------ handles
+
+struct fgb_nq {
+    fgb::BoxHost box;
+    fgb::GridHost grid;
+    const float *points;  // caller's (n,3)
+    int64_t n;
+    double r_cell;
+    float4 *sorted;        // (n) cell-local xyz + index bits
+    uint32_t *sorted_cell; // (n)
+    uint32_t *cell_start;  // (ncell+1)
+    float2 *origin_buf;    // all origin tables, packed
+    fgb::OriginTables org;
+    cudaStream_t stream;
+};
+
+struct fgb_nlist {
+    int64_t n_query, n_points, n_pairs;
+    int32_t *qi, *pj, *counts;
+    float *dist;
+    int64_t *segments;
+    int64_t escalations;
+    int symmetric;
+    int kind;  // 0 ball, 1 knn, 2 user arrays
+    cudaStream_t stream;
+};
+
+namespace fgb {
+
+// Sorted view of query points for a query launch (either the NeighborQuery's own
+// sorted arrays or a separately binned copy of the query points).
+struct QueryPoints {
+    const float4 *sorted;
+    const uint32_t *cell;
+    const float *orig;  // (nq, 3) original coordinates
+    int64_t n;
+    bool self;
+    // owned buffers (non-null when a separate copy was binned)
+    float4 *own_sorted;
+    uint32_t *own_cell;
+};
+
+int bin_points(const BoxHost &box, const GridHost &grid, const OriginTables &org, const float *pts, int64_t n,
+               float4 *sorted, uint32_t *sorted_cell, uint32_t *cell_start, cudaStream_t s);
+int grid_for(const BoxHost &box, double r_cell, int64_t n, GridHost *g);
+int prepare_queries(fgb_nq *nq, const float *qpts, int64_t n_query, cudaStream_t s, QueryPoints *out);
+void release_queries(QueryPoints *q, cudaStream_t s);
+
+// Stencil set-up for a query radius R over nq's cell grid (query.cu): walked
+// half-widths, the FP32 offset table (device, caller frees `table`) and the FP32 error
+// bound on r^2 for pairs up to distance R.
+struct StencilPlan {
+    int s[3];       // half-width walked per axis (axes not scanned whole)
+    int ts[3];      // half-width of the offset table (mode 0)
+    int full[3];    // axis scanned whole once
+    int mode;       // 0: fixed per-cell image offsets, 1: rint reduction per candidate
+    float4 *table;  // owned (mode 0)
+    double eps_d;   // bound on the FP32 error of one displacement component
+    double Lsum;
+};
+int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, StencilPlan *p);
+double r2_error_bound(const StencilPlan &p, double R);
+// FP32 band [lo, hi) around the exact threshold T, widened by `delta` and rounded outward.
+void band_around(double T, double delta, float *lo, float *hi);
+
+// Exclusive scan helpers (scan.cu).  out has n+1 entries (out[n] = total).
+int scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, uint32_t *max_out, cudaStream_t s);
+int scan_u32_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+
+}  // namespace fgb

@@ -1,0 +1,378 @@
+// k-nearest-neighbor query (Section "Implementation": queries by number of neighbors;
+// freud's num_neighbors).  Neighbors of a query are ordered by (r2, point index) with r2
+// from the defining FP64 sequence; see query.cu for the overview.
+#include <cmath>
+#include <cstring>
+
+#include "fgb_device.cuh"
+
+namespace fgb {
+
+struct KnnArgs {
+    int nc[3];
+    int ts[3];             // offset-table half-width (mode 0 possible while s <= ts)
+    const float4 *off;
+    float3 step[3];
+    float wc[3];           // perpendicular cell widths
+    BoxF bf;
+    BoxD bd;
+    const float4 *pts;
+    const uint32_t *cell_start;
+    const float4 *qs;
+    const uint32_t *qcell;
+    int64_t nq;
+    int64_t npts;
+    const float *p_orig;
+    const float *q_orig;
+    int k;
+    int exclude;
+    int self;
+    int stride;            // row stride of the output (m if uniform, else k)
+    float ext, rowmax, Lsum;
+    float half_wmin2;      // (w_min / 2)^2, slightly reduced
+    int *flag_count;
+    int4 *flags;           // (t, s, threshold bits, 0)
+    int flag_cap;
+    int *err;              // 1 = box too small, 2 = flag list overflow
+    int32_t *qi_out, *pj_out;
+    float *d_out;
+    int32_t *counts;
+};
+
+// FP32 error bound on r2 at radius R for a walk with half-width s (mode 0) or the
+// general route (mode 1); same terms as plan_stencil/r2_error_bound on the host.
+__device__ __forceinline__ float knn_delta(const KnnArgs &a, int mode, int s, float R) {
+    const float u = kU32;
+    const float e = mode == 0 ? 2.f * u * (5.f * a.ext + 2.f * s * a.rowmax + R)
+                              : 2.f * u * (5.f * a.ext + 8.f * a.Lsum + 4.f * R);
+    const float d = 3.4641016f * R * e + 3.f * e * e + 3.f * u * (R + e) * (R + e) + 1e-12f * (R + a.Lsum) * (R + a.Lsum);
+    return 1.5f * d;
+}
+
+__device__ __forceinline__ Stencil knn_stencil(const KnnArgs &a, int s, bool &all_full) {
+    Stencil S;
+    S.mode = 0;
+    all_full = true;
+    for (int k = 0; k < 3; ++k) {
+        S.nc[k] = a.nc[k];
+        S.s[k] = s;
+        S.ts[k] = a.ts[k];
+        S.full[k] = 2 * s + 1 > a.nc[k];
+        if (S.full[k] || s > a.ts[k] || a.off == nullptr) S.mode = 1;
+        all_full &= (bool)S.full[k];
+        S.step[k] = a.step[k];
+    }
+    S.off = a.off;
+    return S;
+}
+
+template <int KT>
+__device__ __forceinline__ void topk_insert(float (&br)[KT], int (&bj)[KT], float r2, int j) {
+    float cr = r2;
+    int cj = j;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const bool less = cr < br[q] || (cr == br[q] && cj < bj[q]);
+        const float tr = less ? br[q] : cr;
+        const int tj = less ? bj[q] : cj;
+        br[q] = less ? cr : br[q];
+        bj[q] = less ? cj : bj[q];
+        cr = tr;
+        cj = tj;
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nq) return;
+    const float4 q = a.qs[t];
+    const int i = __float_as_int(q.w);
+    int cx, cy, cz;
+    cell_coords(a.qcell[t], a.nc, cx, cy, cz);
+    const int excl = a.exclude ? i : -1;
+    const int avail = (int)min((int64_t)0x7fffffff, a.npts - ((a.exclude && i < a.npts) ? 1 : 0));
+    const int m = min(a.k, avail);
+    float br[KT];
+    int bj[KT];
+    int found = 0, s = 1, mode = 0;
+    float delta = 0.f;
+    for (;; ++s) {
+        bool all_full;
+        const Stencil S = knn_stencil(a, s, all_full);
+        mode = S.mode;
+#pragma unroll
+        for (int q2 = 0; q2 < KT; ++q2) {
+            br[q2] = INFINITY;
+            bj[q2] = 0x7fffffff;
+        }
+        found = 0;
+        for_stencil(S, cx, cy, cz, make_float3(q.x, q.y, q.z), false, [&](int cell, float qx, float qy, float qz, bool) {
+            const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
+            for (uint32_t p = beg; p < end; ++p) {
+                const float4 c = __ldg(a.pts + p);
+                const int j = __float_as_int(c.w);
+                if (j == excl) continue;
+                const float3 d = cand_disp(S, a.bf, c, qx, qy, qz);
+                const float r2 = r2_f32(d.x, d.y, d.z);
+                ++found;
+                if (r2 < br[KT - 1] || (r2 == br[KT - 1] && j < bj[KT - 1])) topk_insert<KT>(br, bj, r2, j);
+            }
+        });
+        if (all_full) {
+            delta = knn_delta(a, mode, s, m > 0 ? sqrtf(br[min(m, KT) - 1]) : 0.f);
+            break;
+        }
+        float rcov = INFINITY;
+        for (int k2 = 0; k2 < 3; ++k2)
+            if (!S.full[k2]) rcov = fminf(rcov, s * a.wc[k2]);
+        rcov *= 0.99999f;
+        if (found >= m && m > 0) {
+            const float rk2 = br[m - 1];
+            delta = knn_delta(a, mode, s, sqrtf(rk2) + 1e-3f);
+            if (rk2 + delta < rcov * rcov) break;
+        } else if (m == 0) {
+            break;
+        }
+    }
+    a.counts[i] = m;
+    if (m > 0 && br[m - 1] + delta >= a.half_wmin2) {
+        atomicOr(a.err, 1);
+        return;
+    }
+    // a ranking is certain when every neighboring gap among the first m+1 exceeds 2 delta
+    bool ambiguous = false;
+    const int last = min(found, KT) - 1;
+#pragma unroll
+    for (int q2 = 0; q2 + 1 < KT; ++q2)
+        if (q2 < m && q2 + 1 <= last && br[q2 + 1] - br[q2] <= 2.f * delta) ambiguous = true;
+    const int64_t row = (int64_t)i * a.stride;
+    if (ambiguous) {
+        const int slot = atomicAdd(a.flag_count, 1);
+        if (slot < a.flag_cap) {
+            const float thr = br[m - 1] + 2.f * delta;
+            a.flags[slot] = make_int4((int)t, s, __float_as_int(thr * 1.0000005f), 0);
+        } else {
+            atomicOr(a.err, 2);
+        }
+        return;
+    }
+#pragma unroll
+    for (int q2 = 0; q2 < KT; ++q2)
+        if (q2 < m) {
+            a.qi_out[row + q2] = i;
+            a.pj_out[row + q2] = bj[q2];
+            a.d_out[row + q2] = sqrtf(br[q2]);
+        }
+}
+
+// Exact ranking for flagged queries: candidates whose FP32 r2 is within the threshold
+// get their FP64 r2 and are ranked by (r2, j) in double precision.
+template <int KT>
+__global__ void __launch_bounds__(64) k_knn_exact(KnnArgs a) {
+    const int nflag = min(*a.flag_count, a.flag_cap);
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nflag; f += gridDim.x * blockDim.x) {
+        const int4 fl = a.flags[f];
+        const int64_t t = fl.x;
+        const int s = fl.y;
+        const float thr = __int_as_float(fl.z);
+        const float4 q = a.qs[t];
+        const int i = __float_as_int(q.w);
+        int cx, cy, cz;
+        cell_coords(a.qcell[t], a.nc, cx, cy, cz);
+        const int excl = a.exclude ? i : -1;
+        const int m = a.counts[i];
+        bool all_full;
+        const Stencil S = knn_stencil(a, s, all_full);
+        double br[KT];
+        int bj[KT];
+#pragma unroll
+        for (int q2 = 0; q2 < KT; ++q2) {
+            br[q2] = INFINITY;
+            bj[q2] = 0x7fffffff;
+        }
+        for_stencil(S, cx, cy, cz, make_float3(q.x, q.y, q.z), false, [&](int cell, float qx, float qy, float qz, bool) {
+            const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
+            for (uint32_t p = beg; p < end; ++p) {
+                const float4 c = __ldg(a.pts + p);
+                const int j = __float_as_int(c.w);
+                if (j == excl) continue;
+                const float3 d = cand_disp(S, a.bf, c, qx, qy, qz);
+                const float r2 = r2_f32(d.x, d.y, d.z);
+                if (r2 > thr) continue;
+                const double e = exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j);
+                if (e < br[KT - 1] || (e == br[KT - 1] && j < bj[KT - 1])) {
+                    double cr = e;
+                    int cj = j;
+#pragma unroll
+                    for (int q2 = 0; q2 < KT; ++q2) {
+                        const bool less = cr < br[q2] || (cr == br[q2] && cj < bj[q2]);
+                        const double tr = less ? br[q2] : cr;
+                        const int tj = less ? bj[q2] : cj;
+                        br[q2] = less ? cr : br[q2];
+                        bj[q2] = less ? cj : bj[q2];
+                        cr = tr;
+                        cj = tj;
+                    }
+                }
+            }
+        });
+        const int64_t row = (int64_t)i * a.stride;
+#pragma unroll
+        for (int q2 = 0; q2 < KT; ++q2)
+            if (q2 < m) {
+                a.qi_out[row + q2] = i;
+                a.pj_out[row + q2] = bj[q2];
+                a.d_out[row + q2] = (float)sqrt(br[q2]);
+            }
+    }
+}
+
+// Packs rows of stride k into the final arrays (only when row lengths differ).
+__global__ void k_knn_compact(const int64_t *__restrict__ seg, const int32_t *__restrict__ counts, int64_t nq, int k,
+                              const int32_t *__restrict__ tqi, const int32_t *__restrict__ tpj,
+                              const float *__restrict__ td, int32_t *qi, int32_t *pj, float *d) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    for (int a = 0; a < counts[i]; ++a) {
+        qi[seg[i] + a] = tqi[i * k + a];
+        pj[seg[i] + a] = tpj[i * k + a];
+        d[seg[i] + a] = td[i * k + a];
+    }
+}
+
+__global__ void k_knn_segments(int64_t nq, int m, int64_t *seg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nq) seg[i] = i * (int64_t)m;
+}
+
+template <int KT>
+static void launch_knn(const KnnArgs &a, cudaStream_t s) {
+    k_knn<KT><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a);
+    k_knn_exact<KT><<<num_sms() * 2, 64, 0, s>>>(a);
+}
+
+int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cudaStream_t s, fgb_nlist *nl) {
+    const int k = args->num_neighbors;
+    if (k > 32) return fail(FGB_ERR_UNSUPPORTED, "num_neighbors > 32 is not supported");
+    const int64_t nqq = Q.n, np = nq->n;
+    const bool excl = args->exclude_ii != 0;
+    // every query has the same row length unless exclusion removes a point for some
+    // queries only (separate query points with at most k points)
+    int64_t avail_min = np - ((excl && (Q.self || nqq > 0)) ? 1 : 0);
+    const bool uniform = Q.self || !excl || np > k;
+    const int m_uniform = (int)std::min<int64_t>(k, std::max<int64_t>(0, Q.self ? avail_min : (excl ? np - 1 : np)));
+    StencilPlan plan;
+    FGB_TRY(plan_stencil(nq, nq->grid.wc[0] * 0.5, kMaxStencil, s, &plan));
+    KnnArgs a;
+    memset(&a, 0, sizeof(a));
+    const GridHost &g = nq->grid;
+    const BoxHost &b = nq->box;
+    for (int q = 0; q < 3; ++q) {
+        a.nc[q] = g.nc[q];
+        a.ts[q] = plan.mode == 0 ? plan.ts[q] : 0;
+        a.wc[q] = (float)g.wc[q];
+    }
+    a.off = plan.mode == 0 ? plan.table : nullptr;
+    a.step[0] = make_float3((float)(b.M[0][0] / g.nc[0]), 0.f, 0.f);
+    a.step[1] = make_float3((float)(b.M[0][1] / g.nc[1]), (float)(b.M[1][1] / g.nc[1]), 0.f);
+    a.step[2] = make_float3((float)(b.M[0][2] / g.nc[2]), (float)(b.M[1][2] / g.nc[2]), (float)(b.M[2][2] / g.nc[2]));
+    a.bf = b.f;
+    a.bd = b.d;
+    a.pts = nq->sorted;
+    a.cell_start = nq->cell_start;
+    a.qs = Q.sorted;
+    a.qcell = Q.cell;
+    a.nq = nqq;
+    a.npts = np;
+    a.p_orig = nq->points;
+    a.q_orig = Q.orig;
+    a.k = k;
+    a.exclude = excl ? 1 : 0;
+    a.self = Q.self ? 1 : 0;
+    a.stride = uniform ? m_uniform : k;
+    double rowmax = 0;
+    for (int r = 0; r < 3; ++r) {
+        double e = 0;
+        for (int c = 0; c < 3; ++c) e += std::fabs(b.M[r][c]) / g.nc[c];
+        rowmax = std::max(rowmax, e);
+    }
+    a.ext = (float)g.ext;
+    a.rowmax = (float)rowmax;
+    a.Lsum = (float)plan.Lsum;
+    a.half_wmin2 = (float)(0.25 * b.wmin * b.wmin * (1.0 - 1e-4));
+    a.flag_cap = (int)std::min<int64_t>(std::max<int64_t>(nqq, 1), 1 << 24);
+    int *ctl = nullptr;  // [0] flag count, [1] error bits
+    nl->n_query = nqq;
+    nl->n_points = np;
+    const int64_t rows = uniform ? nqq * (int64_t)m_uniform : nqq * (int64_t)k;
+    int32_t *tqi = nullptr, *tpj = nullptr;
+    float *td = nullptr;
+    int st = dalloc_n(&ctl, 2, s);
+    st = st ? st : dalloc_n(&a.flags, a.flag_cap, s);
+    st = st ? st : dalloc_n(&nl->counts, nqq, s);
+    st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
+    st = st ? st : dalloc_n(&tqi, rows, s);
+    st = st ? st : dalloc_n(&tpj, rows, s);
+    st = st ? st : dalloc_n(&td, rows, s);
+    if (st == FGB_OK) {
+        cudaMemsetAsync(ctl, 0, 2 * sizeof(int), s);
+        a.flag_count = ctl;
+        a.err = ctl + 1;
+        a.qi_out = tqi;
+        a.pj_out = tpj;
+        a.d_out = td;
+        a.counts = nl->counts;
+        if (nqq > 0) {
+            const int KT = k + 1;
+            if (KT <= 5) launch_knn<5>(a, s);
+            else if (KT <= 9) launch_knn<9>(a, s);
+            else if (KT <= 13) launch_knn<13>(a, s);
+            else if (KT <= 17) launch_knn<17>(a, s);
+            else if (KT <= 25) launch_knn<25>(a, s);
+            else launch_knn<33>(a, s);
+        }
+        if (uniform) {
+            k_knn_segments<<<(unsigned)((nqq + 256) / 256), 256, 0, s>>>(nqq, m_uniform, nl->segments);
+        } else {
+            st = scan_u32_i64(reinterpret_cast<uint32_t *>(nl->counts), nl->segments, nqq, nullptr, s);
+        }
+        int hctl[2] = {0, 0};
+        int64_t total = rows;
+        cudaMemcpyAsync(hctl, ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!uniform) cudaMemcpyAsync(&total, nl->segments + nqq, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st == FGB_OK && e != cudaSuccess) st = fail(FGB_ERR_CUDA, "kNN query failed: %s", cudaGetErrorString(e));
+        if (st == FGB_OK && (hctl[1] & 1))
+            st = fail(FGB_ERR_BOX_TOO_SMALL, "a k-th nearest neighbor lies at or beyond half the smallest box width");
+        if (st == FGB_OK && (hctl[1] & 2)) st = fail(FGB_ERR_CAPACITY, "kNN re-ranking list overflowed");
+        nl->escalations = hctl[0];
+        nl->n_pairs = total;
+        if (st == FGB_OK && uniform) {
+            nl->qi = tqi;
+            nl->pj = tpj;
+            nl->dist = td;
+            tqi = tpj = nullptr;
+            td = nullptr;
+        } else if (st == FGB_OK) {
+            st = st ? st : dalloc_n(&nl->qi, total, s);
+            st = st ? st : dalloc_n(&nl->pj, total, s);
+            st = st ? st : dalloc_n(&nl->dist, total, s);
+            if (st == FGB_OK && nqq > 0)
+                k_knn_compact<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(nl->segments, nl->counts, nqq, k, tqi, tpj,
+                                                                           td, nl->qi, nl->pj, nl->dist);
+        }
+    }
+    dfree(tqi, s);
+    dfree(tpj, s);
+    dfree(td, s);
+    dfree(ctl, s);
+    dfree(a.flags, s);
+    dfree(plan.table, s);
+    nl->symmetric = 0;
+    nl->kind = 1;
+    (void)avail_min;
+    return st;
+}
+
+}  // namespace fgb

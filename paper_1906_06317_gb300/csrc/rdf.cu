@@ -1,0 +1,340 @@
+// Radial distribution function (density module; reset=False accumulation of the
+// Compute-class protocol in Section "Implementation").
+//
+// Fused query + histogram: pairs are never stored (the paper's lazy neighbor iterators,
+// Section "General Utilities").  One thread per query point in cell order; for a self
+// query each unordered pair is visited once (half stencil, same-cell pairs by sorted
+// position) and counted twice.  Counts go to privatised shared-memory histograms
+// (one copy per group of warps) merged into a global uint64 accumulator at block end
+// (the thread-local histograms with lazy reduction of Section "Implementation").
+// Pairs whose FP32 r2 lies inside the error band of a bin edge are appended to a list
+// and binned by a second kernel with the defining FP64 sequence.
+#include <cmath>
+#include <cstring>
+
+#include "fgb_device.cuh"
+
+struct fgb_rdf {
+    int bins;
+    double r_max, r_min;
+    unsigned long long *hist;  // device, bins
+    double *T;                 // device, exact r2 thresholds of the bins+1 edges
+    std::vector<double> T_host;
+    double norm;               // sum over frames of N_query * N_points / V
+    float2 *band;              // device, FP32 bands around the edges
+    double band_delta;
+    int2 *esc;
+    int esc_cap;
+    int *esc_count;            // device [0] count
+    int64_t last_esc;
+    cudaStream_t stream;
+};
+
+namespace fgb {
+
+struct RdfArgs {
+    Stencil S;
+    BoxF bf;
+    BoxD bd;
+    const float4 *pts;
+    const uint32_t *cell_start;
+    const float4 *qs;
+    const uint32_t *qcell;
+    int64_t nq;
+    const float *p_orig;
+    const float *q_orig;
+    int exclude;
+    int half;
+    int bins;
+    int copies;
+    float rmin, invdelta;
+    const float2 *band;  // (bins+1): lo/hi around each edge
+    const double *T;
+    unsigned long long *hist;
+    int2 *esc;
+    int esc_cap;
+    int *esc_count;
+    unsigned weight;
+};
+
+__device__ __forceinline__ int exact_bin(const double *T, int bins, double e) {
+    if (!(e >= T[0]) || !(e < T[bins])) return -1;
+    int lo = 0, hi = bins;  // T[lo] <= e < T[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (T[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <bool SHARED>
+__global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
+    extern __shared__ uint32_t sh[];  // copies * bins
+    if (SHARED) {
+        for (int b = threadIdx.x; b < a.bins * a.copies; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t *my = sh + ((threadIdx.x >> 5) % a.copies) * a.bins;
+    if (t < a.nq) {
+        const float4 q = a.qs[t];
+        const int i = __float_as_int(q.w);
+        int cx, cy, cz;
+        cell_coords(a.qcell[t], a.S.nc, cx, cy, cz);
+        const int excl = a.exclude ? i : -1;
+        const float rmax_hi = a.band[a.bins].y;
+        const float rmin_lo = a.band[0].x;
+        for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), a.half != 0,
+                    [&](int cell, float qx, float qy, float qz, bool center) {
+                        uint32_t beg = __ldg(a.cell_start + cell);
+                        const uint32_t end = __ldg(a.cell_start + cell + 1);
+                        if (a.half && center) beg = max(beg, (uint32_t)t + 1u);
+                        for (uint32_t p = beg; p < end; ++p) {
+                            const float4 c = __ldg(a.pts + p);
+                            const float3 d = cand_disp(a.S, a.bf, c, qx, qy, qz);
+                            const float r2 = r2_f32(d.x, d.y, d.z);
+                            if (r2 >= rmax_hi || r2 < rmin_lo) continue;
+                            const int j = __float_as_int(c.w);
+                            if (j == excl) continue;
+                            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+                            int b = (int)((r - a.rmin) * a.invdelta);
+                            b = min(max(b, 0), a.bins - 1);
+                            float2 e0 = __ldg(a.band + b), e1 = __ldg(a.band + b + 1);
+                            if (r2 < e0.x && b > 0) {
+                                --b;
+                                e1 = e0;
+                                e0 = __ldg(a.band + b);
+                            } else if (r2 >= e1.y && b + 1 < a.bins) {
+                                ++b;
+                                e0 = e1;
+                                e1 = __ldg(a.band + b + 1);
+                            }
+                            if (r2 >= e0.y && r2 < e1.x) {
+                                if (SHARED)
+                                    atomicAdd(my + b, 1u);
+                                else
+                                    atomicAdd(a.hist + b, (unsigned long long)a.weight);
+                            } else {
+                                const int slot = atomicAdd(a.esc_count, 1);
+                                if (slot < a.esc_cap) {
+                                    a.esc[slot] = make_int2(i, j);
+                                } else {
+                                    const int be = exact_bin(a.T, a.bins, exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j));
+                                    if (be >= 0) atomicAdd(a.hist + be, (unsigned long long)a.weight);
+                                }
+                            }
+                        }
+                    });
+    }
+    if (SHARED) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+            uint32_t v = 0;
+            for (int c = 0; c < a.copies; ++c) v += sh[c * a.bins + b];
+            if (v) atomicAdd(a.hist + b, (unsigned long long)v * a.weight);
+        }
+    }
+}
+
+// Band around each exact edge threshold, rounded outward.
+__global__ void k_band(const double *__restrict__ T, int n, double delta, float2 *__restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) out[b] = make_float2(__double2float_rd(__dsub_rd(T[b], delta)), __double2float_ru(__dadd_ru(T[b], delta)));
+}
+
+__global__ void k_rdf_escalated(RdfArgs a) {
+    const int n = min(*a.esc_count, a.esc_cap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int2 p = a.esc[e];
+        const int b = exact_bin(a.T, a.bins, exact_r2_idx(a.bd, a.q_orig, p.x, a.p_orig, p.y));
+        if (b >= 0) atomicAdd(a.hist + b, (unsigned long long)a.weight);
+    }
+}
+
+// Histogram of the pairs of a NeighborList: every pair decided with the FP64 sequence.
+__global__ void k_rdf_nlist(BoxD bd, const int32_t *__restrict__ qi, const int32_t *__restrict__ pj, int64_t m,
+                            const float *q_orig, const float *p_orig, const double *T, int bins,
+                            unsigned long long *hist) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = exact_bin(T, bins, exact_r2_idx(bd, q_orig, qi[e], p_orig, pj[e]));
+        if (b >= 0) atomicAdd(hist + b, 1ull);
+    }
+}
+
+}  // namespace fgb
+
+using namespace fgb;
+
+extern "C" int fgb_rdf_create(int32_t bins, double r_max, double r_min, fgb_rdf **out) {
+    clear_error();
+    if (!out) return fail(FGB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (bins <= 0 || bins > (1 << 24)) return fail(FGB_ERR_INVALID_ARG, "bins must be in [1, 2^24]");
+    if (!(r_min >= 0.0) || !(r_max > r_min) || !std::isfinite(r_max))
+        return fail(FGB_ERR_INVALID_ARG, "need 0 <= r_min < r_max");
+    fgb_rdf *r = new fgb_rdf();
+    r->bins = bins;
+    r->r_max = r_max;
+    r->r_min = r_min;
+    r->T_host.resize(bins + 1);
+    const double delta = (r_max - r_min) / bins;
+    for (int b = 0; b < bins; ++b) r->T_host[b] = sqrt_threshold(r_min + b * delta);
+    r->T_host[bins] = sqrt_threshold(r_max);
+    *out = r;
+    return FGB_OK;
+}
+
+extern "C" void fgb_rdf_destroy(fgb_rdf *r) {
+    if (!r) return;
+    dfree(r->hist, r->stream);
+    dfree(r->T, r->stream);
+    dfree(r->esc, r->stream);
+    dfree(r->esc_count, r->stream);
+    dfree(r->band, r->stream);
+    delete r;
+}
+
+static int rdf_ensure(fgb_rdf *r, int64_t esc_cap, cudaStream_t s) {
+    if (!r->hist) {
+        r->stream = s;
+        FGB_TRY(dalloc_n(&r->hist, r->bins, s));
+        FGB_CUDA(cudaMemsetAsync(r->hist, 0, sizeof(unsigned long long) * r->bins, s));
+        FGB_TRY(dalloc_n(&r->T, r->bins + 1, s));
+        FGB_CUDA(cudaMemcpyAsync(r->T, r->T_host.data(), sizeof(double) * (r->bins + 1), cudaMemcpyHostToDevice, s));
+        FGB_CUDA(cudaStreamSynchronize(s));
+        FGB_TRY(dalloc_n(&r->esc_count, 2, s));
+    }
+    if (esc_cap > r->esc_cap) {
+        dfree(r->esc, s);
+        r->esc = nullptr;
+        r->esc_cap = 0;
+        FGB_TRY(dalloc_n(&r->esc, esc_cap, s));
+        r->esc_cap = (int)esc_cap;
+    }
+    return FGB_OK;
+}
+
+extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points, int64_t n_query,
+                               const fgb_nlist *nlist, int32_t reset, void *stream) {
+    clear_error();
+    if (!r || !nq) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = as_stream(stream);
+    const double R = r->r_max;
+    if (!(R < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
+        return fail(FGB_ERR_BOX_TOO_SMALL, "RDF r_max=%g must be below half the smallest box width (%g)", R,
+                    0.5 * nq->box.wmin);
+    QueryPoints Q;
+    FGB_TRY(prepare_queries(nq, nlist ? nullptr : query_points, n_query, s, &Q));
+    const int64_t nqq = nlist ? nlist->n_query : Q.n;
+    // expected number of band hits is well below one per query; overflow falls back to
+    // deciding in the main kernel
+    int st = rdf_ensure(r, std::min<int64_t>(std::max<int64_t>(nqq * 2, 1 << 16), 1 << 27), s);
+    if (st == FGB_OK && reset) {
+        cudaMemsetAsync(r->hist, 0, sizeof(unsigned long long) * r->bins, s);
+        r->norm = 0.0;
+    }
+    if (st == FGB_OK) cudaMemsetAsync(r->esc_count, 0, sizeof(int), s);
+    if (st == FGB_OK && nlist) {
+        const float *q_orig = query_points ? query_points : nq->points;
+        if (nlist->n_pairs > 0)
+            k_rdf_nlist<<<num_sms() * 8, 256, 0, s>>>(nq->box.d, nlist->qi, nlist->pj, nlist->n_pairs, q_orig,
+                                                      nq->points, r->T, r->bins, r->hist);
+        st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "rdf nlist launch failed");
+    } else if (st == FGB_OK && nqq > 0) {
+        StencilPlan plan;
+        st = plan_stencil(nq, R, 0, s, &plan);
+        if (st == FGB_OK) {
+            RdfArgs a;
+            memset(&a, 0, sizeof(a));
+            a.S = to_device(nq, plan);
+            a.bf = nq->box.f;
+            a.bd = nq->box.d;
+            a.pts = nq->sorted;
+            a.cell_start = nq->cell_start;
+            a.qs = Q.sorted;
+            a.qcell = Q.cell;
+            a.nq = nqq;
+            a.p_orig = nq->points;
+            a.q_orig = Q.orig;
+            a.exclude = Q.self ? 1 : 0;
+            a.half = (Q.self && plan.mode == 0) ? 1 : 0;
+            a.weight = a.half ? 2u : 1u;
+            a.bins = r->bins;
+            a.rmin = (float)r->r_min;
+            a.invdelta = (float)(r->bins / (r->r_max - r->r_min));
+            a.T = r->T;
+            a.hist = r->hist;
+            a.esc = r->esc;
+            a.esc_cap = r->esc_cap;
+            a.esc_count = r->esc_count;
+            // bands around every edge (rebuilt only when the error bound changes)
+            const double delta = r2_error_bound(plan, R);
+            if (!r->band) st = dalloc_n(&r->band, r->bins + 1, s);
+            if (st == FGB_OK && delta != r->band_delta) {
+                k_band<<<(r->bins + 256) / 256, 256, 0, s>>>(r->T, r->bins + 1, delta, r->band);
+                r->band_delta = delta;
+            }
+            if (st == FGB_OK) {
+                a.band = r->band;
+                const int block = 256;
+                int copies = 4;
+                while (copies > 1 && (size_t)copies * r->bins * 4 > 32 * 1024) copies >>= 1;
+                const size_t smem = (size_t)copies * r->bins * 4;
+                a.copies = copies;
+                const unsigned grid = (unsigned)((nqq + block - 1) / block);
+                if (smem <= 48 * 1024)
+                    k_rdf<true><<<grid, block, smem, s>>>(a);
+                else
+                    k_rdf<false><<<grid, block, 0, s>>>(a);
+                k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "rdf launch failed: %s", cudaGetErrorString(e));
+            }
+            dfree(plan.table, s);
+        }
+    }
+    if (st == FGB_OK) r->norm += (double)nqq * (double)nq->n / (nq->box.p[0] * nq->box.p[1] * nq->box.p[2]);
+    release_queries(&Q, s);
+    return st;
+}
+
+extern "C" int fgb_rdf_result(fgb_rdf *r, uint64_t *counts, double *rdf_values, double *bin_centers, void *stream) {
+    clear_error();
+    if (!r) return fail(FGB_ERR_INVALID_ARG, "rdf is NULL");
+    cudaStream_t s = as_stream(stream);
+    std::vector<unsigned long long> h(r->bins, 0ull);
+    if (r->hist) {
+        FGB_CUDA(cudaMemcpyAsync(h.data(), r->hist, sizeof(unsigned long long) * r->bins, cudaMemcpyDeviceToHost, s));
+        FGB_CUDA(cudaStreamSynchronize(s));
+    }
+    const double delta = (r->r_max - r->r_min) / r->bins;
+    for (int b = 0; b < r->bins; ++b) {
+        if (counts) counts[b] = h[b];
+        const double R0 = r->r_min + b * delta;
+        const double R1 = b + 1 < r->bins ? r->r_min + (b + 1) * delta : r->r_max;
+        const double shell = 4.0 / 3.0 * M_PI * (R1 * R1 * R1 - R0 * R0 * R0);
+        if (rdf_values) rdf_values[b] = r->norm > 0 ? (double)h[b] / (r->norm * shell) : 0.0;
+        if (bin_centers) bin_centers[b] = r->r_min + (b + 0.5) * delta;
+    }
+    return FGB_OK;
+}
+
+extern "C" int fgb_rdf_counts_device(const fgb_rdf *r, const uint64_t **counts) {
+    if (!r || !counts) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    *counts = reinterpret_cast<const uint64_t *>(r->hist);
+    return FGB_OK;
+}
+
+extern "C" int fgb_rdf_escalations(fgb_rdf *r, int64_t *n, void *stream) {
+    if (!r || !n) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    int v = 0;
+    if (r->esc_count) {
+        FGB_CUDA(cudaMemcpyAsync(&v, r->esc_count, sizeof(int), cudaMemcpyDeviceToHost, as_stream(stream)));
+        FGB_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    }
+    *n = v;
+    return FGB_OK;
+}
