@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of the cell-list neighbor query + RDF on 4,194,304 points (one GB300).
+
+Workload (one step): N = 4,194,304 uniform points in a cubic box at density 0.85 (seeded,
+synthetic, shaped like the paper's random-point benchmarks); build the cell list; ball
+query r_max = 2.5 producing the full sorted NeighborList (~2.33e8 pairs); fused RDF of
+500 bins on [0, 5] (~1.87e9 ordered pairs, never stored).  value = neighbor pairs
+handled per second = (NeighborList pairs + RDF pairs) / step time, summed over ranks.
+
+Timing: W untimed warm-up steps; K timed steps, each bracketed by CUDA events on the
+launching stream; L2 is flushed (a 512 MB write) before every step outside the events;
+barrier + synchronize around the timed region; max over ranks.  Per-kernel device times
+come from libfgb's own CUDA events over the same region.  `e2e` repeats the step through
+the public API from pinned host memory (H2D of the points and D2H of the RDF counts and
+pair total inside the events).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload on all host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 2 ** 20
+ORACLE_SAMPLE = 65536  # queries of the workload the CPU oracle times per step
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------ oracle arm
+
+
+def oracle_rate(w, sample: int, threads: int):
+    """Pairs per second of the CPU oracle on queries [0, sample), with the O(N) cell-list
+    builds charged in proportion (sample / N)."""
+    import oracle
+    p = w.params
+    n = len(w.points)
+    t0 = time.perf_counter()
+    c_nl = oracle.Cells(w.box, w.points, p["r_max"])
+    c_rdf = oracle.Cells(w.box, w.points, p["rdf_r_max"])
+    t_cells = time.perf_counter() - t0
+    del c_nl, c_rdf
+    t1 = time.perf_counter()
+    counts, _, _, _ = oracle.ball_query(w.box, w.points, p["r_max"], queries=(0, sample), threads=threads)
+    h = oracle.rdf_counts(w.box, w.points, p["rdf_bins"], p["rdf_r_max"], queries=(0, sample), threads=threads)
+    t_q = time.perf_counter() - t1
+    pairs = int(counts.sum()) + int(h.sum())
+    # each oracle call builds its own cell list over all N points; charge those builds
+    # only in proportion to the fraction of the workload the sample covers
+    t = t_q - 2 * t_cells * (1.0 - sample / n)
+    return pairs / t, pairs, t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = W.c3()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_rate(w, ORACLE_SAMPLE // 8, threads)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads)
+        rates.append(r)
+        times.append(t)
+    v = statistics.median(rates)
+    sample = f"queries [0, {ORACLE_SAMPLE}) of {len(w.points)} (ball r=2.5 + RDF 500 bins [0,5]); cell builds charged pro rata"
+    line = {"impl": "reference", "metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": v,
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c3: cubic rho=0.85, N=4194304 uniform, ball r=2.5 NL + RDF 500 bins [0,5]",
+                       "oracle_sample": sample},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the kNN / Q6 / batch component timings")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1906_06317_gb300 as fgb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    w = W.c3(seed=3 + rank)
+    p = w.params
+    host = torch.from_numpy(w.points).pin_memory()
+    pts = host.to(dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    rdf = fgb.RDF(p["rdf_bins"], p["rdf_r_max"])
+    stream = torch.cuda.current_stream()
+
+    def step(x):
+        nq = fgb.NeighborQuery(w.box, x, r_cell=p["r_max"])
+        nl = nq.query(None, dict(r_max=p["r_max"], exclude_ii=True)).toNeighborList()
+        rdf.compute(nq, reset=True)
+        return nl
+
+    for _ in range(max(3, args.warmup)):
+        nl = step(pts)
+    torch.cuda.synchronize()
+    nl_pairs = nl.n_pairs
+    rdf_pairs = int(rdf.bin_counts.sum())
+    units = nl_pairs + rdf_pairs
+    del nl
+
+    # ---------------- timed region (device-resident inputs)
+    fgb.timing_reset()
+    fgb.timing_enable(True)
+    launches0 = fgb.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if world == 1 else local)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nl = step(pts)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del nl
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    launches = (fgb.kernel_launches() - launches0) // args.steps
+    fgb.timing_enable(False)
+    kern = {}
+    for name in ("k_bin", "k_radix_hist", "k_radix_scatter", "k_cell_start", "k_ball_count", "k_ball_write",
+                 "k_reduce", "k_top", "k_down", "k_rdf", "k_rdf_escalated", "k_offset_table", "k_origin_tables",
+                 "k_band"):
+        t, n = fgb.timing_read(name)
+        if n:
+            kern[name] = {"ms_per_step": t / args.steps, "launches_per_step": n / args.steps}
+    step_ms = sum(ms) / len(ms)
+    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t_max.item())
+    value = units * world / (step_ms_max * 1e-3)
+
+    # ---------------- end to end through the public API, host buffers
+    e2e_ms = []
+    for k in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x = host.to(dev, non_blocking=True)
+        nl = step(x)
+        counts = rdf.bin_counts           # D2H of the step's result (synchronises)
+        got = int(counts.sum()) + nl.n_pairs
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        assert got == units
+        del nl, x
+    e2e_step = statistics.median(e2e_ms)
+
+    # ---------------- roofline of the dominant kernel
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    n = len(w.points)
+    dominant = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    sm_clock = (clk or {}).get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12   # FP32 lane-instructions per second, T/s
+    rdf_unordered = rdf_pairs / 2
+    roofs = {
+        # 12 B per stored pair + the sorted query read (16 B), counts and offsets (12 B) per query
+        "k_ball_write": ("hbm", (12.0 * nl_pairs + 28.0 * n) / 1e9, "GB/s", hbm),
+        # 16 B sorted point read + 4 B count write per query
+        "k_ball_count": ("hbm", 20.0 * n / 1e9, "GB/s", hbm),
+        # ~10 FP32 operations per unordered pair inside r_max (difference, r^2, bin, compare)
+        "k_rdf": ("alu", 10.0 * rdf_unordered / 1e12, "TOP/s", alu_peak),
+    }
+    bound, work, unit, peak = roofs.get(dominant, ("hbm", 0.0, "GB/s", hbm))
+    t_dom = kern[dominant]["ms_per_step"] / kern[dominant]["launches_per_step"] * 1e-3
+    achieved = work / t_dom
+    roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm"
+                else f"derived: 152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
+    others = {}
+    for k, (b, wk, u, pk) in roofs.items():
+        if k in kern:
+            tk = kern[k]["ms_per_step"] / kern[k]["launches_per_step"] * 1e-3
+            others[k] = {"bound": b, "achieved": wk / tk, "peak": pk, "unit": u, "frac": wk / tk / pk,
+                         "ms": tk * 1e3}
+
+    # ---------------- other parts of the hot path (component timings)
+    components = {}
+    if not args.no_extras and rank == 0:
+        components = extras(fgb, torch, dev, stream, flush)
+
+    # ---------------- CPU oracle baseline (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads)
+        cpu = {"value": r, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": f"queries [0, {ORACLE_SAMPLE}) of {n}: {pairs} pairs in {t:.1f} s "
+                         "(cell builds charged pro rata)"}
+
+    if rank == 0:
+        line = {"metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": value, "unit": "pairs/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": "c3: cubic rho=0.85, N=4194304 uniform, cell list r=2.5, ball r=2.5 full "
+                                       "sorted NeighborList + fused RDF 500 bins [0,5]",
+                           "nl_pairs": nl_pairs, "rdf_pairs": rdf_pairs, "points_per_rank": n,
+                           "l2": "flushed (512 MB write) before every step", "parallelism": f"{world} independent frames"},
+                "e2e": {"value": units * world / (e2e_step * 1e-3), "unit": "pairs/s",
+                        "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": p["rdf_bins"] * 8},
+                "gpu_launches": int(launches), "roofline": roofline, "kernels": kern, "kernel_rooflines": others,
+                "components": components, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def timed(fn, stream, flush, reps=5, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def extras(fgb, torch, dev, stream, flush):
+    comp = {}
+    # kNN k=12 on the same 4M-point workload (its own cell size)
+    w = W.c3()
+    x = torch.from_numpy(w.points).to(dev)
+
+    def knn():
+        nq = fgb.NeighborQuery(w.box, x, r_cell=1.6)
+        return nq.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
+
+    comp["c3_knn12_ms"] = timed(knn, stream, flush)
+    # Q6 forward + backward, N = 2^20, fixed neighbor list r = 1.3
+    w4 = W.c4()
+    x4 = torch.from_numpy(w4.points).to(dev)
+    nq4 = fgb.NeighborQuery(w4.box, x4, r_cell=1.3)
+    nl4 = nq4.query(None, dict(r_max=1.3, exclude_ii=True)).toNeighborList()
+    st = fgb.Steinhardt(6)
+
+    def fwd():
+        st.compute(nq4, neighbors=nl4)
+
+    def fwdbwd():
+        st.compute(nq4, neighbors=nl4)
+        st.backward(1.0)
+
+    comp["c4_q6_fwd_ms"] = timed(fwd, stream, flush)
+    comp["c4_q6_fwd_bwd_ms"] = timed(fwdbwd, stream, flush)
+    # batched frames
+    if hasattr(fgb.lib(), "fgb_batch_run"):
+        try:
+            comp.update(batch_extras(fgb, torch, dev, stream, flush))
+        except Exception as e:  # report, do not hide
+            comp["c5_error"] = repr(e)
+    return comp
+
+
+def batch_extras(fgb, torch, dev, stream, flush):
+    frames = W.c5()
+    P = W.C5_PARAMS
+    sizes = [len(f.points) for f in frames]
+    pts = torch.from_numpy(np.concatenate([f.points for f in frames])).to(dev)
+    b = fgb.Batch(sizes, [f.box for f in frames], r_max=P["r_max"], l=P["l"], rdf_bins=P["rdf_bins"],
+                  rdf_r_max=P["rdf_r_max"])
+    tuned = b.tune(pts)
+    t_graph = timed(lambda: b.run(pts, graph=True), stream, flush)
+    xs = [torch.from_numpy(f.points).to(dev) for f in frames]
+    rdf = fgb.RDF(P["rdf_bins"], P["rdf_r_max"])
+    st = fgb.Steinhardt(P["l"])
+
+    def loop():
+        for f, xf in zip(frames, xs):
+            nq = fgb.NeighborQuery(f.box, xf, r_cell=P["r_max"])
+            rdf.compute(nq, reset=True)
+            st.compute(nq, neighbors=dict(r_max=P["r_max"], exclude_ii=True))
+
+    t_loop = timed(loop, stream, flush, reps=3, warm=1)
+    return {"c5_frames": len(frames), "c5_points": int(sum(sizes)), "c5_batched_graph_ms": t_graph,
+            "c5_frames_per_s_batched": len(frames) / (t_graph * 1e-3), "c5_per_frame_loop_ms": t_loop,
+            "c5_frames_per_s_per_frame_loop": len(frames) / (t_loop * 1e-3), "c5_tuned": tuned}
+
+
+if __name__ == "__main__":
+    main()

@@ -75,6 +75,16 @@ const char *fgb_last_error(void);
 /* Library ABI version (major*10000 + minor*100 + patch). */
 int32_t fgb_version(void);
 
+/* Diagnostics.  fgb_kernel_launches: kernels launched by this library since it was
+ * loaded (all threads).  fgb_timing_enable(1) brackets every later launch with CUDA
+ * events on its stream; fgb_timing_read waits for the recorded events and returns the
+ * summed device time (ms) and launch count of kernels named `name` (the __global__
+ * function name, e.g. "k_ball_write"); fgb_timing_reset clears the totals. */
+int64_t fgb_kernel_launches(void);
+int fgb_timing_enable(int32_t on);
+int fgb_timing_read(const char *name, double *total_ms, int64_t *count);
+int fgb_timing_reset(void);
+
 /* --------------------------------------------------------- NeighborQuery (cell list) */
 
 /*

@@ -60,6 +60,10 @@ class fgb_batch_params(ctypes.Structure):
 _SIGS = {
     "fgb_last_error": (ctypes.c_char_p, []),
     "fgb_version": (_I32, []),
+    "fgb_kernel_launches": (_I64, []),
+    "fgb_timing_enable": (_I32, [_I32]),
+    "fgb_timing_read": (_I32, [ctypes.c_char_p, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "fgb_timing_reset": (_I32, []),
     "fgb_nq_create": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _D, _P, _PP]),
     "fgb_nq_destroy": (None, [_P]),
     "fgb_nq_dims": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
@@ -108,6 +112,26 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libfgb in this process so far."""
+    return int(lib().fgb_kernel_launches())
+
+
+def timing_enable(on: bool = True):
+    _check(lib().fgb_timing_enable(int(bool(on))))
+
+
+def timing_read(name: str):
+    """(total device ms, launches) of the named kernel since the last reset."""
+    ms, n = _D(), _I64()
+    _check(lib().fgb_timing_read(name.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def timing_reset():
+    _check(lib().fgb_timing_reset())
 
 
 def exported_symbols():

@@ -19,10 +19,10 @@ __global__ void __launch_bounds__(128) k_ball_count(BallArgs a, uint32_t *__rest
     if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
 }
 
-// Write pass.  SHARED: each thread keeps its query's hits (j, distance bits) sorted by j
-// in a shared slab laid out [slot][thread]; the warp then writes each query's segment
-// with coalesced stores.  !SHARED (very large neighbor counts): insertion happens in the
-// output arrays themselves.
+// Write pass.  SHARED: each thread appends its query's hits (j, distance bits) to a
+// shared slab laid out [slot][thread], sorts them by j once the walk is done, and the warp
+// then writes each query's segment with coalesced stores.  !SHARED (very large neighbor
+// counts): insertion happens in the output arrays themselves.
 template <bool SHARED>
 __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *__restrict__ seg,
                                                     const uint32_t *__restrict__ counts, int cap,
@@ -46,16 +46,10 @@ __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *_
                 return;
             }
             const float dist = e < 0.0 ? sqrtf(r2) : (float)sqrt(e);
-            uint32_t pos = n;
             if (SHARED) {
-                while (pos > 0) {
-                    const uint2 prev = slab[(pos - 1) * blockDim.x + threadIdx.x];
-                    if ((int)prev.x < j) break;
-                    slab[pos * blockDim.x + threadIdx.x] = prev;
-                    --pos;
-                }
-                slab[pos * blockDim.x + threadIdx.x] = make_uint2((uint32_t)j, __float_as_uint(dist));
+                slab[n * blockDim.x + threadIdx.x] = make_uint2((uint32_t)j, __float_as_uint(dist));
             } else {
+                uint32_t pos = n;
                 while (pos > 0) {
                     const int pj = pj_out[off + pos - 1];
                     if (pj < j) break;
@@ -68,6 +62,26 @@ __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *_
             }
             ++n;
         });
+        if (SHARED) {
+            // hits arrive as one index-sorted run per stencil cell; a shell sort (gaps
+            // 57, 23, 10, 4, 1) orders them by point index with few moves
+            const int gaps[5] = {57, 23, 10, 4, 1};
+            const int B = blockDim.x, me = threadIdx.x;
+            for (int gi = 0; gi < 5; ++gi) {
+                const int g = gaps[gi];
+                for (int k = g; k < (int)n; ++k) {
+                    const uint2 v = slab[k * B + me];
+                    int m = k;
+                    while (m >= g) {
+                        const uint2 u = slab[(m - g) * B + me];
+                        if ((int)u.x < (int)v.x) break;
+                        slab[m * B + me] = u;
+                        m -= g;
+                    }
+                    slab[m * B + me] = v;
+                }
+            }
+        }
         if (n != want) atomicExch(a.err, 2);
     }
     if (SHARED) {
@@ -131,7 +145,10 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
     uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
     if (st == FGB_OK && nqq > 0) {
-        k_ball_count<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, counts);
+        {
+            FGB_KSCOPE("k_ball_count", s);
+            k_ball_count<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, counts);
+        }
         st = scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK) {
         cudaMemsetAsync(nl->segments, 0, sizeof(int64_t), s);
@@ -159,10 +176,16 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
         if (smem <= 200 * 1024) {
             if (smem > 48 * 1024)
                 cudaFuncSetAttribute(k_ball_write<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_ball_write<true><<<grid, block, smem, s>>>(a, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist);
+            {
+                FGB_KSCOPE("k_ball_write", s);
+                k_ball_write<true><<<grid, block, smem, s>>>(a, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist);
+            }
         } else {
-            k_ball_write<false><<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, nl->segments, counts, 0, nl->qi,
-                                                                             nl->pj, nl->dist);
+            {
+                FGB_KSCOPE("k_ball_write", s);
+                k_ball_write<false><<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, nl->segments, counts, 0, nl->qi,
+                                                                                 nl->pj, nl->dist);
+            }
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "ball query write launch failed: %s", cudaGetErrorString(e));
@@ -288,8 +311,11 @@ extern "C" int fgb_nlist_from_arrays(int64_t n_query, int64_t n_points, const in
         cudaMemsetAsync(nl->counts, 0, sizeof(int32_t) * (n_query > 0 ? n_query : 1), s);
         cudaMemsetAsync(err, 0, sizeof(int), s);
         if (m > 0)
-            k_count_from_qi<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
-                nl->qi, m, n_query, reinterpret_cast<uint32_t *>(nl->counts), err);
+            {
+                FGB_KSCOPE("k_count_from_qi", s);
+                k_count_from_qi<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+                    nl->qi, m, n_query, reinterpret_cast<uint32_t *>(nl->counts), err);
+            }
         st = scan_u32_i64(reinterpret_cast<uint32_t *>(nl->counts), nl->segments, n_query, nullptr, s);
         int herr = 0;
         cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -162,4 +162,129 @@ __device__ __forceinline__ float3 cand_disp(const Stencil &S, const BoxF &bf, fl
 
 Stencil to_device(const fgb_nq *nq, const StencilPlan &p);
 
+// ------------------------------------------------------------------ RDF binning
+
+// Bin of one pair for the RDF.  The fast test places x = (r - r_min)/Delta from the FP32
+// r and accepts bin floor(x) when x sits further than e from both edges, with
+//   e = g2h / r + 8u (x + r_min/Delta + 1),
+// g2h = 0.55 G2 / Delta bounding the shift of x caused by an r2 error of at most G2
+// (valid once r2 > 16 G2), the 8u term covering rsqrt, the product with 1/Delta and the
+// FP64 edge positions.  Otherwise the FP32 bands around the exact edge thresholds decide,
+// and pairs inside a band are left to the FP64 sequence.
+struct BinParams {
+    int bins;
+    float rmin, invdelta, rmin_invdelta, g2h, r2_fast;  // r2_fast = 16 G2
+    float rmax_hi, rmin_lo;                               // bands of the outer edges
+    const float2 *band;                                   // (bins+1) bands [lo, hi)
+};
+
+// >= 0: the bin; -1: certainly outside [r_min, r_max); -2: decide in FP64.
+__device__ __forceinline__ int rdf_bin(const BinParams &P, float r2) {
+    if (r2 >= P.rmax_hi || r2 < P.rmin_lo) return -1;
+    if (r2 > P.r2_fast) {
+        const float inv = rsqrtf(r2);
+        const float x = fmaf(r2 * inv, P.invdelta, -P.rmin_invdelta);
+        const float fb = floorf(x);
+        const float f = x - fb;
+        const float e = fmaf(8.f * kU32, x + P.rmin_invdelta + 1.f, P.g2h * inv);
+        const int b = (int)fb;
+        if (f > e && f < 1.f - e && b >= 0 && b < P.bins) return b;
+    }
+    const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+    int b = (int)((r - P.rmin) * P.invdelta);
+    b = min(max(b, 0), P.bins - 1);
+    float2 e0 = __ldg(P.band + b), e1 = __ldg(P.band + b + 1);
+    if (r2 < e0.x && b > 0) {
+        --b;
+        e1 = e0;
+        e0 = __ldg(P.band + b);
+    } else if (r2 >= e1.y && b + 1 < P.bins) {
+        ++b;
+        e0 = e1;
+        e1 = __ldg(P.band + b + 1);
+    }
+    if (r2 >= e0.y && r2 < e1.x) return b;
+    return -2;
+}
+Stencil to_device(const BoxHost &b, const GridHost &g, const StencilPlan &p, const float4 *table);
+
+// ------------------------------------------------------------------ binning
+
+struct GridDev {
+    int nc[3];
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Sum of three hi/lo pairs, returned as hi + lo.
+__device__ __forceinline__ float2 ds_sum3(float2 a, float2 b, float2 c) {
+    float s1, e1, s2, e2;
+    two_sum(a.x, b.x, s1, e1);
+    two_sum(s1, c.x, s2, e2);
+    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(a.y, b.y), c.y));
+    float hi = __fadd_rn(s2, lo);
+    lo = __fsub_rn(lo, __fsub_rn(hi, s2));
+    return make_float2(hi, lo);
+}
+
+// Cell and cell-local coordinate of one point.  The fractional coordinate is formed in
+// FP32 (it only selects a cell; the stencil margin absorbs its rounding).  The local
+// coordinate x - M (n + c/nc - 1/2) is formed from hi/lo origin tables, so its error is a
+// few ulps of the cell size rather than of the box size.  Points more than a few box
+// lengths away, or outside the primary box, take an FP64 route.
+__device__ __forceinline__ void bin_point(const BoxF &b, const BoxD &bd, const GridDev &g, const OriginTables &org,
+                                          float x, float y, float z, uint32_t &key, float4 &loc) {
+    float s[3];
+    s[2] = __fmaf_rn(z, b.inv22, 0.5f);
+    s[1] = __fmaf_rn(z, b.inv12, __fmaf_rn(y, b.inv11, 0.5f));
+    s[0] = __fmaf_rn(z, b.inv02, __fmaf_rn(y, b.inv01, __fmaf_rn(x, b.inv00, 0.5f)));
+    int c[3];
+    bool inbox = true;
+    float n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        n[k] = floorf(s[k]);
+        float f = __fsub_rn(s[k], n[k]);
+        int ck = (int)(f * (float)g.nc[k]);
+        c[k] = min(max(ck, 0), g.nc[k] - 1);
+        inbox &= (n[k] == 0.0f);
+    }
+    if (inbox) {
+        float2 ox = ds_sum3(__ldg(org.Tx + c[0]), __ldg(org.Txy + c[1]), __ldg(org.Txz + c[2]));
+        float2 oy = ds_sum3(__ldg(org.Ty + c[1]), __ldg(org.Tyz + c[2]), make_float2(0.f, 0.f));
+        float2 oz = __ldg(org.Tz + c[2]);
+        loc.x = __fsub_rn(__fsub_rn(x, ox.x), ox.y);
+        loc.y = __fsub_rn(__fsub_rn(y, oy.x), oy.y);
+        loc.z = __fsub_rn(__fsub_rn(z, oz.x), oz.y);
+    } else {
+        // FP64 route: fractional coordinate, wrap count and cell again in double
+        double xd = x, yd = y, zd = z;
+        double sd[3];
+        sd[2] = zd * bd.invL[2] + 0.5;
+        sd[1] = (yd - (sd[2] - 0.5) * bd.a3y) * bd.invL[1] + 0.5;
+        sd[0] = (xd - (sd[1] - 0.5) * bd.a2x - (sd[2] - 0.5) * bd.a3x) * bd.invL[0] + 0.5;
+        double gk[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double nk = floor(sd[k]);
+            double f = sd[k] - nk;
+            int ck = (int)(f * g.nc[k]);
+            c[k] = min(max(ck, 0), g.nc[k] - 1);
+            gk[k] = nk + (double)c[k] / g.nc[k] - 0.5;
+        }
+        double Ox = gk[0] * bd.L[0] + gk[1] * bd.a2x + gk[2] * bd.a3x;
+        double Oy = gk[1] * bd.L[1] + gk[2] * bd.a3y;
+        double Oz = gk[2] * bd.L[2];
+        loc.x = (float)(xd - Ox);
+        loc.y = (float)(yd - Oy);
+        loc.z = (float)(zd - Oz);
+    }
+    key = (uint32_t)((c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0]);
+}
+
+
 }  // namespace fgb

@@ -44,6 +44,19 @@ int dalloc_n(T **p, size_t n, cudaStream_t s) {
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 int num_sms();
 
+// Every kernel launch goes through a KernelScope: it counts the launch and, when timing
+// is enabled, brackets it with CUDA events on the launching stream.
+void note_launch(const char *name, cudaStream_t s, bool begin);
+struct KernelScope {
+    const char *name;
+    cudaStream_t s;
+    KernelScope(const char *n, cudaStream_t st) : name(n), s(st) { note_launch(name, s, true); }
+    ~KernelScope() { note_launch(name, s, false); }
+};
+#define FGB_KSCOPE_CAT2(a, b) a##b
+#define FGB_KSCOPE_CAT(a, b) FGB_KSCOPE_CAT2(a, b)
+#define FGB_KSCOPE(name, s) ::fgb::KernelScope FGB_KSCOPE_CAT(fgb_kscope_, __LINE__)(name, s)
+
 // ------------------------------------------------------------------ box
 
 // FP32 view of the box for the fast paths.  Box vectors a1 = (Lx,0,0),
@@ -162,12 +175,28 @@ struct StencilPlan {
     double Lsum;
 };
 int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, StencilPlan *p);
+// Same plan without device work; the mode-0 offset table is returned on the host.
+int plan_stencil_host(const BoxHost &b, const GridHost &g, double R, int s_table_min, StencilPlan *p,
+                      std::vector<float4> *table);
 double r2_error_bound(const StencilPlan &p, double R);
 // FP32 band [lo, hi) around the exact threshold T, widened by `delta` and rounded outward.
 void band_around(double T, double delta, float *lo, float *hi);
 
+// RDF bin parameters for an error bound G2 on r^2 (rdf.cu).
+struct BinParams;
+BinParams bin_params(int bins, double rmin, double rmax, double G2, const float2 *band, const std::vector<double> &T);
+
 // Exclusive scan helpers (scan.cu).  out has n+1 entries (out[n] = total).
 int scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, uint32_t *max_out, cudaStream_t s);
 int scan_u32_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+size_t scan_ws_bytes(int64_t n);
+int scan_u32_u32_ws(const uint32_t *in, uint32_t *out, int64_t n, void *ws, cudaStream_t s);
+
+// Stable radix sort of (cell key, point index) with caller workspace of sort_ws_bytes(n)
+// bytes; the final pass writes payload[index] records and keys in sorted order.
+size_t sort_ws_bytes(int64_t n);
+int radix_sort_cells(uint32_t *keys, uint32_t *vals, int64_t n, int64_t ncell, const float4 *payload, float4 *out_sorted,
+                     uint32_t *out_keys, void *ws, cudaStream_t s);
+int launch_cell_start(const uint32_t *skeys, int64_t n, int64_t ncell, uint32_t *start, cudaStream_t s);
 
 }  // namespace fgb

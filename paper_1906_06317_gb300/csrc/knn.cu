@@ -248,8 +248,14 @@ __global__ void k_knn_segments(int64_t nq, int m, int64_t *seg) {
 
 template <int KT>
 static void launch_knn(const KnnArgs &a, cudaStream_t s) {
-    k_knn<KT><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a);
-    k_knn_exact<KT><<<num_sms() * 2, 64, 0, s>>>(a);
+    {
+        FGB_KSCOPE("k_knn", s);
+        k_knn<KT><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a);
+    }
+    {
+        FGB_KSCOPE("k_knn_exact", s);
+        k_knn_exact<KT><<<num_sms() * 2, 64, 0, s>>>(a);
+    }
 }
 
 int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cudaStream_t s, fgb_nlist *nl) {
@@ -333,7 +339,10 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
             else launch_knn<33>(a, s);
         }
         if (uniform) {
-            k_knn_segments<<<(unsigned)((nqq + 256) / 256), 256, 0, s>>>(nqq, m_uniform, nl->segments);
+            {
+                FGB_KSCOPE("k_knn_segments", s);
+                k_knn_segments<<<(unsigned)((nqq + 256) / 256), 256, 0, s>>>(nqq, m_uniform, nl->segments);
+            }
         } else {
             st = scan_u32_i64(reinterpret_cast<uint32_t *>(nl->counts), nl->segments, nqq, nullptr, s);
         }
@@ -359,8 +368,11 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
             st = st ? st : dalloc_n(&nl->pj, total, s);
             st = st ? st : dalloc_n(&nl->dist, total, s);
             if (st == FGB_OK && nqq > 0)
-                k_knn_compact<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(nl->segments, nl->counts, nqq, k, tqi, tpj,
-                                                                           td, nl->qi, nl->pj, nl->dist);
+                {
+                    FGB_KSCOPE("k_knn_compact", s);
+                    k_knn_compact<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(nl->segments, nl->counts, nqq, k, tqi, tpj,
+                                                                               td, nl->qi, nl->pj, nl->dist);
+                }
         }
     }
     dfree(tqi, s);

@@ -116,82 +116,6 @@ int grid_for(const BoxHost &box, double r_cell, int64_t n, GridHost *g) {
 
 // ------------------------------------------------------------------ device: binning
 
-struct GridDev {
-    int nc[3];
-};
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Sum of three hi/lo pairs, returned as hi + lo.
-__device__ __forceinline__ float2 ds_sum3(float2 a, float2 b, float2 c) {
-    float s1, e1, s2, e2;
-    two_sum(a.x, b.x, s1, e1);
-    two_sum(s1, c.x, s2, e2);
-    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(a.y, b.y), c.y));
-    float hi = __fadd_rn(s2, lo);
-    lo = __fsub_rn(lo, __fsub_rn(hi, s2));
-    return make_float2(hi, lo);
-}
-
-// Cell and cell-local coordinate of one point.  The fractional coordinate is formed in
-// FP32 (it only selects a cell; the stencil margin absorbs its rounding).  The local
-// coordinate x - M (n + c/nc - 1/2) is formed from hi/lo origin tables, so its error is a
-// few ulps of the cell size rather than of the box size.  Points more than a few box
-// lengths away, or outside the primary box, take an FP64 route.
-__device__ __forceinline__ void bin_point(const BoxF &b, const BoxD &bd, const GridDev &g, const OriginTables &org,
-                                          float x, float y, float z, uint32_t &key, float4 &loc) {
-    float s[3];
-    s[2] = __fmaf_rn(z, b.inv22, 0.5f);
-    s[1] = __fmaf_rn(z, b.inv12, __fmaf_rn(y, b.inv11, 0.5f));
-    s[0] = __fmaf_rn(z, b.inv02, __fmaf_rn(y, b.inv01, __fmaf_rn(x, b.inv00, 0.5f)));
-    int c[3];
-    bool inbox = true;
-    float n[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        n[k] = floorf(s[k]);
-        float f = __fsub_rn(s[k], n[k]);
-        int ck = (int)(f * (float)g.nc[k]);
-        c[k] = min(max(ck, 0), g.nc[k] - 1);
-        inbox &= (n[k] == 0.0f);
-    }
-    if (inbox) {
-        float2 ox = ds_sum3(__ldg(org.Tx + c[0]), __ldg(org.Txy + c[1]), __ldg(org.Txz + c[2]));
-        float2 oy = ds_sum3(__ldg(org.Ty + c[1]), __ldg(org.Tyz + c[2]), make_float2(0.f, 0.f));
-        float2 oz = __ldg(org.Tz + c[2]);
-        loc.x = __fsub_rn(__fsub_rn(x, ox.x), ox.y);
-        loc.y = __fsub_rn(__fsub_rn(y, oy.x), oy.y);
-        loc.z = __fsub_rn(__fsub_rn(z, oz.x), oz.y);
-    } else {
-        // FP64 route: fractional coordinate, wrap count and cell again in double
-        double xd = x, yd = y, zd = z;
-        double sd[3];
-        sd[2] = zd * bd.invL[2] + 0.5;
-        sd[1] = (yd - (sd[2] - 0.5) * bd.a3y) * bd.invL[1] + 0.5;
-        sd[0] = (xd - (sd[1] - 0.5) * bd.a2x - (sd[2] - 0.5) * bd.a3x) * bd.invL[0] + 0.5;
-        double gk[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double nk = floor(sd[k]);
-            double f = sd[k] - nk;
-            int ck = (int)(f * g.nc[k]);
-            c[k] = min(max(ck, 0), g.nc[k] - 1);
-            gk[k] = nk + (double)c[k] / g.nc[k] - 0.5;
-        }
-        double Ox = gk[0] * bd.L[0] + gk[1] * bd.a2x + gk[2] * bd.a3x;
-        double Oy = gk[1] * bd.L[1] + gk[2] * bd.a3y;
-        double Oz = gk[2] * bd.L[2];
-        loc.x = (float)(xd - Ox);
-        loc.y = (float)(yd - Oy);
-        loc.z = (float)(zd - Oz);
-    }
-    key = (uint32_t)((c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0]);
-}
-
 __global__ void k_bin(BoxF b, BoxD bd, GridDev g, OriginTables org, const float *__restrict__ pts, int64_t n,
                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, float4 *__restrict__ local) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,60 +223,86 @@ __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
 
 static int grid1d(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+size_t sort_ws_bytes(int64_t n) {
+    const int64_t nblocks = (n + kSortTile - 1) / kSortTile;
+    const int64_t hist = nblocks * kRadix;
+    return 2 * sizeof(uint32_t) * (size_t)n + sizeof(uint32_t) * (size_t)(2 * hist + 1) + scan_ws_bytes(hist) + 1024;
+}
+
+int radix_sort_cells(uint32_t *keys, uint32_t *vals, int64_t n, int64_t ncell, const float4 *payload, float4 *out_sorted,
+                     uint32_t *out_keys, void *ws, cudaStream_t s) {
+    const int64_t nblocks = (n + kSortTile - 1) / kSortTile;
+    const int64_t nh = nblocks * kRadix;
+    char *w = static_cast<char *>(ws);
+    uint32_t *kB = reinterpret_cast<uint32_t *>(w);
+    uint32_t *vB = kB + n;
+    uint32_t *hist = vB + n;
+    uint32_t *offs = hist + nh;
+    void *scan_ws = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(offs + nh + 1) + 255) & ~uintptr_t(255));
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)ncell) ++bits;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    uint32_t *ck = keys, *cv = vals, *nk = kB, *nv = vB;
+    if (passes == 0) {
+        FGB_CUDA(cudaMemcpyAsync(out_sorted, payload, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        FGB_CUDA(cudaMemcpyAsync(out_keys, keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * kRadixBits;
+        const bool last = pass == passes - 1;
+        {
+            FGB_KSCOPE("k_radix_hist", s);
+            k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, s>>>(ck, n, shift, (int)nblocks, hist);
+        }
+        FGB_TRY(scan_u32_u32_ws(hist, offs, nh, scan_ws, s));
+        {
+            FGB_KSCOPE("k_radix_scatter", s);
+            k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, s>>>(ck, cv, n, shift, (int)nblocks, offs,
+                                                                       last ? out_keys : nk, nv, last ? payload : nullptr,
+                                                                       last ? out_sorted : nullptr);
+        }
+        std::swap(ck, nk);
+        std::swap(cv, nv);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+int launch_cell_start(const uint32_t *skeys, int64_t n, int64_t ncell, uint32_t *start, cudaStream_t s) {
+    if (n == 0) {
+        FGB_KSCOPE("k_fill_u32", s);
+        k_fill_u32<<<grid1d(ncell + 1, 256), 256, 0, s>>>(start, ncell + 1, 0u);
+    } else {
+        FGB_KSCOPE("k_cell_start", s);
+        k_cell_start<<<grid1d(n, 256), 256, 0, s>>>(skeys, n, ncell, start);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
 int bin_points(const BoxHost &box, const GridHost &grid, const OriginTables &org, const float *pts, int64_t n,
                float4 *sorted, uint32_t *sorted_cell, uint32_t *cell_start, cudaStream_t s) {
-    if (n == 0) {
-        k_fill_u32<<<grid1d(grid.ncell + 1, 256), 256, 0, s>>>(cell_start, grid.ncell + 1, 0u);
-        FGB_LAUNCH_CHECK();
-        return FGB_OK;
-    }
+    if (n == 0) return launch_cell_start(nullptr, 0, grid.ncell, cell_start, s);
     GridDev g = {{grid.nc[0], grid.nc[1], grid.nc[2]}};
-    uint32_t *kA = nullptr, *kB = nullptr, *vA = nullptr, *vB = nullptr, *hist = nullptr, *offs = nullptr;
+    uint32_t *keys = nullptr, *vals = nullptr;
     float4 *local = nullptr;
-    const int64_t nblocks = (n + kSortTile - 1) / kSortTile;
-    int st = FGB_OK;
-    st = st ? st : dalloc_n(&kA, n, s);
-    st = st ? st : dalloc_n(&kB, n, s);
-    st = st ? st : dalloc_n(&vA, n, s);
-    st = st ? st : dalloc_n(&vB, n, s);
+    void *ws = nullptr;
+    int st = dalloc_n(&keys, n, s);
+    st = st ? st : dalloc_n(&vals, n, s);
     st = st ? st : dalloc_n(&local, n, s);
-    st = st ? st : dalloc_n(&hist, nblocks * kRadix, s);
-    st = st ? st : dalloc_n(&offs, nblocks * kRadix + 1, s);
+    st = st ? st : dalloc(&ws, sort_ws_bytes(n), s);
     if (st == FGB_OK) {
-        k_bin<<<grid1d(n, 256), 256, 0, s>>>(box.f, box.d, g, org, pts, n, kA, vA, local);
-        int bits = 0;
-        while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)grid.ncell) ++bits;
-        const int passes = (bits + kRadixBits - 1) / kRadixBits;
-        uint32_t *ck = kA, *cv = vA, *nk = kB, *nv = vB;
-        if (passes == 0) {
-            cudaMemcpyAsync(sorted, local, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
-            cudaMemcpyAsync(sorted_cell, kA, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        {
+            FGB_KSCOPE("k_bin", s);
+            k_bin<<<grid1d(n, 256), 256, 0, s>>>(box.f, box.d, g, org, pts, n, keys, vals, local);
         }
-        for (int pass = 0; pass < passes && st == FGB_OK; ++pass) {
-            const int shift = pass * kRadixBits;
-            const bool last = pass == passes - 1;
-            k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, s>>>(ck, n, shift, (int)nblocks, hist);
-            st = scan_u32_u32(hist, offs, nblocks * kRadix, s);
-            if (st) break;
-            k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, s>>>(ck, cv, n, shift, (int)nblocks, offs,
-                                                                       last ? sorted_cell : nk, nv,
-                                                                       last ? local : nullptr, last ? sorted : nullptr);
-            std::swap(ck, nk);
-            std::swap(cv, nv);
-        }
-        if (st == FGB_OK) {
-            k_cell_start<<<grid1d(n, 256), 256, 0, s>>>(sorted_cell, n, grid.ncell, cell_start);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "binning launch failed: %s", cudaGetErrorString(e));
-        }
+        st = radix_sort_cells(keys, vals, n, grid.ncell, local, sorted, sorted_cell, ws, s);
+        st = st ? st : launch_cell_start(sorted_cell, n, grid.ncell, cell_start, s);
     }
-    dfree(kA, s);
-    dfree(kB, s);
-    dfree(vA, s);
-    dfree(vB, s);
+    dfree(keys, s);
+    dfree(vals, s);
     dfree(local, s);
-    dfree(hist, s);
-    dfree(offs, s);
+    dfree(ws, s);
     return st;
 }
 
@@ -386,8 +336,11 @@ static int build_origin_tables(const BoxHost &box, const GridHost &g, float2 **b
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
     const int total = nx + 2 * ny + 3 * nz;
     FGB_TRY(dalloc_n(buf, total, s));
-    k_origin_tables<<<(total + 255) / 256, 256, 0, s>>>(box.M[0][0], box.M[0][1], box.M[1][1], box.M[0][2], box.M[1][2],
-                                                        box.M[2][2], nx, ny, nz, *buf);
+    {
+        FGB_KSCOPE("k_origin_tables", s);
+        k_origin_tables<<<(total + 255) / 256, 256, 0, s>>>(box.M[0][0], box.M[0][1], box.M[1][1], box.M[0][2], box.M[1][2],
+                                                            box.M[2][2], nx, ny, nz, *buf);
+    }
     FGB_LAUNCH_CHECK();
     org->Tx = *buf;
     org->Txy = *buf + nx;

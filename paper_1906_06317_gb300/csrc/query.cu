@@ -34,10 +34,9 @@ __global__ void k_offset_table(double m00, double m01, double m02, double m11, d
     out[t] = make_float4((float)(m00 * fx + m01 * fy + m02 * fz), (float)(m11 * fy + m12 * fz), (float)(m22 * fz), 0.f);
 }
 
-int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, StencilPlan *p) {
+int plan_stencil_host(const BoxHost &b, const GridHost &g, double R, int s_table_min, StencilPlan *p,
+                      std::vector<float4> *table) {
     memset(p, 0, sizeof(*p));
-    const GridHost &g = nq->grid;
-    const BoxHost &b = nq->box;
     int smax = 0;
     for (int k = 0; k < 3; ++k) {
         int s = (int)std::ceil(R * (1.0 + 0.5 * kCellMargin) / g.wc[k]);
@@ -55,19 +54,23 @@ int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, S
     if (p->mode == 0) {
         for (int k = 0; k < 3; ++k)
             p->ts[k] = std::max(p->s[k], std::min(std::min(s_table_min, kMaxStencil), (g.nc[k] - 1) / 2));
-        const int wx = 2 * p->ts[0] + 1, wy = 2 * p->ts[1] + 1, wz = 2 * p->ts[2] + 1;
-        const int total = wx * wy * wz;
         double offmax = 0;
         for (int r = 0; r < 3; ++r) {
             double e = 0;
             for (int c = 0; c < 3; ++c) e += std::fabs(b.M[r][c]) * p->ts[c] / g.nc[c];
             offmax = std::max(offmax, e);
         }
-        FGB_TRY(dalloc_n(&p->table, total, st));
-        k_offset_table<<<(total + 127) / 128, 128, 0, st>>>(b.M[0][0], b.M[0][1], b.M[0][2], b.M[1][1], b.M[1][2],
-                                                            b.M[2][2], g.nc[0], g.nc[1], g.nc[2], p->ts[0], p->ts[1],
-                                                            p->ts[2], p->table);
-        FGB_LAUNCH_CHECK();
+        if (table) {
+            table->clear();
+            for (int oz = -p->ts[2]; oz <= p->ts[2]; ++oz)
+                for (int oy = -p->ts[1]; oy <= p->ts[1]; ++oy)
+                    for (int ox = -p->ts[0]; ox <= p->ts[0]; ++ox) {
+                        const double fx = (double)ox / g.nc[0], fy = (double)oy / g.nc[1], fz = (double)oz / g.nc[2];
+                        table->push_back(make_float4((float)(b.M[0][0] * fx + b.M[0][1] * fy + b.M[0][2] * fz),
+                                                     (float)(b.M[1][1] * fy + b.M[1][2] * fz), (float)(b.M[2][2] * fz),
+                                                     0.f));
+                    }
+        }
         // error of one displacement component:
         //   local_i, local_j: 2 roundings each of a value <= ext      -> 4 u ext
         //   offset rounded once from FP64 (|off| <= offmax)          -> u offmax
@@ -80,6 +83,24 @@ int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, S
         // reduction with split box vectors (|intermediate| <= 2 Lsum + R), local
         // coordinates as above; doubled for slack.
         p->eps_d = 2.0 * u * (5.0 * g.ext + 8.0 * p->Lsum + 4.0 * R);
+    }
+    return FGB_OK;
+}
+
+int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, StencilPlan *p) {
+    FGB_TRY(plan_stencil_host(nq->box, nq->grid, R, s_table_min, p, nullptr));
+    if (p->mode == 0) {
+        const BoxHost &b = nq->box;
+        const GridHost &g = nq->grid;
+        const int total = (2 * p->ts[0] + 1) * (2 * p->ts[1] + 1) * (2 * p->ts[2] + 1);
+        FGB_TRY(dalloc_n(&p->table, total, st));
+        {
+            FGB_KSCOPE("k_offset_table", st);
+            k_offset_table<<<(total + 127) / 128, 128, 0, st>>>(b.M[0][0], b.M[0][1], b.M[0][2], b.M[1][1], b.M[1][2],
+                                                                b.M[2][2], g.nc[0], g.nc[1], g.nc[2], p->ts[0],
+                                                                p->ts[1], p->ts[2], p->table);
+        }
+        FGB_LAUNCH_CHECK();
     }
     return FGB_OK;
 }
@@ -102,19 +123,19 @@ void band_around(double T, double delta, float *lo, float *hi) {
     *hi = hf;
 }
 
-Stencil to_device(const fgb_nq *nq, const StencilPlan &p) {
+Stencil to_device(const fgb_nq *nq, const StencilPlan &p) { return to_device(nq->box, nq->grid, p, p.table); }
+
+Stencil to_device(const BoxHost &b, const GridHost &g, const StencilPlan &p, const float4 *table) {
     Stencil S;
     memset(&S, 0, sizeof(S));
     for (int k = 0; k < 3; ++k) {
-        S.nc[k] = nq->grid.nc[k];
+        S.nc[k] = g.nc[k];
         S.s[k] = p.s[k];
         S.ts[k] = p.ts[k];
         S.full[k] = p.full[k];
     }
     S.mode = p.mode;
-    S.off = p.table;
-    const BoxHost &b = nq->box;
-    const GridHost &g = nq->grid;
+    S.off = table;
     S.step[0] = make_float3((float)(b.M[0][0] / g.nc[0]), 0.f, 0.f);
     S.step[1] = make_float3((float)(b.M[0][1] / g.nc[1]), (float)(b.M[1][1] / g.nc[1]), 0.f);
     S.step[2] = make_float3((float)(b.M[0][2] / g.nc[2]), (float)(b.M[1][2] / g.nc[2]), (float)(b.M[2][2] / g.nc[2]));

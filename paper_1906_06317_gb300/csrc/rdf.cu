@@ -47,8 +47,7 @@ struct RdfArgs {
     int half;
     int bins;
     int copies;
-    float rmin, invdelta;
-    const float2 *band;  // (bins+1): lo/hi around each edge
+    BinParams P;
     const double *T;
     unsigned long long *hist;
     int2 *esc;
@@ -56,6 +55,24 @@ struct RdfArgs {
     int *esc_count;
     unsigned weight;
 };
+
+BinParams bin_params(int bins, double rmin, double rmax, double G2, const float2 *band, const std::vector<double> &T) {
+    BinParams P;
+    P.bins = bins;
+    const double invd = bins / (rmax - rmin);
+    P.rmin = (float)rmin;
+    P.invdelta = (float)invd;
+    P.rmin_invdelta = (float)(rmin * invd);
+    P.g2h = (float)(0.55 * G2 * invd);
+    P.r2_fast = (float)(16.0 * G2);
+    float lo, hi;
+    band_around(T[bins], G2, &lo, &hi);
+    P.rmax_hi = hi;
+    band_around(T[0], G2, &lo, &hi);
+    P.rmin_lo = lo;
+    P.band = band;
+    return P;
+}
 
 __device__ __forceinline__ int exact_bin(const double *T, int bins, double e) {
     if (!(e >= T[0]) || !(e < T[bins])) return -1;
@@ -85,34 +102,21 @@ __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
         int cx, cy, cz;
         cell_coords(a.qcell[t], a.S.nc, cx, cy, cz);
         const int excl = a.exclude ? i : -1;
-        const float rmax_hi = a.band[a.bins].y;
-        const float rmin_lo = a.band[0].x;
         for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), a.half != 0,
                     [&](int cell, float qx, float qy, float qz, bool center) {
                         uint32_t beg = __ldg(a.cell_start + cell);
                         const uint32_t end = __ldg(a.cell_start + cell + 1);
                         if (a.half && center) beg = max(beg, (uint32_t)t + 1u);
+#pragma unroll 2
                         for (uint32_t p = beg; p < end; ++p) {
                             const float4 c = __ldg(a.pts + p);
                             const float3 d = cand_disp(a.S, a.bf, c, qx, qy, qz);
                             const float r2 = r2_f32(d.x, d.y, d.z);
-                            if (r2 >= rmax_hi || r2 < rmin_lo) continue;
+                            const int b = rdf_bin(a.P, r2);
+                            if (b == -1) continue;
                             const int j = __float_as_int(c.w);
                             if (j == excl) continue;
-                            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-                            int b = (int)((r - a.rmin) * a.invdelta);
-                            b = min(max(b, 0), a.bins - 1);
-                            float2 e0 = __ldg(a.band + b), e1 = __ldg(a.band + b + 1);
-                            if (r2 < e0.x && b > 0) {
-                                --b;
-                                e1 = e0;
-                                e0 = __ldg(a.band + b);
-                            } else if (r2 >= e1.y && b + 1 < a.bins) {
-                                ++b;
-                                e0 = e1;
-                                e1 = __ldg(a.band + b + 1);
-                            }
-                            if (r2 >= e0.y && r2 < e1.x) {
+                            if (b >= 0) {
                                 if (SHARED)
                                     atomicAdd(my + b, 1u);
                                 else
@@ -240,8 +244,11 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
     if (st == FGB_OK && nlist) {
         const float *q_orig = query_points ? query_points : nq->points;
         if (nlist->n_pairs > 0)
-            k_rdf_nlist<<<num_sms() * 8, 256, 0, s>>>(nq->box.d, nlist->qi, nlist->pj, nlist->n_pairs, q_orig,
-                                                      nq->points, r->T, r->bins, r->hist);
+            {
+                FGB_KSCOPE("k_rdf_nlist", s);
+                k_rdf_nlist<<<num_sms() * 8, 256, 0, s>>>(nq->box.d, nlist->qi, nlist->pj, nlist->n_pairs, q_orig,
+                                                          nq->points, r->T, r->bins, r->hist);
+            }
         st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "rdf nlist launch failed");
     } else if (st == FGB_OK && nqq > 0) {
         StencilPlan plan;
@@ -263,8 +270,6 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
             a.half = (Q.self && plan.mode == 0) ? 1 : 0;
             a.weight = a.half ? 2u : 1u;
             a.bins = r->bins;
-            a.rmin = (float)r->r_min;
-            a.invdelta = (float)(r->bins / (r->r_max - r->r_min));
             a.T = r->T;
             a.hist = r->hist;
             a.esc = r->esc;
@@ -274,11 +279,14 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
             const double delta = r2_error_bound(plan, R);
             if (!r->band) st = dalloc_n(&r->band, r->bins + 1, s);
             if (st == FGB_OK && delta != r->band_delta) {
-                k_band<<<(r->bins + 256) / 256, 256, 0, s>>>(r->T, r->bins + 1, delta, r->band);
+                {
+                    FGB_KSCOPE("k_band", s);
+                    k_band<<<(r->bins + 256) / 256, 256, 0, s>>>(r->T, r->bins + 1, delta, r->band);
+                }
                 r->band_delta = delta;
             }
             if (st == FGB_OK) {
-                a.band = r->band;
+                a.P = bin_params(r->bins, r->r_min, r->r_max, delta, r->band, r->T_host);
                 const int block = 256;
                 int copies = 4;
                 while (copies > 1 && (size_t)copies * r->bins * 4 > 32 * 1024) copies >>= 1;
@@ -286,10 +294,19 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                 a.copies = copies;
                 const unsigned grid = (unsigned)((nqq + block - 1) / block);
                 if (smem <= 48 * 1024)
-                    k_rdf<true><<<grid, block, smem, s>>>(a);
+                    {
+                        FGB_KSCOPE("k_rdf", s);
+                        k_rdf<true><<<grid, block, smem, s>>>(a);
+                    }
                 else
-                    k_rdf<false><<<grid, block, 0, s>>>(a);
-                k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
+                    {
+                        FGB_KSCOPE("k_rdf", s);
+                        k_rdf<false><<<grid, block, 0, s>>>(a);
+                    }
+                {
+                    FGB_KSCOPE("k_rdf_escalated", s);
+                    k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
+                }
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "rdf launch failed: %s", cudaGetErrorString(e));
             }

@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(kThreads) k_down(const TI *__restrict__ in, in
     }
 }
 
+// ws: at least nb * (sizeof(TO) + 4) bytes, nb = ceil(n / kTile); NULL allocates.
 template <class TI, class TO>
-int scan_impl(const TI *in, TO *out, int64_t n, uint32_t *max_out, cudaStream_t s) {
+int scan_impl(const TI *in, TO *out, int64_t n, uint32_t *max_out, void *ws, cudaStream_t s) {
     if (n < 0) return fail(FGB_ERR_INVALID_ARG, "scan: negative length");
     if (n == 0) {
         FGB_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), s));
@@ -142,32 +143,44 @@ int scan_impl(const TI *in, TO *out, int64_t n, uint32_t *max_out, cudaStream_t 
     const int64_t nb = (n + kTile - 1) / kTile;
     TO *partial = nullptr;
     uint32_t *pmax = nullptr;
-    FGB_TRY(dalloc_n(&partial, nb, s));
-    if (max_out) {
-        int st = dalloc_n(&pmax, nb, s);
-        if (st) {
-            dfree(partial, s);
-            return st;
-        }
+    const bool own = ws == nullptr;
+    if (own) {
+        FGB_TRY(dalloc(&ws, nb * (sizeof(TO) + sizeof(uint32_t)) + 256, s));
     }
-    k_reduce<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, pmax);
-    k_top<TO><<<1, kTopThreads, 0, s>>>(partial, nb, out + n, pmax, max_out);
-    k_down<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, out);
+    partial = static_cast<TO *>(ws);
+    if (max_out) pmax = reinterpret_cast<uint32_t *>(partial + nb);
+    {
+        FGB_KSCOPE("k_reduce", s);
+        k_reduce<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, pmax);
+    }
+    {
+        FGB_KSCOPE("k_top", s);
+        k_top<TO><<<1, kTopThreads, 0, s>>>(partial, nb, out + n, pmax, max_out);
+    }
+    {
+        FGB_KSCOPE("k_down", s);
+        k_down<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, out);
+    }
     cudaError_t e = cudaGetLastError();
-    dfree(partial, s);
-    dfree(pmax, s);
+    if (own) dfree(ws, s);
     if (e != cudaSuccess) return fail(FGB_ERR_CUDA, "scan launch failed: %s", cudaGetErrorString(e));
     return FGB_OK;
 }
 
 }  // namespace
 
+size_t scan_ws_bytes(int64_t n) { return (size_t)((n + kTile - 1) / kTile) * 12 + 256; }
+
 int scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, uint32_t *max_out, cudaStream_t s) {
-    return scan_impl<uint32_t, int64_t>(in, out, n, max_out, s);
+    return scan_impl<uint32_t, int64_t>(in, out, n, max_out, nullptr, s);
 }
 
 int scan_u32_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s) {
-    return scan_impl<uint32_t, uint32_t>(in, out, n, nullptr, s);
+    return scan_impl<uint32_t, uint32_t>(in, out, n, nullptr, nullptr, s);
+}
+
+int scan_u32_u32_ws(const uint32_t *in, uint32_t *out, int64_t n, void *ws, cudaStream_t s) {
+    return scan_impl<uint32_t, uint32_t>(in, out, n, nullptr, ws, s);
 }
 
 }  // namespace fgb

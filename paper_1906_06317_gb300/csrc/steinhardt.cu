@@ -14,185 +14,14 @@
 //   d/dz Y~ = (c_lm / c_l,m+1) Abar_l,m+1 w^m,
 // projected on the sphere with (I - u u^T)/|d|, and the gradient at -u is (-1)^(l-1)
 // times the gradient at u.
+// Spherical-harmonic helpers: fgb_ylm.cuh.
 #include <cmath>
 #include <cstring>
 
 #include "fgb_ball.cuh"
+#include "fgb_ylm.cuh"
 
 namespace fgb {
-
-constexpr int kLMax = 12;
-
-struct LegendreConsts {
-    float amm[kLMax + 1];                  // Abar_mm
-    float first[kLMax + 1];                // Abar_{m+1,m} = first[m] z Abar_mm
-    float alpha[kLMax + 1][kLMax + 1];     // Abar_lm = alpha z Abar_{l-1,m} - beta Abar_{l-2,m}
-    float beta[kLMax + 1][kLMax + 1];
-    float gamma[kLMax + 1][kLMax + 2];     // d Abar_lm / dz = gamma Abar_{l,m+1}
-};
-
-__constant__ LegendreConsts c_leg;
-
-static int ensure_consts() {
-    static bool done = false;
-    if (done) return FGB_OK;
-    auto fact = [](int n) {
-        double f = 1;
-        for (int i = 2; i <= n; ++i) f *= i;
-        return f;
-    };
-    auto c = [&](int l, int m) {
-        return ((m & 1) ? -1.0 : 1.0) * std::sqrt((2 * l + 1) / (4.0 * M_PI) * fact(l - m) / fact(l + m));
-    };
-    LegendreConsts h;
-    memset(&h, 0, sizeof(h));
-    for (int m = 0; m <= kLMax; ++m) {
-        double dfact = 1;  // (2m-1)!!
-        for (int k = 2 * m - 1; k > 1; k -= 2) dfact *= k;
-        h.amm[m] = (float)(c(m, m) * dfact);
-        if (m + 1 <= kLMax) h.first[m] = (float)((2 * m + 1) * c(m + 1, m) / c(m, m));
-        for (int l = m + 2; l <= kLMax; ++l) {
-            h.alpha[l][m] = (float)((2.0 * l - 1) / (l - m) * c(l, m) / c(l - 1, m));
-            h.beta[l][m] = (float)((double)(l + m - 1) / (l - m) * c(l, m) / c(l - 2, m));
-        }
-    }
-    for (int l = 0; l <= kLMax; ++l)
-        for (int m = 0; m < l; ++m) h.gamma[l][m] = (float)(c(l, m) / c(l, m + 1));
-    FGB_CUDA(cudaMemcpyToSymbol(c_leg, &h, sizeof(h)));
-    done = true;
-    return FGB_OK;
-}
-
-// Abar_Lm(z) for m = 0..L (A[L+1] = 0 for the derivative).
-template <int L>
-__device__ __forceinline__ void legendre_row(float z, float (&A)[L + 2]) {
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-        float p0 = c_leg.amm[m];
-        if (m == L) {
-            A[m] = p0;
-            continue;
-        }
-        float p1 = c_leg.first[m] * z * p0;
-#pragma unroll
-        for (int l = m + 2; l <= L; ++l) {
-            const float p2 = c_leg.alpha[l][m] * z * p1 - c_leg.beta[l][m] * p0;
-            p0 = p1;
-            p1 = p2;
-        }
-        A[m] = p1;
-    }
-    A[L + 1] = 0.f;
-}
-
-template <int L>
-__device__ __forceinline__ void powers(float x, float y, float (&wr)[L + 1], float (&wi)[L + 1]) {
-    wr[0] = 1.f;
-    wi[0] = 0.f;
-#pragma unroll
-    for (int m = 1; m <= L; ++m) {
-        wr[m] = wr[m - 1] * x - wi[m - 1] * y;
-        wi[m] = wr[m - 1] * y + wi[m - 1] * x;
-    }
-}
-
-template <int L>
-__device__ __forceinline__ void accumulate_bond(float3 d, float (&sr)[L + 1], float (&si)[L + 1]) {
-    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-    if (!(r2 > 0.f)) return;  // coincident points have no bond direction
-    const float inv = rsqrtf(r2);
-    float A[L + 2], wr[L + 1], wi[L + 1];
-    legendre_row<L>(d.z * inv, A);
-    powers<L>(d.x * inv, d.y * inv, wr, wi);
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-        sr[m] += A[m] * wr[m];
-        si[m] += A[m] * wi[m];
-    }
-}
-
-// Raw gradient of Re sum_m f_m conj(Q_m) Y~_m at u (before projection), f_0 = 1, f_m = 2.
-template <int L>
-__device__ __forceinline__ float3 contract_grad(const float (&A)[L + 2], const float (&wr)[L + 1],
-                                                const float (&wi)[L + 1], const float2 *Q) {
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-        const float2 q = Q[m];
-        const float f = m == 0 ? 1.f : 2.f;
-        if (m > 0) {
-            const float am = A[m] * (float)m;
-            const float pr = wr[m - 1], pi = wi[m - 1];
-            gx += f * am * (q.x * pr + q.y * pi);
-            gy += f * am * (q.y * pr - q.x * pi);
-        }
-        if (m < L) {
-            const float g = c_leg.gamma[L][m] * A[m + 1];
-            gz += f * g * (q.x * wr[m] + q.y * wi[m]);
-        }
-    }
-    return make_float3(gx, gy, gz);
-}
-
-// (I - u u^T) g / r
-__device__ __forceinline__ float3 project(float3 g, float3 u, float inv_r) {
-    const float ug = u.x * g.x + u.y * g.y + u.z * g.z;
-    return make_float3((g.x - ug * u.x) * inv_r, (g.y - ug * u.y) * inv_r, (g.z - ug * u.z) * inv_r);
-}
-
-// Bond vector x_j - x_i under the minimum image in FP32.  When no image shift is needed
-// the plain difference is already accurate (|d| is a bond length); otherwise the
-// difference and the shifts are carried as hi + lo pairs so the large intermediate
-// values lose nothing.
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void ds_sub_shift(float &h, float &l, float n, float ahi, float alo) {
-    float s, e;
-    // n is a small integer: n * ahi is formed exactly through its error term
-    const float p = __fmul_rn(n, ahi);
-    const float pe = __fmaf_rn(n, ahi, -p);
-    two_sum_f(h, -p, s, e);
-    h = s;
-    l = __fadd_rn(l, __fsub_rn(__fsub_rn(e, pe), __fmul_rn(n, alo)));
-}
-
-__device__ __forceinline__ float3 bond_f32(const BoxF &b, const float *x, int64_t i, int64_t j) {
-    const float xi0 = __ldg(x + 3 * i), xi1 = __ldg(x + 3 * i + 1), xi2 = __ldg(x + 3 * i + 2);
-    const float xj0 = __ldg(x + 3 * j), xj1 = __ldg(x + 3 * j + 1), xj2 = __ldg(x + 3 * j + 2);
-    float3 d = make_float3(xj0 - xi0, xj1 - xi1, xj2 - xi2);
-    const float nz = rintf(d.z * b.invL[2]);
-    const float ny = rintf((d.y - nz * b.a3y) * b.invL[1]);
-    const float nx = rintf((d.x - nz * b.a3x - ny * b.a2x) * b.invL[0]);
-    if (nz == 0.f && ny == 0.f && nx == 0.f) return d;
-    float hx, lx, hy, ly, hz, lz;
-    two_sum_f(xj0, -xi0, hx, lx);
-    two_sum_f(xj1, -xi1, hy, ly);
-    two_sum_f(xj2, -xi2, hz, lz);
-    ds_sub_shift(hx, lx, nz, b.a3x_hi, b.a3x_lo);
-    ds_sub_shift(hy, ly, nz, b.a3y_hi, b.a3y_lo);
-    ds_sub_shift(hz, lz, nz, b.Lhi[2], b.Llo[2]);
-    ds_sub_shift(hx, lx, ny, b.a2x_hi, b.a2x_lo);
-    ds_sub_shift(hy, ly, ny, b.Lhi[1], b.Llo[1]);
-    ds_sub_shift(hx, lx, nx, b.Lhi[0], b.Llo[0]);
-    return make_float3(hx + lx, hy + ly, hz + lz);
-}
-
-template <int L>
-__device__ __forceinline__ void finish(int64_t i, int n, const float (&sr)[L + 1], const float (&si)[L + 1], float *q,
-                                       float2 *Q, int32_t *nn) {
-    float s = sr[0] * sr[0] + si[0] * si[0];
-#pragma unroll
-    for (int m = 1; m <= L; ++m) s += 2.f * (sr[m] * sr[m] + si[m] * si[m]);
-    const float invn = n > 0 ? 1.f / (float)n : 0.f;
-    q[i] = n > 0 ? sqrtf(4.f * (float)M_PI / (2 * L + 1) * s) * invn : 0.f;
-#pragma unroll
-    for (int m = 0; m <= L; ++m) Q[i * (L + 1) + m] = make_float2(sr[m] * invn, si[m] * invn);
-    nn[i] = n;
-}
 
 // Forward pass over a NeighborList: one thread per query particle.
 template <int L>
@@ -301,22 +130,34 @@ template <int L>
 struct StLaunch {
     static void nlist(const BoxF &b, const float *x, const fgb_nlist *nl, float *q, float2 *Q, int32_t *nn,
                       cudaStream_t s) {
-        k_st_nlist<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(b, x, nl->segments, nl->pj, nl->n_query, q,
-                                                                           Q, nn);
+        {
+            FGB_KSCOPE("k_st_nlist", s);
+            k_st_nlist<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(b, x, nl->segments, nl->pj, nl->n_query, q,
+                                                                               Q, nn);
+        }
     }
     static void fused(const BallArgs &a, float *q, float2 *Q, int32_t *nn, cudaStream_t s) {
-        k_st_fused<L><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a, q, Q, nn);
+        {
+            FGB_KSCOPE("k_st_fused", s);
+            k_st_fused<L><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a, q, Q, nn);
+        }
     }
     static void bwd(const BoxF &b, const float *x, const fgb_nlist *nl, const float *q, const float2 *Q,
                     const int32_t *nn, float scale, float *grad, cudaStream_t s) {
         if (nl->symmetric) {
-            k_st_bwd_gather<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(
-                b, x, nl->segments, nl->pj, nl->n_query, q, Q, nn, scale, reinterpret_cast<float3 *>(grad));
+            {
+                FGB_KSCOPE("k_st_bwd_gather", s);
+                k_st_bwd_gather<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(
+                    b, x, nl->segments, nl->pj, nl->n_query, q, Q, nn, scale, reinterpret_cast<float3 *>(grad));
+            }
         } else {
             cudaMemsetAsync(grad, 0, sizeof(float) * 3 * nl->n_points, s);
             if (nl->n_pairs > 0)
-                k_st_bwd_scatter<L><<<(unsigned)((nl->n_pairs + 127) / 128), 128, 0, s>>>(b, x, nl->qi, nl->pj, nl->n_pairs,
-                                                                                        q, Q, nn, scale, grad);
+                {
+                    FGB_KSCOPE("k_st_bwd_scatter", s);
+                    k_st_bwd_scatter<L><<<(unsigned)((nl->n_pairs + 127) / 128), 128, 0, s>>>(b, x, nl->qi, nl->pj, nl->n_pairs,
+                                                                                            q, Q, nn, scale, grad);
+                }
         }
     }
 };

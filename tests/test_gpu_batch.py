@@ -1,0 +1,81 @@
+"""Batched frames (one persistent launch, CUDA-graph replay, autotuner) against the
+oracle frame by frame: RDF counts bit-exact, q_l within 1e-5 * max(q, 1e-2)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fgb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_06317_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def frames():
+    fr = W.c5(seed=11, n_frames=10, n_lo=600, n_hi=5000)
+    P = W.C5_PARAMS
+    refs = []
+    for f in fr:
+        counts = oracle.rdf_counts(f.box, f.points, P["rdf_bins"], P["rdf_r_max"])
+        _, off, pj, _ = oracle.ball_query(f.box, f.points, P["r_max"])
+        q = oracle.steinhardt(f.box, f.points, off, pj, P["l"])
+        refs.append((counts, q, np.diff(off)))
+    return fr, refs
+
+
+def check(b, fr, refs):
+    counts, q, nn = (t.cpu().numpy() for t in b.outputs())
+    off = b.offsets
+    for k, (c_ref, q_ref, nn_ref) in enumerate(refs):
+        assert np.array_equal(counts[k].astype(np.uint64), c_ref), f"frame {k} RDF counts"
+        qk = q[off[k]:off[k + 1]]
+        assert np.all(np.abs(qk - q_ref) <= 1e-5 * np.maximum(q_ref, 1e-2)), f"frame {k} q6"
+        assert np.array_equal(nn[off[k]:off[k + 1]], nn_ref)
+
+
+@pytest.mark.parametrize("cell_div,block,copies", [(1, 128, 2), (2, 64, 1), (1, 256, 4)])
+def test_batch_matches_oracle(fgb, frames, cell_div, block, copies):
+    fr, refs = frames
+    P = W.C5_PARAMS
+    pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
+    b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
+                  rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"], cell_div=cell_div, block=block,
+                  hist_copies=copies)
+    b.run(pts)
+    torch.cuda.synchronize()
+    check(b, fr, refs)
+
+
+def test_batch_graph_replay_and_tune(fgb, frames):
+    fr, refs = frames
+    P = W.C5_PARAMS
+    pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
+    b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
+                  rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"])
+    chosen = b.tune(pts)
+    assert chosen["cell_div"] in (1, 2) and chosen["block"] in (64, 128, 256)
+    for _ in range(3):
+        b.run(pts, graph=True)
+    torch.cuda.synchronize()
+    check(b, fr, refs)
+    # a new points buffer with the same contents recaptures and gives the same answer
+    pts2 = pts.clone()
+    b.run(pts2, graph=True)
+    torch.cuda.synchronize()
+    check(b, fr, refs)
+
+
+def test_batch_rejects_small_boxes(fgb):
+    box = W.Box.cube(5.0)
+    with pytest.raises(fgb.FGBError) as e:
+        fgb.Batch([10], [box], r_max=1.5, rdf_r_max=3.0)
+    assert e.value.code == fgb.ERR_BOX_TOO_SMALL
