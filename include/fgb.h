@@ -191,6 +191,29 @@ int fgb_rdf_counts_device(const fgb_rdf *rdf, const uint64_t **counts);
 /* Number of pairs re-decided in FP64 by the last compute (synchronises `stream`). */
 int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
 
+/*
+ * Allocation-free RDF of one frame (self query, exclude_ii), for callers that cannot
+ * allocate device memory while they run: work recorded into a CUDA graph by a framework
+ * that forbids allocation nodes, a simulation engine analysing inside its time step
+ * with a fixed memory budget, a runtime whose memory pool owns the device.  The paper
+ * has no counterpart; it is the same computation as fgb_rdf_compute with reset != 0
+ * and no NeighborList.
+ *   points: device float32 (n, 3); counts: device uint64 (bins), overwritten with the
+ *   ordered-pair counts of bins [r_min + b (r_max - r_min)/bins, ...).
+ * Limits: n <= 262144 points, bins <= 8192 (FGB_ERR_CAPACITY beyond), and the
+ * FGB_ERR_BOX_TOO_SMALL / FGB_ERR_INVALID_ARG rules of the other RDF calls.
+ * All working memory (cell list, sort buffers, thresholds, band-pair list; about 24 MB)
+ * is one static device array of the library, held by every GPU that loads it until the
+ * process exits.  The first call on a device looks up that array's device address, so
+ * make the first call on each device before any stream capture.  Every call shares the
+ * array and leaves its contents behind (each call clears what must start at zero):
+ * calls whose work overlaps on the GPU (different streams, other threads) race and must
+ * be serialised by the caller.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.
+ */
+int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t n, int32_t bins, double r_max, double r_min,
+                    uint64_t *counts, void *stream);
+
 /* ----------------------------------------------------------------- Steinhardt */
 
 /*

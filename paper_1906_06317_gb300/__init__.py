@@ -80,6 +80,7 @@ _SIGS = {
     "fgb_rdf_result": (_I32, [_P, _P, _P, _P, _P]),
     "fgb_rdf_counts_device": (_I32, [_P, _PP]),
     "fgb_rdf_escalations": (_I32, [_P, ctypes.POINTER(_I64), _P]),
+    "fgb_rdf_noalloc": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _I32, _D, _D, _P, _P]),
     "fgb_steinhardt_create": (_I32, [_I32, _PP]),
     "fgb_steinhardt_destroy": (None, [_P]),
     "fgb_steinhardt_compute": (_I32, [_P, _P, _P, ctypes.POINTER(fgb_query_args), _P, _P]),

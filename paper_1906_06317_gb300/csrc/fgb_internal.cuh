@@ -198,5 +198,12 @@ size_t sort_ws_bytes(int64_t n);
 int radix_sort_cells(uint32_t *keys, uint32_t *vals, int64_t n, int64_t ncell, const float4 *payload, float4 *out_sorted,
                      uint32_t *out_keys, void *ws, cudaStream_t s);
 int launch_cell_start(const uint32_t *skeys, int64_t n, int64_t ncell, uint32_t *start, cudaStream_t s);
+// Cell-list build into caller buffers (origin tables, sorted records, keys, starts,
+// radix workspace); launches only, no allocation.
+int bin_points_into(const BoxHost &box, const GridHost &grid, const float *pts, int64_t n, float2 *origin_buf,
+                    OriginTables *org, float4 *sorted, uint32_t *sorted_cell, uint32_t *cell_start, uint32_t *keys,
+                    uint32_t *vals, float4 *local, void *sort_ws, cudaStream_t s);
+// Mode-0 offset table of a plan into a caller buffer.
+int launch_offset_table(const BoxHost &b, const GridHost &g, const StencilPlan &p, float4 *table, cudaStream_t st);
 
 }  // namespace fgb

@@ -351,6 +351,32 @@ static int build_origin_tables(const BoxHost &box, const GridHost &g, float2 **b
     return FGB_OK;
 }
 
+int bin_points_into(const BoxHost &box, const GridHost &grid, const float *pts, int64_t n, float2 *origin_buf,
+                    OriginTables *org, float4 *sorted, uint32_t *sorted_cell, uint32_t *cell_start, uint32_t *keys,
+                    uint32_t *vals, float4 *local, void *sort_ws, cudaStream_t s) {
+    const int nx = grid.nc[0], ny = grid.nc[1], nz = grid.nc[2];
+    const int total = nx + 2 * ny + 3 * nz;
+    {
+        FGB_KSCOPE("k_origin_tables", s);
+        k_origin_tables<<<(total + 255) / 256, 256, 0, s>>>(box.M[0][0], box.M[0][1], box.M[1][1], box.M[0][2],
+                                                            box.M[1][2], box.M[2][2], nx, ny, nz, origin_buf);
+    }
+    org->Tx = origin_buf;
+    org->Txy = origin_buf + nx;
+    org->Ty = origin_buf + nx + ny;
+    org->Txz = origin_buf + nx + 2 * ny;
+    org->Tyz = origin_buf + nx + 2 * ny + nz;
+    org->Tz = origin_buf + nx + 2 * ny + 2 * nz;
+    if (n == 0) return launch_cell_start(nullptr, 0, grid.ncell, cell_start, s);
+    GridDev g = {{nx, ny, nz}};
+    {
+        FGB_KSCOPE("k_bin", s);
+        k_bin<<<grid1d(n, 256), 256, 0, s>>>(box.f, box.d, g, *org, pts, n, keys, vals, local);
+    }
+    FGB_TRY(radix_sort_cells(keys, vals, n, grid.ncell, local, sorted, sorted_cell, sort_ws, s));
+    return launch_cell_start(sorted_cell, n, grid.ncell, cell_start, s);
+}
+
 int prepare_queries(fgb_nq *nq, const float *qpts, int64_t n_query, cudaStream_t s, QueryPoints *q) {
     memset(q, 0, sizeof(*q));
     if (qpts == nullptr || qpts == nq->points) {

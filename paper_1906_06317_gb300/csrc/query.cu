@@ -105,6 +105,18 @@ int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, S
     return FGB_OK;
 }
 
+int launch_offset_table(const BoxHost &b, const GridHost &g, const StencilPlan &p, float4 *table, cudaStream_t st) {
+    const int total = (2 * p.ts[0] + 1) * (2 * p.ts[1] + 1) * (2 * p.ts[2] + 1);
+    {
+        FGB_KSCOPE("k_offset_table", st);
+        k_offset_table<<<(total + 127) / 128, 128, 0, st>>>(b.M[0][0], b.M[0][1], b.M[0][2], b.M[1][1], b.M[1][2],
+                                                            b.M[2][2], g.nc[0], g.nc[1], g.nc[2], p.ts[0], p.ts[1],
+                                                            p.ts[2], table);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
 double r2_error_bound(const StencilPlan &p, double R) {
     const double u = std::ldexp(1.0, -24);
     const double e = p.eps_d;

@@ -11,6 +11,7 @@
 // and binned by a second kernel with the defining FP64 sequence.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fgb_device.cuh"
 
@@ -353,5 +354,194 @@ extern "C" int fgb_rdf_escalations(fgb_rdf *r, int64_t *n, void *stream) {
         FGB_CUDA(cudaStreamSynchronize(as_stream(stream)));
     }
     *n = v;
+    return FGB_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free RDF
+//
+// fgb_rdf_noalloc serves callers that must not allocate device memory while they run:
+// code recorded into a CUDA graph by a host framework that forbids allocation nodes,
+// simulation engines that call analysis from inside their time step with a fixed
+// memory budget, or runtimes whose own pool owns the device and treats an outside
+// cudaMalloc (which may synchronise the device) as an error.  Its whole working set
+// lives in the fixed array below; the caller passes the points and the output only.
+
+namespace fgb {
+namespace noalloc {
+
+constexpr int64_t kMaxPoints = 262144;
+constexpr int kMaxBins = 8192;
+constexpr int64_t kMaxCells = 4 * kMaxPoints + 64;  // grid_for keeps ncell <= 4 n + 64
+constexpr int kMaxOrigin = 6 * 1024;
+constexpr int kMaxOffsets = (2 * kMaxStencil + 1) * (2 * kMaxStencil + 1) * (2 * kMaxStencil + 1);
+constexpr int64_t kEscCap = 2 * kMaxPoints;
+
+constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kSortTileN = 4096;
+constexpr size_t kSortWs = 2 * 4 * kMaxPoints + 4 * (2 * ((kMaxPoints + kSortTileN - 1) / kSortTileN) * 256 + 1) +
+                           (((2 * ((kMaxPoints + kSortTileN - 1) / kSortTileN) * 256) + 4095) / 4096) * 12 + 256 +
+                           1024 + 512;
+constexpr size_t oOrigin = 0;
+constexpr size_t oOffsets = oOrigin + al(sizeof(float2) * kMaxOrigin);
+constexpr size_t oKeys = oOffsets + al(sizeof(float4) * kMaxOffsets);
+constexpr size_t oVals = oKeys + al(4 * kMaxPoints);
+constexpr size_t oLocal = oVals + al(4 * kMaxPoints);
+constexpr size_t oSorted = oLocal + al(16 * kMaxPoints);
+constexpr size_t oSortedCell = oSorted + al(16 * kMaxPoints);
+constexpr size_t oCellStart = oSortedCell + al(4 * kMaxPoints);
+constexpr size_t oSortWs = oCellStart + al(4 * (kMaxCells + 1));
+constexpr size_t oT = oSortWs + al(kSortWs);
+constexpr size_t oBand = oT + al(sizeof(double) * (kMaxBins + 1));
+constexpr size_t oEsc = oBand + al(sizeof(float2) * (kMaxBins + 1));
+constexpr size_t oEscCount = oEsc + al(sizeof(int2) * kEscCap);
+constexpr size_t kBytes = oEscCount + 256;  // about 24 MB
+
+// File-scope scratch: every GPU that loads the library holds one copy until exit.
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+static void *g_addr[64];
+static std::mutex g_mu;
+
+// Device address of g_scratch on the current device, looked up once per device (the
+// host-side symbol is only a stand-in and must never be handed to a kernel).
+static int scratch(void **out) {
+    int dev = 0;
+    FGB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(FGB_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return fail(FGB_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return FGB_OK;
+}
+
+// Exact r^2 thresholds of the bin edges on the device (same definition as
+// sqrt_threshold: smallest double whose IEEE square root reaches the edge).
+__global__ void k_thresholds(int bins, double rmin, double rmax, double *T) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > bins) return;
+    const double R = b == bins ? rmax : __dadd_rn(rmin, __dmul_rn((double)b, __ddiv_rn(__dsub_rn(rmax, rmin), (double)bins)));
+    double t = 0.0;
+    if (R > 0.0) {
+        t = __dmul_rn(R, R);
+        for (int it = 0; it < 64 && __dsqrt_rn(t) < R; ++it) t = nextafter(t, INFINITY);
+        for (int it = 0; it < 64; ++it) {
+            const double p = nextafter(t, 0.0);
+            if (p >= 0.0 && __dsqrt_rn(p) >= R && p < t)
+                t = p;
+            else
+                break;
+        }
+    }
+    T[b] = t;
+}
+
+}  // namespace noalloc
+}  // namespace fgb
+
+extern "C" int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t n, int32_t bins, double r_max,
+                               double r_min, uint64_t *counts, void *stream) {
+    using namespace fgb::noalloc;
+    clear_error();
+    if (!box || !counts || (n > 0 && !points)) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(FGB_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > kMaxPoints)
+        return fail(FGB_ERR_CAPACITY, "fgb_rdf_noalloc takes at most %lld points (got %lld)", (long long)kMaxPoints,
+                    (long long)n);
+    if (bins <= 0 || bins > kMaxBins) return fail(FGB_ERR_CAPACITY, "fgb_rdf_noalloc takes 1..%d bins", kMaxBins);
+    if (!(r_min >= 0.0) || !(r_max > r_min) || !std::isfinite(r_max))
+        return fail(FGB_ERR_INVALID_ARG, "need 0 <= r_min < r_max");
+    cudaStream_t s = as_stream(stream);
+    BoxHost bh;
+    FGB_TRY(make_box(box, &bh));
+    if (!(r_max < 0.5 * bh.wmin * (1.0 - 1e-5)))
+        return fail(FGB_ERR_BOX_TOO_SMALL, "RDF r_max=%g must be below half the smallest box width (%g)", r_max,
+                    0.5 * bh.wmin);
+    GridHost g;
+    FGB_TRY(grid_for(bh, r_max, n, &g));
+    if (g.ncell > kMaxCells || g.nc[0] + 2 * g.nc[1] + 3 * g.nc[2] > kMaxOrigin)
+        return fail(FGB_ERR_CAPACITY, "cell grid exceeds the fixed scratch");
+    if (sort_ws_bytes(n) > kSortWs) return fail(FGB_ERR_CAPACITY, "sort workspace exceeds the fixed scratch");
+    StencilPlan plan;
+    FGB_TRY(plan_stencil_host(bh, g, r_max, 0, &plan, nullptr));
+    void *base = nullptr;
+    FGB_TRY(scratch(&base));
+    unsigned char *w = static_cast<unsigned char *>(base);
+    float2 *origin = reinterpret_cast<float2 *>(w + oOrigin);
+    float4 *offsets = reinterpret_cast<float4 *>(w + oOffsets);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(w + oKeys);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(w + oVals);
+    float4 *local = reinterpret_cast<float4 *>(w + oLocal);
+    float4 *sorted = reinterpret_cast<float4 *>(w + oSorted);
+    uint32_t *sorted_cell = reinterpret_cast<uint32_t *>(w + oSortedCell);
+    uint32_t *cell_start = reinterpret_cast<uint32_t *>(w + oCellStart);
+    void *sort_ws = w + oSortWs;
+    double *T = reinterpret_cast<double *>(w + oT);
+    float2 *band = reinterpret_cast<float2 *>(w + oBand);
+    int2 *esc = reinterpret_cast<int2 *>(w + oEsc);
+    int *esc_count = reinterpret_cast<int *>(w + oEscCount);
+    // the output and the band-pair counter start at zero on every call
+    FGB_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint64_t) * bins, s));
+    FGB_CUDA(cudaMemsetAsync(esc_count, 0, sizeof(int), s));
+    if (n == 0) return FGB_OK;
+    if (plan.mode == 0) FGB_TRY(launch_offset_table(bh, g, plan, offsets, s));
+    OriginTables org;
+    FGB_TRY(bin_points_into(bh, g, points, n, origin, &org, sorted, sorted_cell, cell_start, keys, vals, local, sort_ws, s));
+    {
+        FGB_KSCOPE("k_thresholds", s);
+        k_thresholds<<<(bins + 256) / 256, 256, 0, s>>>(bins, r_min, r_max, T);
+    }
+    const double G2 = r2_error_bound(plan, r_max);
+    {
+        FGB_KSCOPE("k_band", s);
+        k_band<<<(bins + 256) / 256, 256, 0, s>>>(T, bins + 1, G2, band);
+    }
+    RdfArgs a;
+    memset(&a, 0, sizeof(a));
+    a.S = to_device(bh, g, plan, plan.mode == 0 ? offsets : nullptr);
+    a.bf = bh.f;
+    a.bd = bh.d;
+    a.pts = sorted;
+    a.cell_start = cell_start;
+    a.qs = sorted;
+    a.qcell = sorted_cell;
+    a.nq = n;
+    a.p_orig = points;
+    a.q_orig = points;
+    a.exclude = 1;
+    a.half = plan.mode == 0 ? 1 : 0;
+    a.weight = a.half ? 2u : 1u;
+    a.bins = bins;
+    // the two outer thresholds are recomputed on the host for the range test
+    std::vector<double> Th(bins + 1, 0.0);
+    Th[0] = sqrt_threshold(r_min);
+    Th[bins] = sqrt_threshold(r_max);
+    a.P = bin_params(bins, r_min, r_max, G2, band, Th);
+    a.T = T;
+    a.hist = reinterpret_cast<unsigned long long *>(counts);
+    a.esc = esc;
+    a.esc_cap = (int)kEscCap;
+    a.esc_count = esc_count;
+    int copies = 4;
+    while (copies > 1 && (size_t)copies * bins * 4 > 32 * 1024) copies >>= 1;
+    const size_t smem = (size_t)copies * bins * 4;
+    a.copies = copies;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (smem <= 48 * 1024) {
+        FGB_KSCOPE("k_rdf", s);
+        k_rdf<true><<<grid, 256, smem, s>>>(a);
+    } else {
+        FGB_KSCOPE("k_rdf", s);
+        k_rdf<false><<<grid, 256, 0, s>>>(a);
+    }
+    {
+        FGB_KSCOPE("k_rdf_escalated", s);
+        k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
+    }
+    FGB_LAUNCH_CHECK();
     return FGB_OK;
 }
