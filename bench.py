@@ -42,6 +42,26 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def frame_seed(rank: int) -> int:
+    """Each rank analyses its own independent frame of the workload (weak scaling)."""
+    return 3 + rank
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over all ranks (the step time every rank waits for)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank: int, world: int, step_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (step_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
 
@@ -153,6 +173,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the kNN / Q6 / batch component timings")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=4_194_304,
+                    help="points of the uniform workload (smaller cases are for profiling only)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -168,7 +190,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    w = W.c3(seed=3 + rank)
+    w = W.c3(seed=frame_seed(rank), n=args.points)
     p = w.params
     host = torch.from_numpy(w.points).pin_memory()
     pts = host.to(dev)
@@ -218,17 +240,14 @@ def main():
     fgb.timing_enable(False)
     kern = {}
     for name in ("k_bin", "k_radix_hist", "k_radix_scatter", "k_cell_start", "k_ball_count", "k_ball_write",
-                 "k_reduce", "k_top", "k_down", "k_rdf", "k_rdf_escalated", "k_offset_table", "k_origin_tables",
-                 "k_band"):
+                 "k_ball_write_global", "k_tile_count", "k_tile_write", "k_tile_rdf", "k_reduce", "k_top", "k_down",
+                 "k_rdf", "k_rdf_escalated", "k_offset_table", "k_origin_tables", "k_band"):
         t, n = fgb.timing_read(name)
         if n:
             kern[name] = {"ms_per_step": t / args.steps, "launches_per_step": n / args.steps}
     step_ms = sum(ms) / len(ms)
-    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t_max.item())
-    value = units * world / (step_ms_max * 1e-3)
+    step_ms_max = max_over_ranks(step_ms, dist, dev)
+    value = weak_value(units, world, step_ms_max)
 
     # ---------------- end to end through the public API, host buffers
     e2e_ms = []
@@ -246,7 +265,7 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
         assert got == units
         del nl, x
-    e2e_step = statistics.median(e2e_ms)
+    e2e_step = max_over_ranks(statistics.median(e2e_ms), dist, dev)
 
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()
@@ -257,13 +276,16 @@ def main():
     sm_clock = (clk or {}).get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12   # FP32 lane-instructions per second, T/s
     rdf_unordered = rdf_pairs / 2
+    nl_bytes = (12.0 * nl_pairs + 28.0 * n) / 1e9    # 12 B per stored pair; record, count, offset per query
+    cnt_bytes = 20.0 * n / 1e9                        # sorted record read + count write per query
+    rdf_ops = 10.0 * rdf_unordered / 1e12             # ~10 FP32 operations per unordered pair inside r_max
     roofs = {
-        # 12 B per stored pair + the sorted query read (16 B), counts and offsets (12 B) per query
-        "k_ball_write": ("hbm", (12.0 * nl_pairs + 28.0 * n) / 1e9, "GB/s", hbm),
-        # 16 B sorted point read + 4 B count write per query
-        "k_ball_count": ("hbm", 20.0 * n / 1e9, "GB/s", hbm),
-        # ~10 FP32 operations per unordered pair inside r_max (difference, r^2, bin, compare)
-        "k_rdf": ("alu", 10.0 * rdf_unordered / 1e12, "TOP/s", alu_peak),
+        "k_ball_write": ("hbm", nl_bytes, "GB/s", hbm),
+        "k_tile_write": ("hbm", nl_bytes, "GB/s", hbm),
+        "k_ball_count": ("hbm", cnt_bytes, "GB/s", hbm),
+        "k_tile_count": ("hbm", cnt_bytes, "GB/s", hbm),
+        "k_rdf": ("alu", rdf_ops, "TOP/s", alu_peak),
+        "k_tile_rdf": ("alu", rdf_ops, "TOP/s", alu_peak),
     }
     bound, work, unit, peak = roofs.get(dominant, ("hbm", 0.0, "GB/s", hbm))
     t_dom = kern[dominant]["ms_per_step"] / kern[dominant]["launches_per_step"] * 1e-3
@@ -302,7 +324,7 @@ def main():
                                        "sorted NeighborList + fused RDF 500 bins [0,5]",
                            "nl_pairs": nl_pairs, "rdf_pairs": rdf_pairs, "points_per_rank": n,
                            "l2": "flushed (512 MB write) before every step", "parallelism": f"{world} independent frames"},
-                "e2e": {"value": units * world / (e2e_step * 1e-3), "unit": "pairs/s",
+                "e2e": {"value": weak_value(units, world, e2e_step), "unit": "pairs/s",
                         "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": p["rdf_bins"] * 8},
                 "gpu_launches": int(launches), "roofline": roofline, "kernels": kern, "kernel_rooflines": others,
                 "components": components, "clocks": clk, "cpu_baseline": cpu}
@@ -330,12 +352,14 @@ def timed(fn, stream, flush, reps=5, warm=2):
 
 def extras(fgb, torch, dev, stream, flush):
     comp = {}
-    # kNN k=12 on the same 4M-point workload (its own cell size)
+    # kNN k=12 on the same 4M-point workload; cells about 1.35x the mean 12th-neighbor
+    # distance so one 27-cell stencil covers almost every query
     w = W.c3()
     x = torch.from_numpy(w.points).to(dev)
+    r12 = (3.0 * 13 / (4.0 * math.pi * 0.85)) ** (1.0 / 3.0)
 
     def knn():
-        nq = fgb.NeighborQuery(w.box, x, r_cell=1.6)
+        nq = fgb.NeighborQuery(w.box, x, r_cell=1.35 * r12)
         return nq.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
 
     comp["c3_knn12_ms"] = timed(knn, stream, flush)

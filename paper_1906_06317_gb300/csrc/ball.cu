@@ -1,106 +1,164 @@
 // Ball query (r_max) and the NeighborList handle.  See query.cu for the overview.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fgb_ball.cuh"
 
 namespace fgb {
 
+// FGB_THREAD_KERNELS=1 selects the thread-per-query kernels even where the cell-tile
+// kernels apply (for comparisons).
+bool force_thread_kernels() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_THREAD_KERNELS");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *a, cudaStream_t s, fgb_nlist *nl);
 
+template <int MODE, bool CHECKJ>
 __global__ void __launch_bounds__(128) k_ball_count(BallArgs a, uint32_t *__restrict__ counts) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.nq) return;
     const float4 q = a.qs[t];
     const int i = __float_as_int(q.w);
-    uint32_t cnt = 0;
-    const int nesc = ball_visit(a, q, a.qcell[t], i, [&](int, float3, float, double) { ++cnt; });
-    counts[i] = cnt;
+    int nesc = 0;
+    counts[i] = ball_count_walk<MODE, CHECKJ>(a, q, a.qcell[t], i, nesc);
     if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
 }
 
-// Write pass.  SHARED: each thread appends its query's hits (j, distance bits) to a
-// shared slab laid out [slot][thread], sorts them by j once the walk is done, and the warp
-// then writes each query's segment with coalesced stores.  !SHARED (very large neighbor
-// counts): insertion happens in the output arrays themselves.
-template <bool SHARED>
+// Write pass.  Each thread walks its query again and appends the neighbor indices to a
+// shared slab laid out [slot][thread] (4 bytes per hit keeps occupancy up).  The warp
+// then takes its 32 queries one at a time: up to 64 hits are sorted by a bitonic network
+// across the warp (two keys per lane); longer lists are ranked by counting the smaller
+// indices in the slab column (broadcast reads).  The float32 distance is recomputed from
+// the input coordinates and every segment is stored sorted by point index with
+// coalesced stores.
+template <int MODE>
 __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *__restrict__ seg,
                                                     const uint32_t *__restrict__ counts, int cap,
                                                     int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
                                                     float *__restrict__ d_out) {
-    extern __shared__ uint2 slab[];
+    extern __shared__ uint32_t slab[];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < a.nq;
+    const int B = blockDim.x + 1;  // odd row stride: a column read by 32 lanes hits 32 banks
     int i = -1;
-    uint32_t n = 0, want = 0;
+    uint32_t n = 0;
     int64_t off = 0;
-    if (valid) {
+    if (t < a.nq) {
         const float4 q = a.qs[t];
         i = __float_as_int(q.w);
         off = seg[i];
-        want = counts[i];
-        const uint32_t lim = SHARED ? (uint32_t)cap : want;
-        ball_visit(a, q, a.qcell[t], i, [&](int j, float3, float r2, double e) {
-            if (n >= lim) {
-                atomicExch(a.err, 1);
-                return;
-            }
-            const float dist = e < 0.0 ? sqrtf(r2) : (float)sqrt(e);
-            if (SHARED) {
-                slab[n * blockDim.x + threadIdx.x] = make_uint2((uint32_t)j, __float_as_uint(dist));
-            } else {
-                uint32_t pos = n;
-                while (pos > 0) {
-                    const int pj = pj_out[off + pos - 1];
-                    if (pj < j) break;
-                    pj_out[off + pos] = pj;
-                    d_out[off + pos] = d_out[off + pos - 1];
-                    --pos;
-                }
-                pj_out[off + pos] = j;
-                d_out[off + pos] = dist;
-            }
+        const uint32_t want = counts[i];
+        ball_visit_m<MODE>(a, q, a.qcell[t], i, [&](int j, float3, float, double) {
+            if (n < (uint32_t)cap) slab[n * B + threadIdx.x] = (uint32_t)j;
             ++n;
         });
-        if (SHARED) {
-            // hits arrive as one index-sorted run per stencil cell; a shell sort (gaps
-            // 57, 23, 10, 4, 1) orders them by point index with few moves
-            const int gaps[5] = {57, 23, 10, 4, 1};
-            const int B = blockDim.x, me = threadIdx.x;
-            for (int gi = 0; gi < 5; ++gi) {
-                const int g = gaps[gi];
-                for (int k = g; k < (int)n; ++k) {
-                    const uint2 v = slab[k * B + me];
-                    int m = k;
-                    while (m >= g) {
-                        const uint2 u = slab[(m - g) * B + me];
-                        if ((int)u.x < (int)v.x) break;
-                        slab[m * B + me] = u;
-                        m -= g;
+        if (n != want || n > (uint32_t)cap) atomicExch(a.err, n > (uint32_t)cap ? 1 : 2);
+        n = min(n, (uint32_t)cap);
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t *wslab = slab + (threadIdx.x & ~31);
+    for (int L = 0; L < 32; ++L) {
+        const uint32_t nL = __shfl_sync(0xffffffffu, n, L);
+        if (nL == 0) continue;
+        const int iL = __shfl_sync(0xffffffffu, i, L);
+        const int64_t oL = __shfl_sync(0xffffffffu, off, L);
+        const uint32_t *col = wslab + L;
+        const float xi0 = __ldg(a.q_orig + 3 * (int64_t)iL), xi1 = __ldg(a.q_orig + 3 * (int64_t)iL + 1),
+                    xi2 = __ldg(a.q_orig + 3 * (int64_t)iL + 2);
+        if (nL <= 64) {
+            // bitonic sort of 64 keys, two per lane (elements 2 lane and 2 lane + 1)
+            uint32_t v0 = 2 * lane < (int)nL ? col[(2 * lane) * B] : 0xffffffffu;
+            uint32_t v1 = 2 * lane + 1 < (int)nL ? col[(2 * lane + 1) * B] : 0xffffffffu;
+#pragma unroll
+            for (int k = 2; k <= 64; k <<= 1) {
+                const bool asc = ((2 * lane) & k) == 0;
+#pragma unroll
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    if (jj == 1) {
+                        const uint32_t lo = min(v0, v1), hi = max(v0, v1);
+                        v0 = asc ? lo : hi;
+                        v1 = asc ? hi : lo;
+                    } else {
+                        const int lm = jj >> 1;
+                        const uint32_t p0 = __shfl_xor_sync(0xffffffffu, v0, lm);
+                        const uint32_t p1 = __shfl_xor_sync(0xffffffffu, v1, lm);
+                        const bool takemin = ((lane & lm) == 0) == asc;
+                        v0 = takemin ? min(v0, p0) : max(v0, p0);
+                        v1 = takemin ? min(v1, p1) : max(v1, p1);
                     }
-                    slab[m * B + me] = v;
                 }
             }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t k = 2 * lane + r;
+                const uint32_t j = r ? v1 : v0;
+                if (k < nL) {
+                    const float3 d = bond_f32v(a.bf, xi0, xi1, xi2, __ldg(a.p_orig + 3 * (int64_t)j),
+                                               __ldg(a.p_orig + 3 * (int64_t)j + 1), __ldg(a.p_orig + 3 * (int64_t)j + 2));
+                    __stcs(qi_out + oL + k, iL);
+                    __stcs(pj_out + oL + k, (int32_t)j);
+                    __stcs(d_out + oL + k, sqrtf(r2_f32(d.x, d.y, d.z)));
+                }
+            }
+            continue;
         }
-        if (n != want) atomicExch(a.err, 2);
-    }
-    if (SHARED) {
-        const int lane = threadIdx.x & 31;
-        const int wbase = threadIdx.x & ~31;
-        for (int L = 0; L < 32; ++L) {
-            const int iL = __shfl_sync(0xffffffffu, i, L);
-            const uint32_t nL = __shfl_sync(0xffffffffu, n, L);
-            const int64_t oL = __shfl_sync(0xffffffffu, off, L);
-            for (uint32_t k = lane; k < nL; k += 32) {
-                const uint2 e = slab[k * blockDim.x + wbase + L];
-                qi_out[oL + k] = iL;
-                pj_out[oL + k] = (int32_t)e.x;
-                d_out[oL + k] = __uint_as_float(e.y);
+        for (uint32_t base = 0; base < nL; base += 32) {
+            const uint32_t k = base + lane;
+            const bool act = k < nL;
+            const uint32_t j = act ? col[k * B] : 0u;
+            uint32_t rank = 0;
+            for (uint32_t m = 0; m < nL; ++m) rank += col[m * B] < j ? 1u : 0u;
+            if (act) {
+                const float3 d = bond_f32v(a.bf, xi0, xi1, xi2, __ldg(a.p_orig + 3 * (int64_t)j),
+                                           __ldg(a.p_orig + 3 * (int64_t)j + 1), __ldg(a.p_orig + 3 * (int64_t)j + 2));
+                // streaming stores: the list is not re-read here, keep L2 for the walks
+                __stcs(qi_out + oL + rank, iL);
+                __stcs(pj_out + oL + rank, (int32_t)j);
+                __stcs(d_out + oL + rank, sqrtf(r2_f32(d.x, d.y, d.z)));
             }
         }
-    } else if (valid) {
-        for (uint32_t k = 0; k < n; ++k) qi_out[off + k] = i;
     }
+}
+
+// Write pass for very large neighbor counts: insertion straight into the output arrays.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_ball_write_global(BallArgs a, const int64_t *__restrict__ seg,
+                                                           const uint32_t *__restrict__ counts,
+                                                           int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                           float *__restrict__ d_out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nq) return;
+    const float4 q = a.qs[t];
+    const int i = __float_as_int(q.w);
+    const int64_t off = seg[i];
+    const uint32_t want = counts[i];
+    uint32_t n = 0;
+    ball_visit_m<MODE>(a, q, a.qcell[t], i, [&](int j, float3, float r2, double e) {
+        if (n >= want) {
+            atomicExch(a.err, 1);
+            return;
+        }
+        const float dist = e < 0.0 ? sqrtf(r2) : (float)sqrt(e);
+        uint32_t pos = n;
+        while (pos > 0) {
+            const int pj = pj_out[off + pos - 1];
+            if (pj < j) break;
+            pj_out[off + pos] = pj;
+            d_out[off + pos] = d_out[off + pos - 1];
+            --pos;
+        }
+        pj_out[off + pos] = j;
+        d_out[off + pos] = dist;
+        ++n;
+    });
+    if (n != want) atomicExch(a.err, 2);
+    for (uint32_t k = 0; k < n; ++k) qi_out[off + k] = i;
 }
 
 struct QueryStatus {
@@ -129,6 +187,7 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     a.T = sqrt_threshold(R);
     band_around(a.T, r2_error_bound(plan, R), &a.band.lo, &a.band.hi);
     a.exclude = args->exclude_ii ? 1 : 0;
+    a.self = Q.self ? 1 : 0;
     QueryStatus *dst = nullptr;
     int st = dalloc_n(&dst, 1, s);
     if (st) {
@@ -144,10 +203,23 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->counts, nqq, s);
     st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
     uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
-    if (st == FGB_OK && nqq > 0) {
+    const bool checkj = !Q.self && a.exclude;
+    const bool tile = Q.self && tile_ok(plan) && !force_thread_kernels();
+    if (st == FGB_OK && nqq > 0 && tile) {
+        st = tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
+        st = st ? st : scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
+    } else if (st == FGB_OK && nqq > 0) {
+        const unsigned grid = (unsigned)((nqq + 127) / 128);
         {
             FGB_KSCOPE("k_ball_count", s);
-            k_ball_count<<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, counts);
+            if (a.S.mode == 0 && !checkj)
+                k_ball_count<0, false><<<grid, 128, 0, s>>>(a, counts);
+            else if (a.S.mode == 0)
+                k_ball_count<0, true><<<grid, 128, 0, s>>>(a, counts);
+            else if (!checkj)
+                k_ball_count<1, false><<<grid, 128, 0, s>>>(a, counts);
+            else
+                k_ball_count<1, true><<<grid, 128, 0, s>>>(a, counts);
         }
         st = scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK) {
@@ -168,24 +240,34 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->pj, hs.total, s);
     st = st ? st : dalloc_n(&nl->dist, hs.total, s);
     if (st == FGB_OK && nqq > 0 && hs.total > 0) {
-        int cap = (int)((hs.maxcount + 3) & ~3u);
+        const int cap = (int)((hs.maxcount + 3) & ~3u);
+        if (tile && tile_write_smem(cap) <= 160 * 1024) {
+            st = tile_write(nq, plan, R, a.exclude, a.err, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist, s);
+        } else {
         int block = 128;
-        while (block > 32 && (size_t)cap * block * sizeof(uint2) > 96 * 1024) block >>= 1;
-        const size_t smem = (size_t)cap * block * sizeof(uint2);
+        while (block > 32 && (size_t)cap * (block + 1) * sizeof(uint32_t) > 100 * 1024) block >>= 1;
+        const size_t smem = (size_t)cap * (block + 1) * sizeof(uint32_t);
         const unsigned grid = (unsigned)((nqq + block - 1) / block);
         if (smem <= 200 * 1024) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_ball_write<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            {
+            if (a.S.mode == 0) {
+                if (smem > 48 * 1024)
+                    cudaFuncSetAttribute(k_ball_write<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 FGB_KSCOPE("k_ball_write", s);
-                k_ball_write<true><<<grid, block, smem, s>>>(a, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist);
+                k_ball_write<0><<<grid, block, smem, s>>>(a, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist);
+            } else {
+                if (smem > 48 * 1024)
+                    cudaFuncSetAttribute(k_ball_write<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                FGB_KSCOPE("k_ball_write", s);
+                k_ball_write<1><<<grid, block, smem, s>>>(a, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist);
             }
         } else {
-            {
-                FGB_KSCOPE("k_ball_write", s);
-                k_ball_write<false><<<(unsigned)((nqq + 127) / 128), 128, 0, s>>>(a, nl->segments, counts, 0, nl->qi,
-                                                                                 nl->pj, nl->dist);
-            }
+            const unsigned g2 = (unsigned)((nqq + 127) / 128);
+            FGB_KSCOPE("k_ball_write_global", s);
+            if (a.S.mode == 0)
+                k_ball_write_global<0><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+            else
+                k_ball_write_global<1><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+        }
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "ball query write launch failed: %s", cudaGetErrorString(e));

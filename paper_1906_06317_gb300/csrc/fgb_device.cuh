@@ -69,6 +69,51 @@ __device__ __forceinline__ float3 min_image_f32(const BoxF &b, float3 d) {
     return d;
 }
 
+// Bond vector x_j - x_i under the minimum image in FP32.  When no image shift is needed
+// the plain difference is already accurate (|d| is a bond length); otherwise the
+// difference and the shifts are carried as hi + lo pairs so the large intermediate
+// values lose nothing.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void ds_sub_shift(float &h, float &l, float n, float ahi, float alo) {
+    float s, e;
+    // n is a small integer: n * ahi is formed exactly through its error term
+    const float p = __fmul_rn(n, ahi);
+    const float pe = __fmaf_rn(n, ahi, -p);
+    two_sum_f(h, -p, s, e);
+    h = s;
+    l = __fadd_rn(l, __fsub_rn(__fsub_rn(e, pe), __fmul_rn(n, alo)));
+}
+
+__device__ __forceinline__ float3 bond_f32v(const BoxF &b, float xi0, float xi1, float xi2, float xj0, float xj1,
+                                            float xj2) {
+    float3 d = make_float3(xj0 - xi0, xj1 - xi1, xj2 - xi2);
+    const float nz = rintf(d.z * b.invL[2]);
+    const float ny = rintf((d.y - nz * b.a3y) * b.invL[1]);
+    const float nx = rintf((d.x - nz * b.a3x - ny * b.a2x) * b.invL[0]);
+    if (nz == 0.f && ny == 0.f && nx == 0.f) return d;
+    float hx, lx, hy, ly, hz, lz;
+    two_sum_f(xj0, -xi0, hx, lx);
+    two_sum_f(xj1, -xi1, hy, ly);
+    two_sum_f(xj2, -xi2, hz, lz);
+    ds_sub_shift(hx, lx, nz, b.a3x_hi, b.a3x_lo);
+    ds_sub_shift(hy, ly, nz, b.a3y_hi, b.a3y_lo);
+    ds_sub_shift(hz, lz, nz, b.Lhi[2], b.Llo[2]);
+    ds_sub_shift(hx, lx, ny, b.a2x_hi, b.a2x_lo);
+    ds_sub_shift(hy, ly, ny, b.Lhi[1], b.Llo[1]);
+    ds_sub_shift(hx, lx, nx, b.Lhi[0], b.Llo[0]);
+    return make_float3(hx + lx, hy + ly, hz + lz);
+}
+
+__device__ __forceinline__ float3 bond_f32(const BoxF &b, const float *x, int64_t i, int64_t j) {
+    return bond_f32v(b, __ldg(x + 3 * i), __ldg(x + 3 * i + 1), __ldg(x + 3 * i + 2), __ldg(x + 3 * j),
+                     __ldg(x + 3 * j + 1), __ldg(x + 3 * j + 2));
+}
+
 __device__ __forceinline__ float r2_f32(float dx, float dy, float dz) {
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
@@ -166,7 +211,7 @@ Stencil to_device(const fgb_nq *nq, const StencilPlan &p);
 
 // Bin of one pair for the RDF.  The fast test places x = (r - r_min)/Delta from the FP32
 // r and accepts bin floor(x) when x sits further than e from both edges, with
-//   e = g2h / r + 8u (x + r_min/Delta + 1),
+//   e = g2h / r + 8u (bins + r_min/Delta + 2)  (x < bins + 1 wherever it matters),
 // g2h = 0.55 G2 / Delta bounding the shift of x caused by an r2 error of at most G2
 // (valid once r2 > 16 G2), the 8u term covering rsqrt, the product with 1/Delta and the
 // FP64 edge positions.  Otherwise the FP32 bands around the exact edge thresholds decide,
@@ -174,22 +219,21 @@ Stencil to_device(const fgb_nq *nq, const StencilPlan &p);
 struct BinParams {
     int bins;
     float rmin, invdelta, rmin_invdelta, g2h, r2_fast;  // r2_fast = 16 G2
+    float eps;                                            // 8u (bins + r_min/Delta + 2)
     float rmax_hi, rmin_lo;                               // bands of the outer edges
     const float2 *band;                                   // (bins+1) bands [lo, hi)
 };
 
 // >= 0: the bin; -1: certainly outside [r_min, r_max); -2: decide in FP64.
+// The fast test needs neither 0 <= b nor b < bins: an x just outside [0, bins) lies
+// within e of an edge and fails it.
 __device__ __forceinline__ int rdf_bin(const BinParams &P, float r2) {
     if (r2 >= P.rmax_hi || r2 < P.rmin_lo) return -1;
-    if (r2 > P.r2_fast) {
-        const float inv = rsqrtf(r2);
-        const float x = fmaf(r2 * inv, P.invdelta, -P.rmin_invdelta);
-        const float fb = floorf(x);
-        const float f = x - fb;
-        const float e = fmaf(8.f * kU32, x + P.rmin_invdelta + 1.f, P.g2h * inv);
-        const int b = (int)fb;
-        if (f > e && f < 1.f - e && b >= 0 && b < P.bins) return b;
-    }
+    const float inv = rsqrtf(r2);
+    const float x = fmaf(r2 * inv, P.invdelta, -P.rmin_invdelta);
+    const float fb = floorf(x);
+    const float e = fmaf(P.g2h, inv, P.eps);
+    if (r2 > P.r2_fast && fabsf((x - fb) - 0.5f) < 0.5f - e) return (int)fb;
     const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
     int b = (int)((r - P.rmin) * P.invdelta);
     b = min(max(b, 0), P.bins - 1);

@@ -182,6 +182,15 @@ double r2_error_bound(const StencilPlan &p, double R);
 // FP32 band [lo, hi) around the exact threshold T, widened by `delta` and rounded outward.
 void band_around(double T, double delta, float *lo, float *hi);
 
+// Cell-tile kernels (tile.cu): one warp per query cell, self queries on the shift route.
+bool tile_ok(const StencilPlan &p);
+bool force_thread_kernels();
+int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
+               uint32_t *counts, cudaStream_t s);
+size_t tile_write_smem(int cap);
+int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+               const uint32_t *counts, int cap, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
+
 // RDF bin parameters for an error bound G2 on r^2 (rdf.cu).
 struct BinParams;
 BinParams bin_params(int bins, double rmin, double rmax, double G2, const float2 *band, const std::vector<double> &T);

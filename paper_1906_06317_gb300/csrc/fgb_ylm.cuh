@@ -144,47 +144,6 @@ __device__ __forceinline__ float3 project(float3 g, float3 u, float inv_r) {
     return make_float3((g.x - ug * u.x) * inv_r, (g.y - ug * u.y) * inv_r, (g.z - ug * u.z) * inv_r);
 }
 
-// Bond vector x_j - x_i under the minimum image in FP32.  When no image shift is needed
-// the plain difference is already accurate (|d| is a bond length); otherwise the
-// difference and the shifts are carried as hi + lo pairs so the large intermediate
-// values lose nothing.
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void ds_sub_shift(float &h, float &l, float n, float ahi, float alo) {
-    float s, e;
-    // n is a small integer: n * ahi is formed exactly through its error term
-    const float p = __fmul_rn(n, ahi);
-    const float pe = __fmaf_rn(n, ahi, -p);
-    two_sum_f(h, -p, s, e);
-    h = s;
-    l = __fadd_rn(l, __fsub_rn(__fsub_rn(e, pe), __fmul_rn(n, alo)));
-}
-
-__device__ __forceinline__ float3 bond_f32(const BoxF &b, const float *x, int64_t i, int64_t j) {
-    const float xi0 = __ldg(x + 3 * i), xi1 = __ldg(x + 3 * i + 1), xi2 = __ldg(x + 3 * i + 2);
-    const float xj0 = __ldg(x + 3 * j), xj1 = __ldg(x + 3 * j + 1), xj2 = __ldg(x + 3 * j + 2);
-    float3 d = make_float3(xj0 - xi0, xj1 - xi1, xj2 - xi2);
-    const float nz = rintf(d.z * b.invL[2]);
-    const float ny = rintf((d.y - nz * b.a3y) * b.invL[1]);
-    const float nx = rintf((d.x - nz * b.a3x - ny * b.a2x) * b.invL[0]);
-    if (nz == 0.f && ny == 0.f && nx == 0.f) return d;
-    float hx, lx, hy, ly, hz, lz;
-    two_sum_f(xj0, -xi0, hx, lx);
-    two_sum_f(xj1, -xi1, hy, ly);
-    two_sum_f(xj2, -xi2, hz, lz);
-    ds_sub_shift(hx, lx, nz, b.a3x_hi, b.a3x_lo);
-    ds_sub_shift(hy, ly, nz, b.a3y_hi, b.a3y_lo);
-    ds_sub_shift(hz, lz, nz, b.Lhi[2], b.Llo[2]);
-    ds_sub_shift(hx, lx, ny, b.a2x_hi, b.a2x_lo);
-    ds_sub_shift(hy, ly, ny, b.Lhi[1], b.Llo[1]);
-    ds_sub_shift(hx, lx, nx, b.Lhi[0], b.Llo[0]);
-    return make_float3(hx + lx, hy + ly, hz + lz);
-}
-
 template <int L>
 __device__ __forceinline__ void finish(int64_t i, int n, const float (&sr)[L + 1], const float (&si)[L + 1], float *q,
                                        float2 *Q, int32_t *nn) {

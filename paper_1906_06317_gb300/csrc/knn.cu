@@ -82,6 +82,16 @@ __device__ __forceinline__ void topk_insert(float (&br)[KT], int (&bj)[KT], floa
     }
 }
 
+// a[idx] for a runtime idx without dynamic register indexing (keeps the list in registers)
+template <int KT, class T>
+__device__ __forceinline__ T pick(const T (&v)[KT], int idx) {
+    T out = v[0];
+#pragma unroll
+    for (int q = 1; q < KT; ++q)
+        if (q == idx) out = v[q];
+    return out;
+}
+
 template <int KT>
 __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
             }
         });
         if (all_full) {
-            delta = knn_delta(a, mode, s, m > 0 ? sqrtf(br[min(m, KT) - 1]) : 0.f);
+            delta = knn_delta(a, mode, s, m > 0 ? sqrtf(pick<KT>(br, min(m, KT) - 1)) : 0.f);
             break;
         }
         float rcov = INFINITY;
@@ -128,7 +138,7 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
             if (!S.full[k2]) rcov = fminf(rcov, s * a.wc[k2]);
         rcov *= 0.99999f;
         if (found >= m && m > 0) {
-            const float rk2 = br[m - 1];
+            const float rk2 = pick<KT>(br, m - 1);
             delta = knn_delta(a, mode, s, sqrtf(rk2) + 1e-3f);
             if (rk2 + delta < rcov * rcov) break;
         } else if (m == 0) {
@@ -136,7 +146,8 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
         }
     }
     a.counts[i] = m;
-    if (m > 0 && br[m - 1] + delta >= a.half_wmin2) {
+    const float rm2 = m > 0 ? pick<KT>(br, m - 1) : 0.f;
+    if (m > 0 && rm2 + delta >= a.half_wmin2) {
         atomicOr(a.err, 1);
         return;
     }
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
     if (ambiguous) {
         const int slot = atomicAdd(a.flag_count, 1);
         if (slot < a.flag_cap) {
-            const float thr = br[m - 1] + 2.f * delta;
+            const float thr = rm2 + 2.f * delta;
             a.flags[slot] = make_int4((int)t, s, __float_as_int(thr * 1.0000005f), 0);
         } else {
             atomicOr(a.err, 2);

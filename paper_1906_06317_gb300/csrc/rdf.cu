@@ -13,7 +13,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "fgb_device.cuh"
+#include "fgb_ball.cuh"
 
 struct fgb_rdf {
     int bins;
@@ -66,6 +66,7 @@ BinParams bin_params(int bins, double rmin, double rmax, double G2, const float2
     P.rmin_invdelta = (float)(rmin * invd);
     P.g2h = (float)(0.55 * G2 * invd);
     P.r2_fast = (float)(16.0 * G2);
+    P.eps = (float)(8.0 * std::ldexp(1.0, -24) * (bins + rmin * invd + 2.0));
     float lo, hi;
     band_around(T[bins], G2, &lo, &hi);
     P.rmax_hi = hi;
@@ -88,7 +89,9 @@ __device__ __forceinline__ int exact_bin(const double *T, int bins, double e) {
     return lo;
 }
 
-template <bool SHARED>
+// HALF: self query with the half stencil; the pair (t, t) is never visited, so no index
+// test is needed.  Otherwise a self query skips j == i explicitly.
+template <bool SHARED, int MODE, bool HALF>
 __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
     extern __shared__ uint32_t sh[];  // copies * bins
     if (SHARED) {
@@ -103,20 +106,20 @@ __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
         int cx, cy, cz;
         cell_coords(a.qcell[t], a.S.nc, cx, cy, cz);
         const int excl = a.exclude ? i : -1;
-        for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), a.half != 0,
+        for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), HALF,
                     [&](int cell, float qx, float qy, float qz, bool center) {
                         uint32_t beg = __ldg(a.cell_start + cell);
                         const uint32_t end = __ldg(a.cell_start + cell + 1);
-                        if (a.half && center) beg = max(beg, (uint32_t)t + 1u);
+                        if (HALF && center) beg = max(beg, (uint32_t)t + 1u);
 #pragma unroll 2
                         for (uint32_t p = beg; p < end; ++p) {
                             const float4 c = __ldg(a.pts + p);
-                            const float3 d = cand_disp(a.S, a.bf, c, qx, qy, qz);
+                            const float3 d = cand_disp_m<MODE>(a.bf, c, qx, qy, qz);
                             const float r2 = r2_f32(d.x, d.y, d.z);
                             const int b = rdf_bin(a.P, r2);
                             if (b == -1) continue;
                             const int j = __float_as_int(c.w);
-                            if (j == excl) continue;
+                            if (!HALF && j == excl) continue;
                             if (b >= 0) {
                                 if (SHARED)
                                     atomicAdd(my + b, 1u);
@@ -142,6 +145,17 @@ __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
             if (v) atomicAdd(a.hist + b, (unsigned long long)v * a.weight);
         }
     }
+}
+
+template <bool SHARED>
+static void launch_rdf(const RdfArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
+    FGB_KSCOPE("k_rdf", s);
+    if (a.half)
+        k_rdf<SHARED, 0, true><<<grid, 256, smem, s>>>(a);
+    else if (a.S.mode == 0)
+        k_rdf<SHARED, 0, false><<<grid, 256, smem, s>>>(a);
+    else
+        k_rdf<SHARED, 1, false><<<grid, 256, smem, s>>>(a);
 }
 
 // Band around each exact edge threshold, rounded outward.
@@ -295,15 +309,9 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                 a.copies = copies;
                 const unsigned grid = (unsigned)((nqq + block - 1) / block);
                 if (smem <= 48 * 1024)
-                    {
-                        FGB_KSCOPE("k_rdf", s);
-                        k_rdf<true><<<grid, block, smem, s>>>(a);
-                    }
+                    launch_rdf<true>(a, grid, smem, s);
                 else
-                    {
-                        FGB_KSCOPE("k_rdf", s);
-                        k_rdf<false><<<grid, block, 0, s>>>(a);
-                    }
+                    launch_rdf<false>(a, grid, 0, s);
                 {
                     FGB_KSCOPE("k_rdf_escalated", s);
                     k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
@@ -531,13 +539,10 @@ extern "C" int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t 
     const size_t smem = (size_t)copies * bins * 4;
     a.copies = copies;
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (smem <= 48 * 1024) {
-        FGB_KSCOPE("k_rdf", s);
-        k_rdf<true><<<grid, 256, smem, s>>>(a);
-    } else {
-        FGB_KSCOPE("k_rdf", s);
-        k_rdf<false><<<grid, 256, 0, s>>>(a);
-    }
+    if (smem <= 48 * 1024)
+        launch_rdf<true>(a, grid, smem, s);
+    else
+        launch_rdf<false>(a, grid, 0, s);
     {
         FGB_KSCOPE("k_rdf_escalated", s);
         k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);

@@ -1,0 +1,516 @@
+// Cell-tile kernels: one warp per query cell.
+//
+// The warp lists the stencil cells of its cell A (offset, first point, running count),
+// then walks their concatenated points 32 at a time, one candidate per lane, already
+// shifted into A's frame (cell-local coordinates + the cell's image offset).  For each
+// chunk it loops over the queries of A, whose coordinates are one uniform load, so every
+// lane tests one pair per round with no per-lane trip-count differences; hits are
+// counted or appended.  This is the shift route only (every axis has at least 2s+1 cells
+// and the stencil has at most kTileMaxStencil cells); other cases use the
+// thread-per-query kernels.  (The RDF keeps the thread-per-query kernel: its in-range
+// binning is cheaper there than with lane groups sharing a chunk.)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fgb_ball.cuh"
+
+namespace fgb {
+
+constexpr int kTileMaxStencil = 128;
+constexpr int kTileWarps = 4;     // warps per block
+constexpr int kTileQueries = 8;   // queries per pass of the write kernel
+
+struct TileArgs {
+    int nc[3];
+    int s[3];
+    int ts[3];
+    const float4 *off;        // offset table of half-width ts
+    const float4 *pts;        // sorted records
+    const uint32_t *cell_start;
+    int64_t ncell;
+    const float *p_orig;
+    BoxF bf;
+    BoxD bd;
+    Band band;
+    double T;
+    int exclude;
+    int half;                 // half stencil (self pairs visited once)
+    unsigned long long *esc;
+    int *err;
+};
+
+struct TileStencil {
+    int beg[kTileMaxStencil];
+    int pre[kTileMaxStencil + 1];
+    float4 off[kTileMaxStencil];
+};
+
+// Builds the (half) stencil list of cell A in `ts` (one warp), returns the number of
+// stencil cells; pre[n] holds the total number of candidates.
+__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TileStencil &ts) {
+    const int lane = threadIdx.x & 31;
+    const int wx = 2 * a.s[0] + 1, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
+    const int nfull = wx * wy * wz;
+    const int owx = 2 * a.ts[0] + 1, owy = 2 * a.ts[1] + 1;
+    int n = 0;
+    // offsets in (oz, oy, ox) order; the half stencil keeps (0,0,0) and what follows it
+    const int first = half ? (nfull - 1) / 2 : 0;
+    for (int b = first; b < nfull; b += 32) {
+        const int o = b + lane;
+        int cnt = 0, beg = 0;
+        float4 of = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (o < nfull) {
+            const int ox = o % wx - a.s[0], oy = (o / wx) % wy - a.s[1], oz = o / (wx * wy) - a.s[2];
+            const int xx = wrap_cell(cx + ox, a.nc[0]), yy = wrap_cell(cy + oy, a.nc[1]),
+                      zz = wrap_cell(cz + oz, a.nc[2]);
+            const int cell = (zz * a.nc[1] + yy) * a.nc[0] + xx;
+            beg = (int)__ldg(a.cell_start + cell);
+            cnt = (int)__ldg(a.cell_start + cell + 1) - beg;
+            of = __ldg(a.off + ((oz + a.ts[2]) * owy + (oy + a.ts[1])) * owx + (ox + a.ts[0]));
+        }
+        // inclusive scan of counts across the warp
+        int inc = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += u;
+        }
+        const int base = n ? ts.pre[n] : 0;
+        if (o < nfull) {
+            const int idx = n + lane;
+            ts.beg[idx] = beg;
+            ts.pre[idx] = base + inc - cnt;
+            ts.off[idx] = of;
+        }
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        const int m = min(32, nfull - b);
+        __syncwarp();
+        if (lane == 0) ts.pre[n + m] = base + tot;
+        __syncwarp();
+        n += m;
+    }
+    return n;
+}
+
+// Stencil cell holding candidate k (largest o with pre[o] <= k; empty cells are skipped
+// because the next non-empty cell shares their prefix).
+__device__ __forceinline__ int tile_find(const TileStencil &ts, int n, int k) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ts.pre[mid] <= k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Candidate k of the current chunk: shifted position, index, sorted position, stencil slot.
+struct TileCand {
+    float x, y, z;
+    int j;
+    int p;
+    int o;
+};
+
+__device__ __forceinline__ TileCand tile_load(const TileArgs &a, const TileStencil &ts, int n, int total, int k) {
+    TileCand c;
+    if (k < total) {
+        const int o = tile_find(ts, n, k);
+        const int p = ts.beg[o] + (k - ts.pre[o]);
+        const float4 r = __ldg(a.pts + p);
+        const float4 of = ts.off[o];
+        c.x = r.x + of.x;
+        c.y = r.y + of.y;
+        c.z = r.z + of.z;
+        c.j = __float_as_int(r.w);
+        c.p = p;
+        c.o = o;
+    } else {
+        c.x = c.y = c.z = 1e30f;
+        c.j = -1;
+        c.p = 0x7fffffff;
+        c.o = -1;
+    }
+    return c;
+}
+
+// Lanes hold queries, candidates are broadcast: a query block of nq <= 32 queries of the
+// cell is spread over qpl = next power of two >= nq lanes, and the warp's 32/qpl lane
+// groups take different candidates of the staged chunk in each round.
+struct QLayout {
+    int qpl, G, myq, g;
+};
+
+__device__ __forceinline__ QLayout qlayout(int nq) {
+    QLayout L;
+    L.qpl = 1;
+    while (L.qpl < nq) L.qpl <<= 1;
+    L.G = 32 / L.qpl;
+    const int lane = threadIdx.x & 31;
+    L.myq = lane & (L.qpl - 1);
+    L.g = lane / L.qpl;
+    return L;
+}
+
+constexpr float kFar = 1e30f;
+
+// Stages candidates [base, base + 32) of the stencil list, shifted into the query cell's
+// frame, as float4 (x, y, z, index bits); missing ones are placed far away.
+__device__ __forceinline__ void tile_stage(const TileArgs &a, const TileStencil &ts, int n, int total, int base,
+                                           float4 *stage) {
+    const int lane = threadIdx.x & 31;
+    const TileCand c = tile_load(a, ts, n, total, base + lane);
+    stage[lane] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+    __syncwarp();
+}
+
+// Dispatches a body templated on the number of lane groups G = 32 / qpl (uniform per warp).
+#define FGB_TILE_DISPATCH_G(G_, CALL) \
+    switch (G_) {                     \
+        case 32: CALL(32); break;     \
+        case 16: CALL(16); break;     \
+        case 8: CALL(8); break;       \
+        case 4: CALL(4); break;       \
+        case 2: CALL(2); break;       \
+        default: CALL(1); break;      \
+    }
+
+// ------------------------------------------------------------------ ball-query count
+
+// One staged chunk against the register-held queries: 32/G unrolled rounds, lane group g
+// takes candidate r*G + g.  Pairs inside the FP32 band are only flagged here.
+template <int G>
+__device__ __forceinline__ uint32_t count_chunk(const float4 *sp, float4 Q, float lo, float hi, bool &band) {
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        cnt += r2 < lo ? 1u : 0u;
+        band |= (r2 >= lo) & (r2 < hi);
+    }
+    return cnt;
+}
+
+// The same chunk again for the rare band pairs, decided by the FP64 sequence.
+template <int G>
+__device__ __forceinline__ uint32_t count_chunk_exact(const TileArgs &a, const float4 *sp, float4 Q, int i, int excl,
+                                                      float lo, float hi, int &nesc) {
+    uint32_t cnt = 0;
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        const int j = __float_as_int(c.w);
+        if (r2 >= lo && r2 < hi && j != excl && j >= 0) {
+            ++nesc;
+            cnt += exact_r2_idx(a.bd, a.p_orig, i, a.p_orig, j) < a.T ? 1u : 0u;
+        }
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, uint32_t *__restrict__ counts) {
+    __shared__ TileStencil sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    const int warp = threadIdx.x >> 5;
+    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    TileStencil &ts = sts[warp];
+    float4 *stage = sstage[warp];
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    const float lo = a.band.lo, hi = a.band.hi;
+    int nesc = 0;
+    for (int qb = 0; qb < nA; qb += 32) {
+        const int nq = min(32, nA - qb);
+        const QLayout L = qlayout(nq);
+        const bool qact = L.myq < nq;
+        const float4 Q = qact ? __ldg(a.pts + begA + qb + L.myq) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const int i = __float_as_int(Q.w);
+        const int excl = a.exclude ? i : -1;
+        const float4 *sp = stage + L.g;
+        uint32_t cnt = 0;
+        for (int base = 0; base < total; base += 32) {
+            tile_stage(a, ts, n, total, base, stage);
+            bool band = false;
+#define FGB_CNT(GV) cnt += count_chunk<GV>(sp, Q, lo, hi, band)
+            FGB_TILE_DISPATCH_G(L.G, FGB_CNT)
+#undef FGB_CNT
+            if (__any_sync(0xffffffffu, band)) {
+#define FGB_CNTX(GV) cnt += count_chunk_exact<GV>(a, sp, Q, i, excl, lo, hi, nesc)
+                FGB_TILE_DISPATCH_G(L.G, FGB_CNTX)
+#undef FGB_CNTX
+            }
+            __syncwarp();
+        }
+        for (int o = L.qpl; o < 32; o <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (L.g == 0 && qact) {
+            if (a.exclude && lo > 0.f) --cnt;  // the query itself, found once at distance 0
+            counts[i] = cnt;
+        }
+    }
+    if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
+}
+
+// ------------------------------------------------------------------ ball-query write
+
+// Hits of a block of up to kTileQueries queries are appended as (index, distance) to
+// per-query rows of a warp-private shared slab (a shared counter per row hands out
+// slots), then each row is sorted by index and stored as its query's segment.  Sort keys
+// pack (index << 7 | slot) into 32 bits when indices fit 25 bits and rows 128 slots, so
+// a bitonic network across the warp moves one word per key (2 or 4 keys per lane);
+// otherwise hits are ranked by counting.
+
+template <int KPL>  // keys per lane (2 or 4): sorts 32 * KPL keys
+__device__ __forceinline__ void bitonic_keys(uint32_t (&v)[KPL]) {
+    const int lane = threadIdx.x & 31;
+    constexpr int N = 32 * KPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            if (jj < KPL) {
+                // partners inside the lane: elements e = KPL*lane + r
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const int p = r ^ jj;
+                    if (p > r) {
+                        const bool asc = (((KPL * lane + r) & k) == 0);
+                        const uint32_t lo = min(v[r], v[p]), hi = max(v[r], v[p]);
+                        v[r] = asc ? lo : hi;
+                        v[p] = asc ? hi : lo;
+                    }
+                }
+            } else {
+                const int lm = jj / KPL;
+                const bool lower = (lane & lm) == 0;
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const bool asc = (((KPL * lane + r) & k) == 0);
+                    const uint32_t p = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                    v[r] = (lower == asc) ? min(v[r], p) : max(v[r], p);
+                }
+            }
+        }
+    }
+}
+
+template <int KPL>
+__device__ __forceinline__ void store_sorted_packed(const uint2 *row, uint32_t nL, int iL, int64_t oL,
+                                                    int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                    float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        v[r] = k < nL ? (row[k].x << 7) | k : 0xffffffffu;
+    }
+    bitonic_keys<KPL>(v);
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        if (k < nL) {
+            const uint2 e = row[v[r] & 127u];
+            __stcs(qi_out + oL + k, iL);
+            __stcs(pj_out + oL + k, (int32_t)e.x);
+            __stcs(d_out + oL + k, __uint_as_float(e.y));
+        }
+    }
+}
+
+__device__ __noinline__ void store_ranked(const uint2 *row, uint32_t nL, int iL, int64_t oL, int32_t *qi_out,
+                                          int32_t *pj_out, float *d_out) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t b0 = 0; b0 < nL; b0 += 32) {
+        const uint32_t k = b0 + lane;
+        const bool act = k < nL;
+        const uint2 e = act ? row[k] : make_uint2(0u, 0u);
+        uint32_t rank = 0;
+        for (uint32_t m = 0; m < nL; ++m) rank += row[m].x < e.x ? 1u : 0u;
+        if (act) {
+            __stcs(qi_out + oL + rank, iL);
+            __stcs(pj_out + oL + rank, (int32_t)e.x);
+            __stcs(d_out + oL + rank, __uint_as_float(e.y));
+        }
+    }
+}
+
+__device__ __forceinline__ void sort_store_row(const uint2 *row, uint32_t nL, int iL, int64_t oL, bool packable,
+                                               int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                               float *__restrict__ d_out) {
+    if (packable && nL <= 64)
+        store_sorted_packed<2>(row, nL, iL, oL, qi_out, pj_out, d_out);
+    else if (packable && nL <= 128)
+        store_sorted_packed<4>(row, nL, iL, oL, qi_out, pj_out, d_out);
+    else
+        store_ranked(row, nL, iL, oL, qi_out, pj_out, d_out);
+}
+
+// Certain hits of one staged chunk; pairs inside the FP32 band are only flagged.
+template <int G>
+__device__ __forceinline__ void write_chunk(const float4 *sp, float4 Q, int excl, float lo, float hi, int *rowcnt,
+                                            uint2 *myrow, int cap, bool &band) {
+#pragma unroll 4
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        band |= (r2 >= lo) & (r2 < hi);
+        if (r2 < lo) {
+            const int j = __float_as_int(c.w);
+            if (j != excl) {
+                const int pos = atomicAdd(rowcnt, 1);
+                if (pos < cap) myrow[pos] = make_uint2((uint32_t)j, __float_as_uint(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f));
+            }
+        }
+    }
+}
+
+// The band pairs of one chunk, decided by the FP64 sequence.
+__device__ __noinline__ void write_chunk_exact(const TileArgs &a, const float4 *sp, int G, float4 Q, int excl, float lo,
+                                               float hi, int *rowcnt, uint2 *myrow, int cap) {
+    const int i = __float_as_int(Q.w);
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        const int j = __float_as_int(c.w);
+        if (r2 >= lo && r2 < hi && j != excl && j >= 0 && i >= 0) {
+            const double e = exact_r2_idx(a.bd, a.p_orig, i, a.p_orig, j);
+            if (e < a.T) {
+                const int pos = atomicAdd(rowcnt, 1);
+                if (pos < cap) myrow[pos] = make_uint2((uint32_t)j, __float_as_uint((float)sqrt(e)));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(TileArgs a, const int64_t *__restrict__ seg,
+                                                                   const uint32_t *__restrict__ counts, int cap,
+                                                                   int packable, int32_t *__restrict__ qi_out,
+                                                                   int32_t *__restrict__ pj_out,
+                                                                   float *__restrict__ d_out) {
+    extern __shared__ uint2 tslab[];  // kTileWarps * kTileQueries * cap
+    __shared__ TileStencil sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    TileStencil &ts = sts[warp];
+    float4 *stage = sstage[warp];
+    int *rowlen = srow[warp];
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    const float lo = a.band.lo, hi = a.band.hi;
+    uint2 *slab = tslab + (size_t)warp * kTileQueries * cap;
+    for (int qb = 0; qb < nA; qb += kTileQueries) {
+        const int nq = min(kTileQueries, nA - qb);
+        const QLayout L = qlayout(nq);
+        const bool qact = L.myq < nq;
+        const float4 Q = qact ? __ldg(a.pts + begA + qb + L.myq) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const int excl = a.exclude ? __float_as_int(Q.w) : -1;
+        if (lane < kTileQueries) rowlen[lane] = 0;
+        __syncwarp();
+        uint2 *myrow = slab + L.myq * cap;
+        int *myrc = rowlen + L.myq;
+        const float4 *sp = stage + L.g;
+        for (int base = 0; base < total; base += 32) {
+            tile_stage(a, ts, n, total, base, stage);
+            bool band = false;
+#define FGB_WR(GV) write_chunk<GV>(sp, Q, excl, lo, hi, myrc, myrow, cap, band)
+            FGB_TILE_DISPATCH_G(L.G, FGB_WR)
+#undef FGB_WR
+            if (__any_sync(0xffffffffu, band)) write_chunk_exact(a, sp, L.G, Q, excl, lo, hi, myrc, myrow, cap);
+            __syncwarp();
+        }
+        __syncwarp();
+        for (int q = 0; q < nq; ++q) {
+            const uint32_t nL = (uint32_t)rowlen[q];
+            const int iL = __float_as_int(__ldg(a.pts + begA + qb + q).w);
+            if (lane == 0 && (nL > (uint32_t)cap || nL != counts[iL])) atomicExch(a.err, nL > (uint32_t)cap ? 1 : 2);
+            if (nL == 0 || nL > (uint32_t)cap) continue;
+            sort_store_row(slab + q * cap, nL, iL, seg[iL], packable != 0, qi_out, pj_out, d_out);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+bool tile_ok(const StencilPlan &p) {
+    if (p.mode != 0) return false;
+    const int n = (2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1);
+    return n <= kTileMaxStencil;
+}
+
+TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude) {
+    TileArgs t;
+    memset(&t, 0, sizeof(t));
+    for (int k = 0; k < 3; ++k) {
+        t.nc[k] = nq->grid.nc[k];
+        t.s[k] = p.s[k];
+        t.ts[k] = p.ts[k];
+    }
+    t.off = p.table;
+    t.pts = nq->sorted;
+    t.cell_start = nq->cell_start;
+    t.ncell = nq->grid.ncell;
+    t.p_orig = nq->points;
+    t.bf = nq->box.f;
+    t.bd = nq->box.d;
+    t.T = sqrt_threshold(R);
+    band_around(t.T, r2_error_bound(p, R), &t.band.lo, &t.band.hi);
+    t.exclude = exclude;
+    return t;
+}
+
+int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
+               uint32_t *counts, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, R, exclude);
+    t.esc = esc;
+    t.err = err;
+    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    {
+        FGB_KSCOPE("k_tile_count", s);
+        k_tile_count<<<grid, kTileWarps * 32, 0, s>>>(t, counts);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+size_t tile_write_smem(int cap);
+
+int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+               const uint32_t *counts, int cap, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, R, exclude);
+    t.err = err;
+    const size_t smem = tile_write_smem(cap);
+    if (smem > 160 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tile write: neighbor count too large");
+    // the kernel also holds ~15 KB of static shared memory: always raise the dynamic limit
+    FGB_CUDA(cudaFuncSetAttribute(k_tile_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    {
+        FGB_KSCOPE("k_tile_write", s);
+        const int packable = cap <= 128 && nq->n < ((int64_t)1 << 25);
+        k_tile_write<<<grid, kTileWarps * 32, smem, s>>>(t, seg, counts, cap, packable, qi, pj, dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+size_t tile_write_smem(int cap) { return (size_t)kTileWarps * kTileQueries * cap * sizeof(uint2); }
+
+}  // namespace fgb

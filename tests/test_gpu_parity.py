@@ -402,3 +402,28 @@ def test_full_c2_steinhardt_and_c4_gradient_sampled(fgb):
             fd = (oracle.steinhardt(w4.box, xp, seg4, pj4, 6, which=aff).sum()
                   - oracle.steinhardt(w4.box, xm, seg4, pj4, 6, which=aff).sum()) / (2 * h * n)
             assert abs(fd - g[k, c]) <= G_TOL * np.abs(g).max() + 1e-3 * abs(fd)
+
+
+def test_thread_per_query_kernels_via_env():
+    """Self ball queries default to the cell-tile kernels; FGB_THREAD_KERNELS=1 selects
+    the thread-per-query count and write kernels, which must agree as well."""
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    code = (
+        "import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb\n"
+        "b = W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15)\n"
+        "x = W.small_random(90, 5000, b)\n"
+        "nq = fgb.NeighborQuery(b, torch.from_numpy(x).cuda(), r_cell=2.0)\n"
+        "nl = nq.query(None, dict(r_max=2.0, exclude_ii=True)).toNeighborList()\n"
+        "_, off, pj, d = oracle.ball_query(b, x, 2.0)\n"
+        "assert np.array_equal(nl.segments.cpu().numpy(), off)\n"
+        "assert np.array_equal(nl.point_indices.cpu().numpy(), pj)\n"
+        "assert np.allclose(nl.distances.cpu().numpy(), d, atol=1e-5)\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FGB_THREAD_KERNELS="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
