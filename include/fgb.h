@@ -81,6 +81,12 @@ int32_t fgb_version(void);
  * summed device time (ms) and launch count of kernels named `name` (the __global__
  * function name, e.g. "k_ball_write"); fgb_timing_reset clears the totals. */
 int64_t fgb_kernel_launches(void);
+
+/* Device blocks of 1 MB or more freed by the library (neighbor lists, sort buffers) are
+ * kept, up to 48 GB, and handed to later allocations of a similar size on any stream
+ * (ordered by an event recorded when they were freed).  fgb_trim_memory waits for
+ * their last use and returns them to the device. */
+int fgb_trim_memory(void);
 int fgb_timing_enable(int32_t on);
 int fgb_timing_read(const char *name, double *total_ms, int64_t *count);
 int fgb_timing_reset(void);

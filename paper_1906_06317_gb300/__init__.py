@@ -61,6 +61,7 @@ _SIGS = {
     "fgb_last_error": (ctypes.c_char_p, []),
     "fgb_version": (_I32, []),
     "fgb_kernel_launches": (_I64, []),
+    "fgb_trim_memory": (_I32, []),
     "fgb_timing_enable": (_I32, [_I32]),
     "fgb_timing_read": (_I32, [ctypes.c_char_p, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "fgb_timing_reset": (_I32, []),
@@ -120,6 +121,11 @@ def kernel_launches() -> int:
     return int(lib().fgb_kernel_launches())
 
 
+def trim_memory():
+    """Return the device blocks the library keeps for reuse."""
+    _check(lib().fgb_trim_memory())
+
+
 def timing_enable(on: bool = True):
     _check(lib().fgb_timing_enable(int(bool(on))))
 
@@ -167,6 +173,22 @@ class _DeviceArray:
         self._owner = owner
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": self._TYPES[dtype],
                                          "data": (int(ptr or 0), False), "version": 2, "strides": None}
+
+
+class _Owned:
+    """Owns one library handle; tensor views of its memory keep this object (not the
+    Python wrapper) alive, so wrappers and views never form a reference cycle and a
+    handle is released as soon as the last of them goes."""
+
+    def __init__(self, ptr, destroy, keep=()):
+        self.ptr = ctypes.c_void_p(ptr)
+        self._destroy = destroy
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            getattr(_lib, self._destroy)(self.ptr)
+            self.ptr = None
 
 
 def _view(ptr, shape, dtype, owner) -> torch.Tensor:
@@ -219,19 +241,20 @@ class NeighborList:
     """Query results, sorted by (query index, point index) (ball) or by distance (kNN)."""
 
     def __init__(self, handle, keep):
-        self._h = ctypes.c_void_p(handle)
-        self._keep = keep
+        self._o = _Owned(handle, "fgb_nlist_destroy", keep)
+        self._h = self._o.ptr
         L = lib()
         m, nq = _I64(), _I64()
         _check(L.fgb_nlist_size(self._h, ctypes.byref(m), ctypes.byref(nq)))
         self.n_pairs, self.n_query = m.value, nq.value
         p = [ctypes.c_void_p() for _ in range(5)]
         _check(L.fgb_nlist_arrays(self._h, *[ctypes.byref(x) for x in p]))
-        self.query_point_indices = _view(p[0].value, (self.n_pairs,), torch.int32, self)
-        self.point_indices = _view(p[1].value, (self.n_pairs,), torch.int32, self)
-        self.distances = _view(p[2].value, (self.n_pairs,), torch.float32, self)
-        self.segments = _view(p[3].value, (self.n_query + 1,), torch.int64, self)
-        self.neighbor_counts = _view(p[4].value, (self.n_query,), torch.int32, self)
+        o = self._o
+        self.query_point_indices = _view(p[0].value, (self.n_pairs,), torch.int32, o)
+        self.point_indices = _view(p[1].value, (self.n_pairs,), torch.int32, o)
+        self.distances = _view(p[2].value, (self.n_pairs,), torch.float32, o)
+        self.segments = _view(p[3].value, (self.n_query + 1,), torch.int64, o)
+        self.neighbor_counts = _view(p[4].value, (self.n_query,), torch.int32, o)
         e = _I64()
         _check(L.fgb_nlist_escalations(self._h, ctypes.byref(e)))
         self.escalations = e.value
@@ -250,11 +273,6 @@ class NeighborList:
 
     def __len__(self):
         return self.n_pairs
-
-    def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.fgb_nlist_destroy(self._h)
-            self._h = None
 
 
 class _QueryResult:
@@ -284,7 +302,8 @@ class NeighborQuery:
         b = self.box._c()
         _check(lib().fgb_nq_create(ctypes.byref(b), self.points.data_ptr(), self.points.shape[0], self.r_cell,
                                    _stream(), ctypes.byref(h)))
-        self._h = h
+        self._o = _Owned(h.value, "fgb_nq_destroy", (self.points,))
+        self._h = self._o.ptr
 
     @property
     def n_points(self) -> int:
@@ -302,8 +321,9 @@ class NeighborQuery:
         _check(lib().fgb_nq_cells(self._h, *[ctypes.byref(x) for x in p]))
         nx, ny, nz = self.cell_dims()
         n = self.n_points
-        return (_view(p[0].value, (n, 4), torch.float32, self), _view(p[1].value, (n,), torch.int32, self),
-                _view(p[2].value, (nx * ny * nz + 1,), torch.int32, self))
+        o = self._o
+        return (_view(p[0].value, (n, 4), torch.float32, o), _view(p[1].value, (n,), torch.int32, o),
+                _view(p[2].value, (nx * ny * nz + 1,), torch.int32, o))
 
     def query(self, query_points=None, query_args=None) -> _QueryResult:
         args = dict(query_args or {})
@@ -312,7 +332,7 @@ class NeighborQuery:
     def _run_query(self, query_points, args) -> NeighborList:
         qa = fgb_query_args(float(args.get("r_max", 0.0) or 0.0), int(args.get("num_neighbors", 0) or 0),
                             int(bool(args.get("exclude_ii", query_points is None or query_points is self.points))))
-        keep = [self]
+        keep = [self._o]
         if query_points is None or query_points is self.points:
             qp, nq = None, 0
         else:
@@ -323,10 +343,6 @@ class NeighborQuery:
         _check(lib().fgb_nq_query(self._h, qp, nq, ctypes.byref(qa), _stream(), ctypes.byref(h)))
         return NeighborList(h.value, keep)
 
-    def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.fgb_nq_destroy(self._h)
-            self._h = None
 
 
 def _as_nq(system, r_cell=None) -> NeighborQuery:
@@ -346,7 +362,8 @@ class RDF:
         self.bins, self.r_max, self.r_min = int(bins), float(r_max), float(r_min)
         h = ctypes.c_void_p()
         _check(lib().fgb_rdf_create(self.bins, self.r_max, self.r_min, ctypes.byref(h)))
-        self._h = h
+        self._o = _Owned(h.value, "fgb_rdf_destroy")
+        self._h = self._o.ptr
 
     def compute(self, system, neighbors=None, query_points=None, reset=True):
         nq = _as_nq(system, self.r_max)
@@ -381,17 +398,13 @@ class RDF:
     def counts_device(self) -> torch.Tensor:
         p = ctypes.c_void_p()
         _check(lib().fgb_rdf_counts_device(self._h, ctypes.byref(p)))
-        return _view(p.value, (self.bins,), torch.int64, self)
+        return _view(p.value, (self.bins,), torch.int64, self._o)
 
     def escalations(self) -> int:
         n = _I64()
         _check(lib().fgb_rdf_escalations(self._h, ctypes.byref(n), _stream()))
         return n.value
 
-    def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.fgb_rdf_destroy(self._h)
-            self._h = None
 
 
 # ------------------------------------------------------------------------ Steinhardt
@@ -404,7 +417,8 @@ class Steinhardt:
         self.l = int(l)
         h = ctypes.c_void_p()
         _check(lib().fgb_steinhardt_create(self.l, ctypes.byref(h)))
-        self._h = h
+        self._o = _Owned(h.value, "fgb_steinhardt_destroy")
+        self._h = self._o.ptr
         self.particle_order = None
 
     def compute(self, system, neighbors=None):
@@ -427,12 +441,12 @@ class Steinhardt:
     def qlm(self) -> torch.Tensor:
         p, c = ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().fgb_steinhardt_state(self._h, ctypes.byref(p), ctypes.byref(c)))
-        return torch.view_as_complex(_view(p.value, (self._nq.n_points, self.l + 1, 2), torch.float32, self))
+        return torch.view_as_complex(_view(p.value, (self._nq.n_points, self.l + 1, 2), torch.float32, self._o))
 
     def neighbor_counts(self) -> torch.Tensor:
         p, c = ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().fgb_steinhardt_state(self._h, ctypes.byref(p), ctypes.byref(c)))
-        return _view(c.value, (self._nq.n_points,), torch.int32, self)
+        return _view(c.value, (self._nq.n_points,), torch.int32, self._o)
 
     def backward(self, upstream: float = 1.0) -> torch.Tensor:
         """d(upstream * mean_i q_l(i)) / d positions, neighbor list of the last compute fixed."""
@@ -443,10 +457,6 @@ class Steinhardt:
                                              float(upstream), g.data_ptr(), _stream()))
         return g
 
-    def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.fgb_steinhardt_destroy(self._h)
-            self._h = None
 
 
 class Q6Mean(torch.autograd.Function):
@@ -484,7 +494,8 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib().fgb_batch_create(len(sizes), self.offsets.ctypes.data, bx, ctypes.byref(self.params), _stream(),
                                       ctypes.byref(h)))
-        self._h = h
+        self._o = _Owned(h.value, "fgb_batch_destroy")
+        self._h = self._o.ptr
         self.n_frames, self.rdf_bins = len(sizes), rdf_bins
         self.total = int(self.offsets[-1])
 
@@ -504,10 +515,6 @@ class Batch:
     def outputs(self):
         r, q, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().fgb_batch_outputs(self._h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(n)))
-        return (_view(r.value, (self.n_frames, self.rdf_bins), torch.int64, self),
-                _view(q.value, (self.total,), torch.float32, self), _view(n.value, (self.total,), torch.int32, self))
-
-    def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.fgb_batch_destroy(self._h)
-            self._h = None
+        o = self._o
+        return (_view(r.value, (self.n_frames, self.rdf_bins), torch.int64, o),
+                _view(q.value, (self.total,), torch.float32, o), _view(n.value, (self.total,), torch.int32, o))

@@ -5,6 +5,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "fgb_internal.cuh"
 
@@ -22,9 +23,75 @@ int fail(int code, const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
+// The device's default memory pool returns freed memory to the system at every
+// synchronisation unless told otherwise; then each neighbor list (gigabytes) is mapped
+// again on the next query.  Keep freed blocks cached in this process instead.
+static void keep_pool_cached() {
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+// Large blocks (neighbor lists, sort buffers) are kept for reuse instead of being freed:
+// even from a cached memory pool, mapping a fresh gigabyte-sized block takes about a
+// millisecond per call.  A kept block carries an event recorded on the stream that freed
+// it; the stream that reuses it waits on that event first, so reuse is ordered on any
+// stream.  fgb_trim_memory() releases everything kept.
+namespace {
+constexpr size_t kKeepMin = size_t(1) << 20;
+constexpr size_t kKeepMax = size_t(48) << 30;
+struct Kept {
+    void *p;
+    size_t bytes;
+    int dev;
+    cudaEvent_t done;
+};
+std::mutex g_amu;
+std::vector<Kept> g_kept;
+size_t g_kept_bytes = 0;
+std::unordered_map<void *, size_t> g_sizes;
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
 int dalloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    keep_pool_cached();
     if (bytes == 0) bytes = 16;
+    if (bytes >= kKeepMin && !capturing(s)) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(g_amu);
+        size_t best = SIZE_MAX;
+        int bi = -1;
+        for (size_t k = 0; k < g_kept.size(); ++k) {
+            const Kept &b = g_kept[k];
+            if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes && b.bytes < best) {
+                best = b.bytes;
+                bi = (int)k;
+            }
+        }
+        if (bi >= 0) {
+            Kept b = g_kept[bi];
+            g_kept.erase(g_kept.begin() + bi);
+            g_kept_bytes -= b.bytes;
+            cudaStreamWaitEvent(s, b.done, 0);
+            cudaEventDestroy(b.done);
+            *p = b.p;
+            g_sizes[b.p] = b.bytes;
+            return FGB_OK;
+        }
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -32,11 +99,48 @@ int dalloc(void **p, size_t bytes, cudaStream_t s) {
         return fail(e == cudaErrorMemoryAllocation ? FGB_ERR_OOM : FGB_ERR_CUDA, "device allocation of %zu bytes failed: %s",
                     bytes, cudaGetErrorString(e));
     }
+    if (bytes >= kKeepMin) {
+        std::lock_guard<std::mutex> lk(g_amu);
+        g_sizes[*p] = bytes;
+    }
     return FGB_OK;
 }
 
 void dfree(void *p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_amu);
+        auto it = g_sizes.find(p);
+        if (it != g_sizes.end()) {
+            const size_t bytes = it->second;
+            g_sizes.erase(it);
+            cudaEvent_t ev;
+            if (g_kept_bytes + bytes <= kKeepMax && !capturing(s) &&
+                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+                if (cudaEventRecord(ev, s) == cudaSuccess) {
+                    int dev = 0;
+                    cudaGetDevice(&dev);
+                    g_kept.push_back({p, bytes, dev, ev});
+                    g_kept_bytes += bytes;
+                    return;
+                }
+                cudaEventDestroy(ev);
+            }
+        }
+    }
+    cudaFreeAsync(p, s);
+}
+
+int trim_memory() {
+    std::lock_guard<std::mutex> lk(g_amu);
+    for (Kept &b : g_kept) {
+        cudaEventSynchronize(b.done);
+        cudaEventDestroy(b.done);
+        cudaFree(b.p);
+    }
+    g_kept.clear();
+    g_kept_bytes = 0;
+    return FGB_OK;
 }
 
 int num_sms() {
@@ -105,6 +209,8 @@ static void resolve_timings() {
 }
 
 }  // namespace fgb
+
+extern "C" int fgb_trim_memory(void) { return fgb::trim_memory(); }
 
 extern "C" int64_t fgb_kernel_launches(void) { return fgb::g_launches.load(); }
 

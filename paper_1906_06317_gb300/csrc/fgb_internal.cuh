@@ -188,6 +188,10 @@ bool force_thread_kernels();
 int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
                uint32_t *counts, cudaStream_t s);
 size_t tile_write_smem(int cap);
+// kNN by radius over cell tiles (self queries, 27-cell stencil, m <= 63); queries it
+// cannot settle are appended (sorted positions) to `list`.
+int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, int32_t *qi, int32_t *pj, float *dist,
+             int32_t *counts, int *list, int *list_count, cudaStream_t s);
 int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
                const uint32_t *counts, int cap, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
 

@@ -37,6 +37,8 @@ struct KnnArgs {
     int32_t *qi_out, *pj_out;
     float *d_out;
     int32_t *counts;
+    const int *list;        // when set: only these sorted positions, list_count of them
+    const int *list_count;
 };
 
 // FP32 error bound on r2 at radius R for a walk with half-width s (mode 0) or the
@@ -94,8 +96,13 @@ __device__ __forceinline__ T pick(const T (&v)[KT], int idx) {
 
 template <int KT>
 __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.nq) return;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.list) {
+        if (t >= *a.list_count) return;
+        t = a.list[t];
+    } else if (t >= a.nq) {
+        return;
+    }
     const float4 q = a.qs[t];
     const int i = __float_as_int(q.w);
     int cx, cy, cz;
@@ -319,13 +326,13 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
     a.Lsum = (float)plan.Lsum;
     a.half_wmin2 = (float)(0.25 * b.wmin * b.wmin * (1.0 - 1e-4));
     a.flag_cap = (int)std::min<int64_t>(std::max<int64_t>(nqq, 1), 1 << 24);
-    int *ctl = nullptr;  // [0] flag count, [1] error bits
+    int *ctl = nullptr;  // [0] flag count, [1] error bits, [2] list length, [4..] list
     nl->n_query = nqq;
     nl->n_points = np;
     const int64_t rows = uniform ? nqq * (int64_t)m_uniform : nqq * (int64_t)k;
     int32_t *tqi = nullptr, *tpj = nullptr;
     float *td = nullptr;
-    int st = dalloc_n(&ctl, 2, s);
+    int st = dalloc_n(&ctl, 5 + nqq, s);
     st = st ? st : dalloc_n(&a.flags, a.flag_cap, s);
     st = st ? st : dalloc_n(&nl->counts, nqq, s);
     st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
@@ -333,13 +340,22 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
     st = st ? st : dalloc_n(&tpj, rows, s);
     st = st ? st : dalloc_n(&td, rows, s);
     if (st == FGB_OK) {
-        cudaMemsetAsync(ctl, 0, 2 * sizeof(int), s);
+        cudaMemsetAsync(ctl, 0, 5 * sizeof(int), s);
         a.flag_count = ctl;
         a.err = ctl + 1;
         a.qi_out = tqi;
         a.pj_out = tpj;
         a.d_out = td;
         a.counts = nl->counts;
+        // self queries on the shift route: radius kernel over cell tiles first, the
+        // thread-per-query kernel only for the queries it leaves
+        const bool tile = Q.self && plan.mode == 0 && plan.s[0] == 1 && plan.s[1] == 1 && plan.s[2] == 1 &&
+                          m_uniform >= 1 && m_uniform <= 62 && !force_thread_kernels();
+        if (tile && nqq > 0) {
+            st = tile_knn(nq, plan, k, m_uniform, a.exclude, tqi, tpj, td, nl->counts, ctl + 4, ctl + 2, s);
+            a.list = ctl + 4;
+            a.list_count = ctl + 2;
+        }
         if (nqq > 0) {
             const int KT = k + 1;
             if (KT <= 5) launch_knn<5>(a, s);

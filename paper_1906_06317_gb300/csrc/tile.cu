@@ -40,15 +40,18 @@ struct TileArgs {
     int *err;
 };
 
-struct TileStencil {
-    int beg[kTileMaxStencil];
-    int pre[kTileMaxStencil + 1];
-    float4 off[kTileMaxStencil];
+template <int NS>
+struct TileStencilT {
+    int beg[NS];
+    int pre[NS + 1];
+    float4 off[NS];
 };
+using TileStencil = TileStencilT<kTileMaxStencil>;
 
 // Builds the (half) stencil list of cell A in `ts` (one warp), returns the number of
 // stencil cells; pre[n] holds the total number of candidates.
-__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TileStencil &ts) {
+template <class TS>
+__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TS &ts) {
     const int lane = threadIdx.x & 31;
     const int wx = 2 * a.s[0] + 1, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
     const int nfull = wx * wy * wz;
@@ -95,7 +98,8 @@ __device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, i
 
 // Stencil cell holding candidate k (largest o with pre[o] <= k; empty cells are skipped
 // because the next non-empty cell shares their prefix).
-__device__ __forceinline__ int tile_find(const TileStencil &ts, int n, int k) {
+template <class TS>
+__device__ __forceinline__ int tile_find(const TS &ts, int n, int k) {
     int lo = 0, hi = n;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -115,7 +119,8 @@ struct TileCand {
     int o;
 };
 
-__device__ __forceinline__ TileCand tile_load(const TileArgs &a, const TileStencil &ts, int n, int total, int k) {
+template <class TS>
+__device__ __forceinline__ TileCand tile_load(const TileArgs &a, const TS &ts, int n, int total, int k) {
     TileCand c;
     if (k < total) {
         const int o = tile_find(ts, n, k);
@@ -159,8 +164,8 @@ constexpr float kFar = 1e30f;
 
 // Stages candidates [base, base + 32) of the stencil list, shifted into the query cell's
 // frame, as float4 (x, y, z, index bits); missing ones are placed far away.
-__device__ __forceinline__ void tile_stage(const TileArgs &a, const TileStencil &ts, int n, int total, int base,
-                                           float4 *stage) {
+template <class TS>
+__device__ __forceinline__ void tile_stage(const TileArgs &a, const TS &ts, int n, int total, int base, float4 *stage) {
     const int lane = threadIdx.x & 31;
     const TileCand c = tile_load(a, ts, n, total, base + lane);
     stage[lane] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
@@ -212,8 +217,9 @@ __device__ __forceinline__ uint32_t count_chunk_exact(const TileArgs &a, const f
     return cnt;
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, uint32_t *__restrict__ counts) {
-    __shared__ TileStencil sts[kTileWarps];
+    __shared__ TileStencilT<NS> sts[kTileWarps];
     __shared__ float4 sstage[kTileWarps][32];
     const int warp = threadIdx.x >> 5;
     const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
     if (nA == 0) return;
     int cx, cy, cz;
     cell_coords((uint32_t)A, a.nc, cx, cy, cz);
-    TileStencil &ts = sts[warp];
+    TileStencilT<NS> &ts = sts[warp];
     float4 *stage = sstage[warp];
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
@@ -392,13 +398,14 @@ __device__ __noinline__ void write_chunk_exact(const TileArgs &a, const float4 *
     }
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(TileArgs a, const int64_t *__restrict__ seg,
                                                                    const uint32_t *__restrict__ counts, int cap,
                                                                    int packable, int32_t *__restrict__ qi_out,
                                                                    int32_t *__restrict__ pj_out,
                                                                    float *__restrict__ d_out) {
     extern __shared__ uint2 tslab[];  // kTileWarps * kTileQueries * cap
-    __shared__ TileStencil sts[kTileWarps];
+    __shared__ TileStencilT<NS> sts[kTileWarps];
     __shared__ float4 sstage[kTileWarps][32];
     __shared__ int srow[kTileWarps][kTileQueries];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(TileArgs a, c
     if (nA == 0) return;
     int cx, cy, cz;
     cell_coords((uint32_t)A, a.nc, cx, cy, cz);
-    TileStencil &ts = sts[warp];
+    TileStencilT<NS> &ts = sts[warp];
     float4 *stage = sstage[warp];
     int *rowlen = srow[warp];
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
@@ -443,6 +450,148 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(TileArgs a, c
             if (lane == 0 && (nL > (uint32_t)cap || nL != counts[iL])) atomicExch(a.err, nL > (uint32_t)cap ? 1 : 2);
             if (nL == 0 || nL > (uint32_t)cap) continue;
             sort_store_row(slab + q * cap, nL, iL, seg[iL], packable != 0, qi_out, pj_out, d_out);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ k nearest
+
+// kNN by radius: every candidate within the stencil's covered radius r0 is collected as
+// (r2 bits, index) into a 64-slot row per query, the row is sorted (bitonic network
+// across the warp), and the first m become the answer when the ranking is certain:
+// every gap between neighbours among the first m+1 exceeds 2 delta and, if fewer than
+// m+1 were found, the m-th sits more than 2 delta inside r0^2.  Other queries (too few
+// points within r0, too many for a row, or a near tie) are listed for the
+// thread-per-query kernel.
+struct KnnTile {
+    float r0sq;      // collect candidates with FP32 r2 < r0sq (r0 = covered radius)
+    float delta;     // FP32 error bound on r2 at r0
+    int k;
+    int stride;      // output row length m
+    int32_t *qi, *pj;
+    float *dist;
+    int32_t *counts;
+    int *list;       // sorted positions of queries left to the thread kernel
+    int *list_count;
+};
+
+template <int G>
+__device__ __forceinline__ void knn_chunk(const float4 *sp, float4 Q, int excl, float r0sq, int *rowcnt, uint2 *myrow) {
+#pragma unroll 4
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        if (r2 < r0sq) {
+            const int j = __float_as_int(c.w);
+            if (j != excl) {
+                const int pos = atomicAdd(rowcnt, 1);
+                if (pos < 64) myrow[pos] = make_uint2(__float_as_uint(r2), (uint32_t)j);
+            }
+        }
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, KnnTile K) {
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ uint2 srowbuf[kTileWarps][kTileQueries][64];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    TileStencilT<NS> &ts = sts[warp];
+    float4 *stage = sstage[warp];
+    int *rowlen = srow[warp];
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    const int m = K.stride;
+    for (int qb = 0; qb < nA; qb += kTileQueries) {
+        const int nq = min(kTileQueries, nA - qb);
+        const QLayout L = qlayout(nq);
+        const bool qact = L.myq < nq;
+        const float4 Q = qact ? __ldg(a.pts + begA + qb + L.myq) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const int excl = a.exclude ? __float_as_int(Q.w) : -1;
+        if (lane < kTileQueries) rowlen[lane] = 0;
+        __syncwarp();
+        uint2 *myrow = srowbuf[warp][L.myq];
+        int *myrc = rowlen + L.myq;
+        const float4 *sp = stage + L.g;
+        for (int base = 0; base < total; base += 32) {
+            tile_stage(a, ts, n, total, base, stage);
+#define FGB_KN(GV) knn_chunk<GV>(sp, Q, excl, K.r0sq, myrc, myrow)
+            FGB_TILE_DISPATCH_G(L.G, FGB_KN)
+#undef FGB_KN
+            __syncwarp();
+        }
+        __syncwarp();
+        for (int q = 0; q < nq; ++q) {
+            const int cnt = rowlen[q];
+            const int t = begA + qb + q;
+            const int iL = __float_as_int(__ldg(a.pts + t).w);
+            bool ok = cnt >= m && cnt <= 64;
+            uint2 e0 = make_uint2(0xffffffffu, 0u), e1 = make_uint2(0xffffffffu, 0u);
+            if (ok) {
+                const uint2 *row = srowbuf[warp][q];
+                if (2 * lane < cnt) e0 = row[2 * lane];
+                if (2 * lane + 1 < cnt) e1 = row[2 * lane + 1];
+#pragma unroll
+                for (int kk = 2; kk <= 64; kk <<= 1) {
+                    const bool asc = ((2 * lane) & kk) == 0;
+#pragma unroll
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        if (jj == 1) {
+                            const bool sw = ((e0.x > e1.x) || (e0.x == e1.x && e0.y > e1.y)) == asc;
+                            const uint2 t0 = sw ? e1 : e0, t1 = sw ? e0 : e1;
+                            e0 = t0;
+                            e1 = t1;
+                        } else {
+                            const int lm = jj >> 1;
+                            const uint32_t k0 = __shfl_xor_sync(0xffffffffu, e0.x, lm);
+                            const uint32_t v0 = __shfl_xor_sync(0xffffffffu, e0.y, lm);
+                            const uint32_t k1 = __shfl_xor_sync(0xffffffffu, e1.x, lm);
+                            const uint32_t v1 = __shfl_xor_sync(0xffffffffu, e1.y, lm);
+                            const bool takemin = ((lane & lm) == 0) == asc;
+                            const bool l0 = k0 < e0.x || (k0 == e0.x && v0 < e0.y);
+                            const bool l1 = k1 < e1.x || (k1 == e1.x && v1 < e1.y);
+                            if (l0 == takemin) e0 = make_uint2(k0, v0);
+                            if (l1 == takemin) e1 = make_uint2(k1, v1);
+                        }
+                    }
+                }
+                // gaps: element e = 2 lane + r against e + 1 (the next lane's first element)
+                const float f0 = __uint_as_float(e0.x), f1 = __uint_as_float(e1.x);
+                const float fnext = __shfl_down_sync(0xffffffffu, f0, 1);
+                const float twod = 2.f * K.delta;
+                bool amb = false;
+                if (2 * lane < m && 2 * lane + 1 < cnt) amb |= f1 - f0 <= twod;
+                if (2 * lane + 1 < m && 2 * lane + 2 < cnt && lane < 31) amb |= fnext - f1 <= twod;
+                const float fm = __shfl_sync(0xffffffffu, (m - 1) & 1 ? f1 : f0, (m - 1) >> 1);
+                if (cnt == m && !(fm + twod < K.r0sq)) amb = true;
+                ok = !__any_sync(0xffffffffu, amb);
+            }
+            if (ok) {
+                const int64_t row0 = (int64_t)iL * m;
+                if (2 * lane < m) {
+                    K.qi[row0 + 2 * lane] = iL;
+                    K.pj[row0 + 2 * lane] = (int32_t)e0.y;
+                    K.dist[row0 + 2 * lane] = sqrtf(__uint_as_float(e0.x));
+                }
+                if (2 * lane + 1 < m) {
+                    K.qi[row0 + 2 * lane + 1] = iL;
+                    K.pj[row0 + 2 * lane + 1] = (int32_t)e1.y;
+                    K.dist[row0 + 2 * lane + 1] = sqrtf(__uint_as_float(e1.x));
+                }
+                if (lane == 0) K.counts[iL] = m;
+            } else if (lane == 0) {
+                K.list[atomicAdd(K.list_count, 1)] = t;
+            }
         }
         __syncwarp();
     }
@@ -483,9 +632,12 @@ int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, un
     t.esc = esc;
     t.err = err;
     const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
-    {
+    if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
         FGB_KSCOPE("k_tile_count", s);
-        k_tile_count<<<grid, kTileWarps * 32, 0, s>>>(t, counts);
+        k_tile_count<32><<<grid, kTileWarps * 32, 0, s>>>(t, counts);
+    } else {
+        FGB_KSCOPE("k_tile_count", s);
+        k_tile_count<kTileMaxStencil><<<grid, kTileWarps * 32, 0, s>>>(t, counts);
     }
     FGB_LAUNCH_CHECK();
     return FGB_OK;
@@ -499,13 +651,45 @@ int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, in
     t.err = err;
     const size_t smem = tile_write_smem(cap);
     if (smem > 160 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tile write: neighbor count too large");
-    // the kernel also holds ~15 KB of static shared memory: always raise the dynamic limit
-    FGB_CUDA(cudaFuncSetAttribute(k_tile_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    const int packable = cap <= 128 && nq->n < ((int64_t)1 << 25);
+    // the kernel also holds static shared memory: always raise the dynamic limit
+    if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
+        FGB_CUDA(cudaFuncSetAttribute(k_tile_write<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FGB_KSCOPE("k_tile_write", s);
+        k_tile_write<32><<<grid, kTileWarps * 32, smem, s>>>(t, seg, counts, cap, packable, qi, pj, dist);
+    } else {
+        FGB_CUDA(cudaFuncSetAttribute(k_tile_write<kTileMaxStencil>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        FGB_KSCOPE("k_tile_write", s);
+        k_tile_write<kTileMaxStencil><<<grid, kTileWarps * 32, smem, s>>>(t, seg, counts, cap, packable, qi, pj, dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+
+int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, int32_t *qi, int32_t *pj, float *dist,
+             int32_t *counts, int *list, int *list_count, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, 1.0, exclude);
+    double r0 = std::min(nq->grid.wc[0], std::min(nq->grid.wc[1], nq->grid.wc[2])) * p.s[0];
+    for (int kk = 1; kk < 3; ++kk) r0 = std::min(r0, nq->grid.wc[kk] * p.s[kk]);
+    r0 *= 0.99999;
+    KnnTile K;
+    K.r0sq = (float)(r0 * r0 * (1.0 - 1e-6));
+    K.delta = (float)r2_error_bound(p, r0);
+    K.k = k;
+    K.stride = m;
+    K.qi = qi;
+    K.pj = pj;
+    K.dist = dist;
+    K.counts = counts;
+    K.list = list;
+    K.list_count = list_count;
     const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
     {
-        FGB_KSCOPE("k_tile_write", s);
-        const int packable = cap <= 128 && nq->n < ((int64_t)1 << 25);
-        k_tile_write<<<grid, kTileWarps * 32, smem, s>>>(t, seg, counts, cap, packable, qi, pj, dist);
+        FGB_KSCOPE("k_tile_knn", s);
+        k_tile_knn<32><<<grid, kTileWarps * 32, 0, s>>>(t, K);
     }
     FGB_LAUNCH_CHECK();
     return FGB_OK;
