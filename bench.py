@@ -240,7 +240,7 @@ def main():
     fgb.timing_enable(False)
     kern = {}
     for name in ("k_bin", "k_radix_hist", "k_radix_scatter", "k_cell_start", "k_ball_count", "k_ball_write",
-                 "k_ball_write_global", "k_tile_count", "k_tile_write", "k_tile_rdf", "k_reduce", "k_top", "k_down",
+                 "k_ball_write_global", "k_tile_count", "k_tile_write", "k_rdf_tile", "k_reduce", "k_top", "k_down",
                  "k_rdf", "k_rdf_escalated", "k_offset_table", "k_origin_tables", "k_band"):
         t, n = fgb.timing_read(name)
         if n:
@@ -285,7 +285,7 @@ def main():
         "k_ball_count": ("hbm", cnt_bytes, "GB/s", hbm),
         "k_tile_count": ("hbm", cnt_bytes, "GB/s", hbm),
         "k_rdf": ("alu", rdf_ops, "TOP/s", alu_peak),
-        "k_tile_rdf": ("alu", rdf_ops, "TOP/s", alu_peak),
+        "k_rdf_tile": ("alu", rdf_ops, "TOP/s", alu_peak),
     }
     bound, work, unit, peak = roofs.get(dominant, ("hbm", 0.0, "GB/s", hbm))
     t_dom = kern[dominant]["ms_per_step"] / kern[dominant]["launches_per_step"] * 1e-3

@@ -114,6 +114,15 @@ __device__ __forceinline__ float3 bond_f32(const BoxF &b, const float *x, int64_
                      __ldg(x + 3 * j + 1), __ldg(x + 3 * j + 2));
 }
 
+// 1/sqrt(x) by the hardware approximation (PTX rsqrt.approx, relative error below
+// 2^-22), with subnormal inputs taken as zero: skips the subnormal rescaling that the
+// non-ftz form adds.  Callers only pass r2 > 0 of pairs that matter or test the result.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float r2_f32(float dx, float dy, float dz) {
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
@@ -224,16 +233,9 @@ struct BinParams {
     const float2 *band;                                   // (bins+1) bands [lo, hi)
 };
 
-// >= 0: the bin; -1: certainly outside [r_min, r_max); -2: decide in FP64.
-// The fast test needs neither 0 <= b nor b < bins: an x just outside [0, bins) lies
-// within e of an edge and fails it.
-__device__ __forceinline__ int rdf_bin(const BinParams &P, float r2) {
-    if (r2 >= P.rmax_hi || r2 < P.rmin_lo) return -1;
-    const float inv = rsqrtf(r2);
-    const float x = fmaf(r2 * inv, P.invdelta, -P.rmin_invdelta);
-    const float fb = floorf(x);
-    const float e = fmaf(P.g2h, inv, P.eps);
-    if (r2 > P.r2_fast && fabsf((x - fb) - 0.5f) < 0.5f - e) return (int)fb;
+// Bin of an in-range pair from the FP32 bands around the exact edge thresholds (the
+// fast test of rdf_bin failed): >= 0 the bin, -2 decide in FP64.
+__device__ __forceinline__ int rdf_bin_band(const BinParams &P, float r2) {
     const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
     int b = (int)((r - P.rmin) * P.invdelta);
     b = min(max(b, 0), P.bins - 1);
@@ -249,6 +251,19 @@ __device__ __forceinline__ int rdf_bin(const BinParams &P, float r2) {
     }
     if (r2 >= e0.y && r2 < e1.x) return b;
     return -2;
+}
+
+// >= 0: the bin; -1: certainly outside [r_min, r_max); -2: decide in FP64.
+// The fast test needs neither 0 <= b nor b < bins: an x just outside [0, bins) lies
+// within e of an edge and fails it.
+__device__ __forceinline__ int rdf_bin(const BinParams &P, float r2) {
+    if (r2 >= P.rmax_hi || r2 < P.rmin_lo) return -1;
+    const float inv = rsqrtf(r2);
+    const float x = fmaf(r2 * inv, P.invdelta, -P.rmin_invdelta);
+    const float fb = floorf(x);
+    const float e = fmaf(P.g2h, inv, P.eps);
+    if (r2 > P.r2_fast && fabsf((x - fb) - 0.5f) < 0.5f - e) return (int)fb;
+    return rdf_bin_band(P, r2);
 }
 Stencil to_device(const BoxHost &b, const GridHost &g, const StencilPlan &p, const float4 *table);
 

@@ -1,0 +1,179 @@
+// Cell-tile building blocks shared by the ball-query, kNN and RDF tile kernels: the
+// per-warp stencil list of a query cell, the candidate stream over it and the lane
+// layouts that put queries or candidates on lanes.
+#pragma once
+
+#include "fgb_ball.cuh"
+
+namespace fgb {
+
+constexpr int kTileMaxStencil = 128;
+constexpr int kTileWarps = 4;     // warps per block
+constexpr int kTileQueries = 8;   // queries per pass of the write kernel
+
+struct TileArgs {
+    int nc[3];
+    int s[3];
+    int ts[3];
+    const float4 *off;        // offset table of half-width ts
+    const float4 *pts;        // sorted records
+    const uint32_t *cell_start;
+    int64_t ncell;
+    const float *p_orig;
+    BoxF bf;
+    BoxD bd;
+    Band band;
+    double T;
+    int exclude;
+    int half;                 // half stencil (self pairs visited once)
+    unsigned long long *esc;
+    int *err;
+};
+
+template <int NS>
+struct TileStencilT {
+    int beg[NS];
+    int pre[NS + 1];
+    float4 off[NS];
+};
+using TileStencil = TileStencilT<kTileMaxStencil>;
+
+// Builds the (half) stencil list of cell A in `ts` (one warp), returns the number of
+// stencil cells; pre[n] holds the total number of candidates.
+template <class TS>
+__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TS &ts) {
+    const int lane = threadIdx.x & 31;
+    const int wx = 2 * a.s[0] + 1, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
+    const int nfull = wx * wy * wz;
+    const int owx = 2 * a.ts[0] + 1, owy = 2 * a.ts[1] + 1;
+    int n = 0;
+    // offsets in (oz, oy, ox) order; the half stencil keeps (0,0,0) and what follows it
+    const int first = half ? (nfull - 1) / 2 : 0;
+    for (int b = first; b < nfull; b += 32) {
+        const int o = b + lane;
+        int cnt = 0, beg = 0;
+        float4 of = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (o < nfull) {
+            const int ox = o % wx - a.s[0], oy = (o / wx) % wy - a.s[1], oz = o / (wx * wy) - a.s[2];
+            const int xx = wrap_cell(cx + ox, a.nc[0]), yy = wrap_cell(cy + oy, a.nc[1]),
+                      zz = wrap_cell(cz + oz, a.nc[2]);
+            const int cell = (zz * a.nc[1] + yy) * a.nc[0] + xx;
+            beg = (int)__ldg(a.cell_start + cell);
+            cnt = (int)__ldg(a.cell_start + cell + 1) - beg;
+            of = __ldg(a.off + ((oz + a.ts[2]) * owy + (oy + a.ts[1])) * owx + (ox + a.ts[0]));
+        }
+        // inclusive scan of counts across the warp
+        int inc = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += u;
+        }
+        const int base = n ? ts.pre[n] : 0;
+        if (o < nfull) {
+            const int idx = n + lane;
+            ts.beg[idx] = beg;
+            ts.pre[idx] = base + inc - cnt;
+            ts.off[idx] = of;
+        }
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        const int m = min(32, nfull - b);
+        __syncwarp();
+        if (lane == 0) ts.pre[n + m] = base + tot;
+        __syncwarp();
+        n += m;
+    }
+    return n;
+}
+
+// Stencil cell holding candidate k (largest o with pre[o] <= k; empty cells are skipped
+// because the next non-empty cell shares their prefix).
+template <class TS>
+__device__ __forceinline__ int tile_find(const TS &ts, int n, int k) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ts.pre[mid] <= k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Candidate k of the current chunk: shifted position, index, sorted position, stencil slot.
+struct TileCand {
+    float x, y, z;
+    int j;
+    int p;
+    int o;
+};
+
+template <class TS>
+__device__ __forceinline__ TileCand tile_load(const TileArgs &a, const TS &ts, int n, int total, int k) {
+    TileCand c;
+    if (k < total) {
+        const int o = tile_find(ts, n, k);
+        const int p = ts.beg[o] + (k - ts.pre[o]);
+        const float4 r = __ldg(a.pts + p);
+        const float4 of = ts.off[o];
+        c.x = r.x + of.x;
+        c.y = r.y + of.y;
+        c.z = r.z + of.z;
+        c.j = __float_as_int(r.w);
+        c.p = p;
+        c.o = o;
+    } else {
+        c.x = c.y = c.z = 1e30f;
+        c.j = -1;
+        c.p = 0x7fffffff;
+        c.o = -1;
+    }
+    return c;
+}
+
+// Lanes hold queries, candidates are broadcast: a query block of nq <= 32 queries of the
+// cell is spread over qpl = next power of two >= nq lanes, and the warp's 32/qpl lane
+// groups take different candidates of the staged chunk in each round.
+struct QLayout {
+    int qpl, G, myq, g;
+};
+
+__device__ __forceinline__ QLayout qlayout(int nq) {
+    QLayout L;
+    L.qpl = 1;
+    while (L.qpl < nq) L.qpl <<= 1;
+    L.G = 32 / L.qpl;
+    const int lane = threadIdx.x & 31;
+    L.myq = lane & (L.qpl - 1);
+    L.g = lane / L.qpl;
+    return L;
+}
+
+constexpr float kFar = 1e30f;
+
+// Stages candidates [base, base + 32) of the stencil list, shifted into the query cell's
+// frame, as float4 (x, y, z, index bits); missing ones are placed far away.
+template <class TS>
+__device__ __forceinline__ void tile_stage(const TileArgs &a, const TS &ts, int n, int total, int base, float4 *stage) {
+    const int lane = threadIdx.x & 31;
+    const TileCand c = tile_load(a, ts, n, total, base + lane);
+    stage[lane] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+    __syncwarp();
+}
+
+// Dispatches a body templated on the number of lane groups G = 32 / qpl (uniform per warp).
+#define FGB_TILE_DISPATCH_G(G_, CALL) \
+    switch (G_) {                     \
+        case 32: CALL(32); break;     \
+        case 16: CALL(16); break;     \
+        case 8: CALL(8); break;       \
+        case 4: CALL(4); break;       \
+        case 2: CALL(2); break;       \
+        default: CALL(1); break;      \
+    }
+
+// Kernel arguments for a self query of radius R on plan p (host).
+TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude);
+
+}  // namespace fgb

@@ -13,7 +13,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "fgb_ball.cuh"
+#include "fgb_tile.cuh"
 
 struct fgb_rdf {
     int bins;
@@ -173,6 +173,149 @@ __global__ void k_rdf_escalated(RdfArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ cell-tile RDF
+//
+// Self queries on the shift route: one warp per query cell A, taken from a work counter
+// by persistent blocks.  The candidates of A's half stencil (A itself first, then the
+// cells after it in (z, y, x) offset order) stream through the lanes 32 at a time,
+// shifted into A's frame, while the warp loops over A's queries, read by a uniform
+// shared-memory load.  Every lane tests one pair per round and no lane waits on another
+// lane's trip count.  A's own points pair only with earlier queries of A, so each
+// unordered pair is binned once (weight 2).  Each warp counts into its own shared
+// histogram; the warps of a block merge theirs into the global counts at the end.
+
+constexpr int kRdfTileWarps = 4;
+constexpr int kRdfTileQ = 32;          // queries staged per pass
+constexpr int kRdfTileMaxBins = 1024;  // private histogram of every warp
+
+struct RdfTileArgs {
+    TileArgs t;
+    BinParams P;
+    const double *T;
+    int bins;
+    unsigned long long *hist;
+    int2 *esc;
+    int esc_cap;
+    int *esc_count;
+    unsigned weight;
+    unsigned *work;
+};
+
+// A pair in [r_min, r_max) whose fast test failed: the band tables decide, else the pair
+// is listed for the FP64 pass (or decided here when the list is full).
+__device__ __noinline__ void rdf_tile_slow(const RdfTileArgs *ap, float r2, int i, int j, uint32_t *h) {
+    const RdfTileArgs &a = *ap;
+    const int b = rdf_bin_band(a.P, r2);
+    if (b >= 0) {
+        atomicAdd(h + b, 1u);
+        return;
+    }
+    const int slot = atomicAdd(a.esc_count, 1);
+    if (slot < a.esc_cap) {
+        a.esc[slot] = make_int2(i, j);
+    } else {
+        const int be = exact_bin(a.T, a.bins, exact_r2_idx(a.t.bd, a.t.p_orig, i, a.t.p_orig, j));
+        if (be >= 0) atomicAdd(a.hist + be, (unsigned long long)a.weight);
+    }
+}
+
+// One staged candidate against the queries [0, nq) of the pass.  CENTER: the candidate
+// may be one of A's own points, valid only against queries before it (tl < lim).
+//
+// The bin work sits behind the in-range test: about a third of the rounds have no lane
+// in range (whole stencil cells lie beyond r_max of a query) and skip it.  The fast test
+// is rdf_bin's; pairs that fail it go to rdf_tile_slow.
+template <bool CENTER>
+__device__ __forceinline__ void rdf_tile_rounds(const RdfTileArgs &a, const float4 *qs, int nq, const TileCand &c,
+                                                int lim, uint32_t *h) {
+    const float rhi = a.P.rmax_hi, rlo = a.P.rmin_lo;
+    const float invd = a.P.invdelta, rmid = a.P.rmin_invdelta, g2h = a.P.g2h, eps = a.P.eps, r2f = a.P.r2_fast;
+#pragma unroll 4
+    for (int tl = 0; tl < nq; ++tl) {
+        const float4 q = qs[tl];
+        const float r2 = r2_f32(c.x - q.x, c.y - q.y, c.z - q.z);
+        bool in = r2 < rhi && r2 >= rlo;
+        if (CENTER) in = in && tl < lim;
+        if (in) {
+            const float inv = rsqrt_ftz(r2);
+            const float x = fmaf(r2 * inv, invd, -rmid);
+            const float fb = floorf(x);
+            const float e = fmaf(g2h, inv, eps);
+            if (r2 > r2f && fabsf((x - fb) - 0.5f) < 0.5f - e)
+                atomicAdd(h + (int)fb, 1u);
+            else
+                rdf_tile_slow(&a, r2, __float_as_int(q.w), c.j, h);
+        }
+    }
+}
+
+__device__ __forceinline__ void rdf_tile_flush(uint32_t *h, int bins, unsigned long long *hist, unsigned weight) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int b = lane; b < bins; b += 32) {
+        const uint32_t v = h[b];
+        if (v) {
+            atomicAdd(hist + b, (unsigned long long)v * weight);
+            h[b] = 0;
+        }
+    }
+    __syncwarp();
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_constant__ RdfTileArgs a) {
+    __shared__ TileStencilT<NS> sts[kRdfTileWarps];
+    __shared__ float4 sq[kRdfTileWarps][kRdfTileQ];
+    extern __shared__ uint32_t shist[];  // kRdfTileWarps * bins
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *h = shist + warp * a.bins;
+    for (int b = lane; b < a.bins; b += 32) h[b] = 0;
+    __syncwarp();
+    TileStencilT<NS> &ts = sts[warp];
+    float4 *qs = sq[warp];
+    uint64_t tests = 0;  // pair tests since the last flush bound every private count
+    for (;;) {
+        unsigned A = 0;
+        if (lane == 0) A = atomicAdd(a.work, 1u);
+        A = __shfl_sync(0xffffffffu, A, 0);
+        if ((int64_t)A >= a.t.ncell) break;
+        const int begA = (int)__ldg(a.t.cell_start + A);
+        const int nA = (int)__ldg(a.t.cell_start + A + 1) - begA;
+        if (nA == 0) continue;
+        int cx, cy, cz;
+        cell_coords(A, a.t.nc, cx, cy, cz);
+        __syncwarp();
+        const int n = tile_stencil(a.t, cx, cy, cz, true, ts);
+        const int total = ts.pre[n];
+        for (int qb = 0; qb < nA; qb += kRdfTileQ) {
+            const int nq = min(kRdfTileQ, nA - qb);
+            __syncwarp();
+            if (lane < nq) qs[lane] = __ldg(a.t.pts + begA + qb + lane);
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                if (tests > 0xffffffffull - 32 * kRdfTileQ) {
+                    rdf_tile_flush(h, a.bins, a.hist, a.weight);
+                    tests = 0;
+                }
+                tests += 32u * (unsigned)nq;
+                const int k = base + lane;
+                const TileCand c = tile_load(a.t, ts, n, total, k);
+                if (base < nA)
+                    rdf_tile_rounds<true>(a, qs, nq, c, k < nA ? k - qb : 0x7fffffff, h);
+                else
+                    rdf_tile_rounds<false>(a, qs, nq, c, 0, h);
+            }
+        }
+    }
+    __syncthreads();
+    // merge the warps' histograms, then one global add per bin and block
+    for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+        unsigned long long v = 0;
+        for (int w = 0; w < kRdfTileWarps; ++w) v += shist[w * a.bins + b];
+        if (v) atomicAdd(a.hist + b, v * a.weight);
+    }
+}
+
 // Histogram of the pairs of a NeighborList: every pair decided with the FP64 sequence.
 __global__ void k_rdf_nlist(BoxD bd, const int32_t *__restrict__ qi, const int32_t *__restrict__ pj, int64_t m,
                             const float *q_orig, const float *p_orig, const double *T, int bins,
@@ -181,6 +324,39 @@ __global__ void k_rdf_nlist(BoxD bd, const int32_t *__restrict__ qi, const int32
         const int b = exact_bin(T, bins, exact_r2_idx(bd, q_orig, qi[e], p_orig, pj[e]));
         if (b >= 0) atomicAdd(hist + b, 1ull);
     }
+}
+
+template <int NS>
+static int launch_rdf_tile_ns(const RdfTileArgs &ta, cudaStream_t s) {
+    const size_t smem = (size_t)kRdfTileWarps * ta.bins * sizeof(uint32_t);
+    int per_sm = 0;
+    FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_tile<NS>, kRdfTileWarps * 32, smem));
+    const int64_t cells = ta.t.ncell;
+    const int64_t want = (cells + kRdfTileWarps - 1) / kRdfTileWarps;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * std::max(per_sm, 1)));
+    FGB_KSCOPE("k_rdf_tile", s);
+    k_rdf_tile<NS><<<grid, kRdfTileWarps * 32, smem, s>>>(ta);
+    return FGB_OK;
+}
+
+// Self query on the shift route, bins <= kRdfTileMaxBins, half stencil of nhalf cells.
+static int launch_rdf_tile(const fgb_nq *nq, const StencilPlan &plan, double R, fgb_rdf *r, const BinParams &P,
+                           int nhalf, cudaStream_t s) {
+    RdfTileArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.t = tile_args(nq, plan, R, 1);
+    ta.P = P;
+    ta.T = r->T;
+    ta.bins = r->bins;
+    ta.hist = r->hist;
+    ta.esc = r->esc;
+    ta.esc_cap = r->esc_cap;
+    ta.esc_count = r->esc_count;
+    ta.weight = 2u;
+    ta.work = reinterpret_cast<unsigned *>(r->esc_count + 1);
+    if (nhalf <= 32) return launch_rdf_tile_ns<32>(ta, s);
+    if (nhalf <= 64) return launch_rdf_tile_ns<64>(ta, s);
+    return launch_rdf_tile_ns<kTileMaxStencil>(ta, s);
 }
 
 }  // namespace fgb
@@ -255,7 +431,7 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
         cudaMemsetAsync(r->hist, 0, sizeof(unsigned long long) * r->bins, s);
         r->norm = 0.0;
     }
-    if (st == FGB_OK) cudaMemsetAsync(r->esc_count, 0, sizeof(int), s);
+    if (st == FGB_OK) cudaMemsetAsync(r->esc_count, 0, 2 * sizeof(int), s);  // [0] band pairs, [1] work
     if (st == FGB_OK && nlist) {
         const float *q_orig = query_points ? query_points : nq->points;
         if (nlist->n_pairs > 0)
@@ -302,16 +478,24 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
             }
             if (st == FGB_OK) {
                 a.P = bin_params(r->bins, r->r_min, r->r_max, delta, r->band, r->T_host);
-                const int block = 256;
-                int copies = 4;
-                while (copies > 1 && (size_t)copies * r->bins * 4 > 32 * 1024) copies >>= 1;
-                const size_t smem = (size_t)copies * r->bins * 4;
-                a.copies = copies;
-                const unsigned grid = (unsigned)((nqq + block - 1) / block);
-                if (smem <= 48 * 1024)
-                    launch_rdf<true>(a, grid, smem, s);
-                else
-                    launch_rdf<false>(a, grid, 0, s);
+                const int nfull = (2 * plan.s[0] + 1) * (2 * plan.s[1] + 1) * (2 * plan.s[2] + 1);
+                const int nhalf = (nfull + 1) / 2;
+                const bool tile = a.half && nhalf <= kTileMaxStencil && r->bins <= kRdfTileMaxBins &&
+                                  !force_thread_kernels();
+                if (tile) {
+                    st = launch_rdf_tile(nq, plan, R, r, a.P, nhalf, s);
+                } else {
+                    const int block = 256;
+                    int copies = 4;
+                    while (copies > 1 && (size_t)copies * r->bins * 4 > 32 * 1024) copies >>= 1;
+                    const size_t smem = (size_t)copies * r->bins * 4;
+                    a.copies = copies;
+                    const unsigned grid = (unsigned)((nqq + block - 1) / block);
+                    if (smem <= 48 * 1024)
+                        launch_rdf<true>(a, grid, smem, s);
+                    else
+                        launch_rdf<false>(a, grid, 0, s);
+                }
                 {
                     FGB_KSCOPE("k_rdf_escalated", s);
                     k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);

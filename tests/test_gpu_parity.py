@@ -246,6 +246,21 @@ def test_rdf_from_neighbor_list_and_query_points(fgb):
     assert np.array_equal(rdf2.bin_counts, oracle.rdf_counts(b, x, 64, 2.5, exclude_ii=False, query_points=y))
 
 
+def test_rdf_dense_cells_duplicates_and_many_bins(fgb):
+    # a tight blob puts hundreds of points in a few cells (several query passes per
+    # cell in the tile kernel), exact duplicates give r = 0 pairs, and 3000 bins take the
+    # kernel with shared or global histograms instead of the private per-warp ones
+    b = W.Box.cube(20.0)
+    rng = np.random.default_rng(7)
+    blob = (rng.normal(size=(900, 3)) * 0.3).astype(np.float32)
+    x = np.concatenate([W.small_random(50, 2000, b), blob, blob[:50]]).astype(np.float32)
+    nq = fgb.NeighborQuery(b, dev(x), r_cell=3.0)
+    for bins, r_max, r_min in [(100, 3.0, 0.0), (3000, 3.0, 0.0), (77, 2.9, 0.4)]:
+        rdf = fgb.RDF(bins, r_max, r_min)
+        rdf.compute(nq)
+        assert np.array_equal(rdf.bin_counts, oracle.rdf_counts(b, x, bins, r_max, r_min)), bins
+
+
 def test_rdf_exact_edges(fgb):
     b = W.Box.cube(16.0)
     g = np.stack(np.meshgrid(*[np.arange(-8, 8)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
