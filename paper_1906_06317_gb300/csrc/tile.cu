@@ -103,12 +103,22 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
 
 // ------------------------------------------------------------------ ball-query write
 
-// Hits of a block of up to kTileQueries queries are appended as (index, distance) to
-// per-query rows of a warp-private shared slab (a shared counter per row hands out
-// slots), then each row is sorted by index and stored as its query's segment.  Sort keys
-// pack (index << 7 | slot) into 32 bits when indices fit 25 bits and rows 128 slots, so
-// a bitonic network across the warp moves one word per key (2 or 4 keys per lane);
-// otherwise hits are ranked by counting.
+// Each query's hits form a row of (index, distance) in shared memory; the row is sorted
+// by index and stored as the query's segment.  Sort keys pack (index << 7 | slot) into
+// 32 bits when indices fit 25 bits and rows 128 slots, so a bitonic network across the
+// warp moves one word per key (2 or 4 keys per lane); otherwise hits are ranked by
+// counting.
+
+constexpr int kWriteStage = 512;  // candidates a cell's stencil may hold for the staged path
+constexpr int kWriteQN = 2;       // queries per pass of the staged path
+
+// Shared bytes one warp of the write kernel needs: the staged path's candidates and row,
+// or the pass path's kTileQueries rows, whichever is larger.
+inline __host__ __device__ size_t write_warp_bytes(int cap) {
+    const size_t staged = (size_t)kWriteStage * 16 + (size_t)kWriteQN * cap * 8;
+    const size_t passes = (size_t)kTileQueries * cap * 8;
+    return ((staged > passes ? staged : passes) + 15) & ~(size_t)15;
+}
 
 template <int KPL>  // keys per lane (2 or 4): sorts 32 * KPL keys
 __device__ __forceinline__ void bitonic_keys(uint32_t (&v)[KPL]) {
@@ -140,6 +150,77 @@ __device__ __forceinline__ void bitonic_keys(uint32_t (&v)[KPL]) {
                     v[r] = (lower == asc) ? min(v[r], p) : max(v[r], p);
                 }
             }
+        }
+    }
+}
+
+// Two independent networks in one instruction stream (rows of two queries), so their
+// shuffles and compare-exchanges overlap.
+template <int KPL>
+__device__ __forceinline__ void bitonic_keys2(uint32_t (&v)[KPL], uint32_t (&w)[KPL]) {
+    const int lane = threadIdx.x & 31;
+    constexpr int N = 32 * KPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            if (jj < KPL) {
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const int p = r ^ jj;
+                    if (p > r) {
+                        const bool asc = (((KPL * lane + r) & k) == 0);
+                        const uint32_t lo = min(v[r], v[p]), hi = max(v[r], v[p]);
+                        const uint32_t lo2 = min(w[r], w[p]), hi2 = max(w[r], w[p]);
+                        v[r] = asc ? lo : hi;
+                        v[p] = asc ? hi : lo;
+                        w[r] = asc ? lo2 : hi2;
+                        w[p] = asc ? hi2 : lo2;
+                    }
+                }
+            } else {
+                const int lm = jj / KPL;
+                const bool lower = (lane & lm) == 0;
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const bool asc = (((KPL * lane + r) & k) == 0);
+                    const uint32_t p = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                    const uint32_t p2 = __shfl_xor_sync(0xffffffffu, w[r], lm);
+                    v[r] = (lower == asc) ? min(v[r], p) : max(v[r], p);
+                    w[r] = (lower == asc) ? min(w[r], p2) : max(w[r], p2);
+                }
+            }
+        }
+    }
+}
+
+template <int KPL>
+__device__ __forceinline__ void store_sorted_packed2(const uint2 *ra, uint32_t na, int ia, int64_t oa, const uint2 *rb,
+                                                     uint32_t nb, int ib, int64_t ob, int32_t *__restrict__ qi_out,
+                                                     int32_t *__restrict__ pj_out, float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v[KPL], w[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        v[r] = k < na ? (ra[k].x << 7) | k : 0xffffffffu;
+        w[r] = k < nb ? (rb[k].x << 7) | k : 0xffffffffu;
+    }
+    bitonic_keys2<KPL>(v, w);
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        if (k < na) {
+            const uint2 e = ra[v[r] & 127u];
+            __stcs(qi_out + oa + k, ia);
+            __stcs(pj_out + oa + k, (int32_t)e.x);
+            __stcs(d_out + oa + k, __uint_as_float(e.y));
+        }
+        if (k < nb) {
+            const uint2 e = rb[w[r] & 127u];
+            __stcs(qi_out + ob + k, ib);
+            __stcs(pj_out + ob + k, (int32_t)e.x);
+            __stcs(d_out + ob + k, __uint_as_float(e.y));
         }
     }
 }
@@ -233,31 +314,108 @@ __device__ __noinline__ void write_chunk_exact(const TileArgs &a, const float4 *
     }
 }
 
-template <int NS>
-__global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(const __grid_constant__ TileArgs a, const int64_t *__restrict__ seg,
-                                                                   const uint32_t *__restrict__ counts, int cap,
-                                                                   int packable, int32_t *__restrict__ qi_out,
-                                                                   int32_t *__restrict__ pj_out,
-                                                                   float *__restrict__ d_out) {
-    extern __shared__ uint2 tslab[];  // kTileWarps * kTileQueries * cap
-    __shared__ TileStencilT<NS> sts[kTileWarps];
-    __shared__ float4 sstage[kTileWarps][32];
-    __shared__ int srow[kTileWarps][kTileQueries];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
-    if (A >= a.ncell) return;
-    const int begA = (int)__ldg(a.cell_start + A);
-    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
-    if (nA == 0) return;
-    int cx, cy, cz;
-    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
-    TileStencilT<NS> &ts = sts[warp];
-    float4 *stage = sstage[warp];
-    int *rowlen = srow[warp];
-    const int n = tile_stencil(a, cx, cy, cz, false, ts);
-    const int total = ts.pre[n];
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// FP64 decision of a pair inside the band: its stored distance, or -1 when outside.
+__device__ __noinline__ float write_band_pair(const TileArgs *ap, int i, int j) {
+    const double e = exact_r2_idx(ap->bd, ap->p_orig, i, ap->p_orig, j);
+    return e < ap->T ? (float)sqrt(e) : -1.f;
+}
+
+// Cells whose stencil holds at most kWriteStage candidates: all of them are staged once
+// (shifted into A's frame), then the queries of A are taken in pairs (two independent
+// chains for the scheduler) with one candidate per lane.  Hits take consecutive row
+// slots in candidate order (ballot + popc, no atomics); both rows are sorted by one
+// interleaved network and stored before the next pair, so the warp needs kWriteQN = 2
+// rows.  A's own points are the centre entry of the stencil, whose offset is zero, so
+// the staged copy is the query itself.
+template <class TS>
+__device__ __forceinline__ void write_cell_staged(const TileArgs &a, const TS &ts, int n, int total, int nA,
+                                                  float4 *stg, uint2 *row, const int64_t *__restrict__ seg,
+                                                  const uint32_t *__restrict__ counts, int cap, bool packable,
+                                                  int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                  float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < total; base += 32) {
+        const TileCand c = tile_load(a, ts, n, total, base + lane);
+        stg[base + lane] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+    }
+    __syncwarp();
+    const int nch = (total + 31) >> 5;
+    const int centre = ts.pre[(n - 1) / 2];
     const float lo = a.band.lo, hi = a.band.hi;
-    uint2 *slab = tslab + (size_t)warp * kTileQueries * cap;
+    const unsigned lt = lanemask_lt();
+    uint2 *rowb = row + cap;
+    for (int q = 0; q < nA; q += 2) {
+        const bool two = q + 1 < nA;
+        const float4 Qa = stg[centre + q];
+        const float4 Qb = two ? stg[centre + q + 1] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const int ia = __float_as_int(Qa.w), ib = __float_as_int(Qb.w);
+        const int xa = a.exclude ? ia : -1, xb = a.exclude ? ib : -1;
+        uint32_t na = 0, nb = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const float4 c = stg[(ch << 5) + lane];
+            const int j = __float_as_int(c.w);
+            const float r2a = r2_f32(c.x - Qa.x, c.y - Qa.y, c.z - Qa.z);
+            const float r2b = r2_f32(c.x - Qb.x, c.y - Qb.y, c.z - Qb.z);
+            bool ha = r2a < lo && j != xa, hb = r2b < lo && j != xb;
+            float da = r2a > 0.f ? r2a * rsqrt_ftz(r2a) : 0.f;
+            float db = r2b > 0.f ? r2b * rsqrt_ftz(r2b) : 0.f;
+            const bool ba = r2a >= lo && r2a < hi && j != xa && j >= 0;
+            const bool bb = r2b >= lo && r2b < hi && j != xb && j >= 0 && ib >= 0;
+            if (__any_sync(0xffffffffu, ba || bb)) {
+                if (ba) {
+                    const float d = write_band_pair(&a, ia, j);
+                    if (d >= 0.f) {
+                        ha = true;
+                        da = d;
+                    }
+                }
+                if (bb) {
+                    const float d = write_band_pair(&a, ib, j);
+                    if (d >= 0.f) {
+                        hb = true;
+                        db = d;
+                    }
+                }
+            }
+            const unsigned ma = __ballot_sync(0xffffffffu, ha), mb = __ballot_sync(0xffffffffu, hb);
+            const uint32_t pa = na + __popc(ma & lt), pb = nb + __popc(mb & lt);
+            if (ha && pa < (uint32_t)cap) row[pa] = make_uint2((uint32_t)j, __float_as_uint(da));
+            if (hb && pb < (uint32_t)cap) rowb[pb] = make_uint2((uint32_t)j, __float_as_uint(db));
+            na += __popc(ma);
+            nb += __popc(mb);
+        }
+        __syncwarp();
+        if (lane == 0 && (na > (uint32_t)cap || na != counts[ia])) atomicExch(a.err, na > (uint32_t)cap ? 1 : 2);
+        if (lane == 0 && two && (nb > (uint32_t)cap || nb != counts[ib])) atomicExch(a.err, nb > (uint32_t)cap ? 1 : 2);
+        const bool oka = na <= (uint32_t)cap, okb = two && nb <= (uint32_t)cap;
+        if (packable && oka && okb && na <= 64 && nb <= 64) {
+            store_sorted_packed2<2>(row, na, ia, seg[ia], rowb, nb, ib, seg[ib], qi_out, pj_out, d_out);
+        } else if (packable && oka && okb && na <= 128 && nb <= 128) {
+            store_sorted_packed2<4>(row, na, ia, seg[ia], rowb, nb, ib, seg[ib], qi_out, pj_out, d_out);
+        } else {
+            if (na != 0 && oka) sort_store_row(row, na, ia, seg[ia], packable, qi_out, pj_out, d_out);
+            if (nb != 0 && okb) sort_store_row(rowb, nb, ib, seg[ib], packable, qi_out, pj_out, d_out);
+        }
+        __syncwarp();
+    }
+}
+
+// Cells with larger stencils: blocks of kTileQueries queries on lane groups, the
+// candidates staged 32 at a time, hits appended through per-row shared counters.
+template <class TS>
+__device__ __forceinline__ void write_cell_passes(const TileArgs &a, const TS &ts, int n, int total, int begA, int nA,
+                                                  float4 *stage, int *rowlen, uint2 *slab,
+                                                  const int64_t *__restrict__ seg, const uint32_t *__restrict__ counts,
+                                                  int cap, bool packable, int32_t *__restrict__ qi_out,
+                                                  int32_t *__restrict__ pj_out, float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    const float lo = a.band.lo, hi = a.band.hi;
     for (int qb = 0; qb < nA; qb += kTileQueries) {
         const int nq = min(kTileQueries, nA - qb);
         const QLayout L = qlayout(nq);
@@ -284,10 +442,42 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_write(const __grid_
             const int iL = __float_as_int(__ldg(a.pts + begA + qb + q).w);
             if (lane == 0 && (nL > (uint32_t)cap || nL != counts[iL])) atomicExch(a.err, nL > (uint32_t)cap ? 1 : 2);
             if (nL == 0 || nL > (uint32_t)cap) continue;
-            sort_store_row(slab + q * cap, nL, iL, seg[iL], packable != 0, qi_out, pj_out, d_out);
+            sort_store_row(slab + q * cap, nL, iL, seg[iL], packable, qi_out, pj_out, d_out);
         }
         __syncwarp();
     }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_constant__ TileArgs a,
+                                                                   const int64_t *__restrict__ seg,
+                                                                   const uint32_t *__restrict__ counts, int cap,
+                                                                   int packable, int32_t *__restrict__ qi_out,
+                                                                   int32_t *__restrict__ pj_out,
+                                                                   float *__restrict__ d_out) {
+    extern __shared__ __align__(16) unsigned char tsm[];  // kTileWarps * write_warp_bytes(cap)
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5;
+    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    TileStencilT<NS> &ts = sts[warp];
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    unsigned char *region = tsm + (size_t)warp * write_warp_bytes(cap);
+    if (total <= kWriteStage)
+        write_cell_staged(a, ts, n, total, nA, reinterpret_cast<float4 *>(region),
+                          reinterpret_cast<uint2 *>(region + kWriteStage * sizeof(float4)), seg, counts, cap,
+                          packable != 0, qi_out, pj_out, d_out);
+    else
+        write_cell_passes(a, ts, n, total, begA, nA, sstage[warp], srow[warp], reinterpret_cast<uint2 *>(region), seg,
+                          counts, cap, packable != 0, qi_out, pj_out, d_out);
 }
 
 // ------------------------------------------------------------------ k nearest
@@ -530,6 +720,6 @@ int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, 
     return FGB_OK;
 }
 
-size_t tile_write_smem(int cap) { return (size_t)kTileWarps * kTileQueries * cap * sizeof(uint2); }
+size_t tile_write_smem(int cap) { return (size_t)kTileWarps * write_warp_bytes(cap); }
 
 }  // namespace fgb
