@@ -105,6 +105,31 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of the top kernels from one ncu capture of the
+# c3 workload at 2,097,152 points (profiles/k_*_c3_2M.md), with the sha256 prefix of the
+# source file of the captured build.  Traffic grows in proportion to N at fixed density,
+# so it is scaled to the bench's N; once the source changes the figure is stale and is
+# reported as null.
+MEASURED_TRAFFIC = {
+    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "0dc5c46fb493e927", 556.983808e6 + 1537.264e6, 2097152),
+    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "0dc5c46fb493e927", 34.419456e6 + 0.015e6, 2097152),
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "902b1d7eb3c7e3f6", 34.194944e6 + 0.014e6, 2097152),
+}
+
+
+def measured_traffic(kernel: str, n: int):
+    """Scaled DRAM bytes per launch, or None when unmeasured or the source has changed."""
+    import hashlib
+    if kernel not in MEASURED_TRAFFIC:
+        return None
+    path, sha, nbytes, n0 = MEASURED_TRAFFIC[kernel]
+    try:
+        cur = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return nbytes * n / n0 if cur.startswith(sha) else None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -291,7 +316,8 @@ def main():
     t_dom = kern[dominant]["ms_per_step"] / kern[dominant]["launches_per_step"] * 1e-3
     achieved = work / t_dom
     roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": None,
+                "unit": unit, "frac": achieved / peak, "traffic": measured_traffic(dominant, n),
+                "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 2,097,152 points)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm"
                 else f"derived: 152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
     others = {}
@@ -299,7 +325,7 @@ def main():
         if k in kern:
             tk = kern[k]["ms_per_step"] / kern[k]["launches_per_step"] * 1e-3
             others[k] = {"bound": b, "achieved": wk / tk, "peak": pk, "unit": u, "frac": wk / tk / pk,
-                         "ms": tk * 1e3}
+                         "ms": tk * 1e3, "traffic": measured_traffic(k, n)}
 
     # ---------------- other parts of the hot path (component timings)
     components = {}
