@@ -389,6 +389,19 @@ def extras(fgb, torch, dev, stream, flush):
         return nq.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
 
     comp["c3_knn12_ms"] = timed(knn, stream, flush)
+
+    # the same r = 2.5 NeighborList from the tree NeighborQuery (build + query) next to
+    # the cell list (build + query)
+    def tree_query():
+        aq = fgb.AABBQuery(w.box, x)
+        return aq.query(None, dict(r_max=2.5, exclude_ii=True)).toNeighborList()
+
+    def cell_query():
+        nq = fgb.NeighborQuery(w.box, x, r_cell=2.5)
+        return nq.query(None, dict(r_max=2.5, exclude_ii=True)).toNeighborList()
+
+    comp["c3_tree_build_query_ms"] = timed(tree_query, stream, flush, reps=3, warm=1)
+    comp["c3_cell_build_query_ms"] = timed(cell_query, stream, flush, reps=3, warm=1)
     # Q6 forward + backward, N = 2^20, fixed neighbor list r = 1.3
     w4 = W.c4()
     x4 = torch.from_numpy(w4.points).to(dev)
@@ -405,6 +418,44 @@ def extras(fgb, torch, dev, stream, flush):
 
     comp["c4_q6_fwd_ms"] = timed(fwd, stream, flush)
     comp["c4_q6_fwd_bwd_ms"] = timed(fwdbwd, stream, flush)
+    # c1: 4,096 points, L = 16: cell list + ball query r = 4 + RDF 100 bins (latency-bound)
+    w1 = W.c1()
+    x1 = torch.from_numpy(w1.points).to(dev)
+    rdf1 = fgb.RDF(100, 4.0)
+
+    def c1_step():
+        nq = fgb.NeighborQuery(w1.box, x1, r_cell=4.0)
+        nl = nq.query(None, dict(r_max=4.0, exclude_ii=True)).toNeighborList()
+        rdf1.compute(nq, reset=True)
+        return nl
+
+    comp["c1_query_rdf_us"] = 1e3 * timed(c1_step, stream, flush)
+    # c2: 500,000-point FCC crystal in a triclinic box: ball query r = 1.3, q4 and q6 from
+    # the list, RDF 200 bins on [0, 5) (its own cell list at r_max / 2)
+    w2 = W.c2()
+    x2 = torch.from_numpy(w2.points).to(dev)
+    holder = {}
+
+    def c2_query():
+        nq = fgb.NeighborQuery(w2.box, x2, r_cell=1.3)
+        holder["nq"], holder["nl"] = nq, nq.query(None, dict(r_max=1.3, exclude_ii=True)).toNeighborList()
+
+    comp["c2_ball_query_ms"] = timed(c2_query, stream, flush)
+    st4, st6 = fgb.Steinhardt(4), fgb.Steinhardt(6)
+
+    def c2_ql():
+        st4.compute(holder["nq"], neighbors=holder["nl"])
+        st6.compute(holder["nq"], neighbors=holder["nl"])
+
+    comp["c2_q4_q6_ms"] = timed(c2_ql, stream, flush)
+    rdf2 = fgb.RDF(200, 5.0)
+
+    def c2_rdf():
+        rdf2.compute(fgb.NeighborQuery(w2.box, x2, r_cell=2.5), reset=True)
+
+    comp["c2_rdf_ms"] = timed(c2_rdf, stream, flush)
+    comp["c2_nl_pairs"] = holder["nl"].n_pairs
+    holder.clear()
     # batched frames
     if hasattr(fgb.lib(), "fgb_batch_run"):
         try:

@@ -106,7 +106,25 @@ int fgb_nq_create(const fgb_box *box, const float *points, int64_t n, double r_c
                   fgb_nq **out);
 void fgb_nq_destroy(fgb_nq *nq);
 
-/* Cell grid of a NeighborQuery: cells per axis (x, y, z) and number of points. */
+/* ----------------------------------------------------- NeighborQuery (AABB tree) */
+
+/*
+ * Builds a tree NeighborQuery over `n` points (Section "General Utilities": the AABBQuery
+ * subclass of NeighborQuery, benchmarked in Fig. 3): a bounding-volume hierarchy over the
+ * points wrapped into the box, ordered by 30-bit Morton code (radix tree built in
+ * parallel, boxes refit bottom-up).  The handle is an fgb_nq: fgb_nq_query answers ball
+ * queries (r_max) with the same NeighborList, bit for bit, as the cell list (kNN returns
+ * UNSUPPORTED), and fgb_rdf_compute / fgb_steinhardt_compute take it together with a
+ * NeighborList.  The call synchronises `stream` once (it checks the coordinates).
+ * Points (and query points) must lie within two box lengths of the box centre
+ * (|s - 1/2| <= 2 in fractional coordinates); points inside the box keep their exact
+ * coordinates.  n may be 0.  Errors: INVALID_ARG (n < 0, points NULL with n > 0,
+ * degenerate box, points out of range), CAPACITY (n >= 2^31), OOM, CUDA.
+ */
+int fgb_aabb_create(const fgb_box *box, const float *points, int64_t n, void *stream, fgb_nq **out);
+
+/* Cell grid of a NeighborQuery: cells per axis (x, y, z) and number of points (a tree
+ * NeighborQuery reports 0 cells). */
 int fgb_nq_dims(const fgb_nq *nq, int32_t ncell[3], int64_t *n_points);
 
 /*
@@ -115,7 +133,7 @@ int fgb_nq_dims(const fgb_nq *nq, int32_t ncell[3], int64_t *n_points);
  *               as the bit pattern of the 4th float, in (cell, index) order;
  *   sorted_cell (n) uint32: cell index of each sorted entry;
  *   cell_start  (ncells + 1) uint32: entries of cell c are cell_start[c] .. cell_start[c+1].
- * Cell index = (cz * ny + cy) * nx + cx.
+ * Cell index = (cz * ny + cy) * nx + cx.  UNSUPPORTED for a tree NeighborQuery.
  */
 int fgb_nq_cells(const fgb_nq *nq, const float **sorted, const uint32_t **sorted_cell,
                  const uint32_t **cell_start);

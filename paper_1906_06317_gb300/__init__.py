@@ -67,6 +67,7 @@ _SIGS = {
     "fgb_timing_reset": (_I32, []),
     "fgb_nq_create": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _D, _P, _PP]),
     "fgb_nq_destroy": (None, [_P]),
+    "fgb_aabb_create": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _P, _PP]),
     "fgb_nq_dims": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "fgb_nq_cells": (_I32, [_P, _PP, _PP, _PP]),
     "fgb_nq_query": (_I32, [_P, _P, _I64, ctypes.POINTER(fgb_query_args), _P, _PP]),
@@ -342,6 +343,28 @@ class NeighborQuery:
         h = ctypes.c_void_p()
         _check(lib().fgb_nq_query(self._h, qp, nq, ctypes.byref(qa), _stream(), ctypes.byref(h)))
         return NeighborList(h.value, keep)
+
+
+class AABBQuery(NeighborQuery):
+    """Tree NeighborQuery (freud locality.AABBQuery): a bounding-volume hierarchy over the
+    device points, answering ball queries (r_max) with the same NeighborList as the cell
+    list.  RDF and Steinhardt take it together with a NeighborList."""
+
+    def __init__(self, box, points: torch.Tensor):
+        self.box = Box.from_box(box)
+        self.points = _need_cuda(points, name="points")
+        if self.points.ndim != 2 or self.points.shape[1] != 3:
+            raise ValueError("points must have shape (N, 3)")
+        self.r_cell = None
+        h = ctypes.c_void_p()
+        b = self.box._c()
+        _check(lib().fgb_aabb_create(ctypes.byref(b), self.points.data_ptr(), self.points.shape[0], _stream(),
+                                     ctypes.byref(h)))
+        self._o = _Owned(h.value, "fgb_nq_destroy", (self.points,))
+        self._h = self._o.ptr
+
+    def cells(self):
+        raise FGBError(ERR_UNSUPPORTED, "a tree NeighborQuery has no cell list")
 
 
 

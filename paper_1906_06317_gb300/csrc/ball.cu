@@ -18,6 +18,15 @@ bool force_thread_kernels() {
     return v == 1;
 }
 
+bool force_tile_kernels() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_TILE_KERNELS");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *a, cudaStream_t s, fgb_nlist *nl);
 
 template <int MODE, bool CHECKJ>
@@ -204,7 +213,7 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
     uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
     const bool checkj = !Q.self && a.exclude;
-    const bool tile = Q.self && tile_ok(plan) && !force_thread_kernels();
+    const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && !force_thread_kernels();
     if (st == FGB_OK && nqq > 0 && tile) {
         st = tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
         st = st ? st : scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
@@ -306,13 +315,19 @@ extern "C" int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_que
     if (query_points && query_points != nq->points && n_query < 0)
         return fail(FGB_ERR_INVALID_ARG, "n_query must be >= 0");
     cudaStream_t s = as_stream(stream);
-    QueryPoints Q;
-    int st = prepare_queries(nq, query_points, n_query, s, &Q);
+    if (nq->kind == 1 && knn) return fail(FGB_ERR_UNSUPPORTED, "the tree query answers r_max queries only");
     fgb_nlist *nl = new fgb_nlist();
     memset(nl, 0, sizeof(*nl));
     nl->stream = s;
-    if (st == FGB_OK) st = ball ? ball_query(nq, Q, args, s, nl) : knn_query(nq, Q, args, s, nl);
-    release_queries(&Q, s);
+    int st = FGB_OK;
+    if (nq->kind == 1) {
+        st = aabb_ball_query(nq, query_points, n_query, args, s, nl);
+    } else {
+        QueryPoints Q;
+        st = prepare_queries(nq, query_points, n_query, s, &Q);
+        if (st == FGB_OK) st = ball ? ball_query(nq, Q, args, s, nl) : knn_query(nq, Q, args, s, nl);
+        release_queries(&Q, s);
+    }
     if (st != FGB_OK) {
         fgb_nlist_destroy(nl);
         return st;

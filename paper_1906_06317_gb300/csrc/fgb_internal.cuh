@@ -128,6 +128,9 @@ struct fgb_nq {
     float2 *origin_buf;    // all origin tables, packed
     fgb::OriginTables org;
     cudaStream_t stream;
+    int kind;              // 0: cell list, 1: bounding-volume hierarchy (sorted = points in Morton order)
+    void *bvh;             // kind 1: n-1 internal nodes (aabb.cu)
+    int bvh_moved;         // kind 1: wrapping moved some point
 };
 
 struct fgb_nlist {
@@ -179,12 +182,30 @@ int plan_stencil(const fgb_nq *nq, double R, int s_table_min, cudaStream_t st, S
 int plan_stencil_host(const BoxHost &b, const GridHost &g, double R, int s_table_min, StencilPlan *p,
                       std::vector<float4> *table);
 double r2_error_bound(const StencilPlan &p, double R);
+// The same bound from a per-component displacement error eps_d (box vector length sum Lsum).
+double r2_error_bound_eps(double eps_d, double Lsum, double R);
 // FP32 band [lo, hi) around the exact threshold T, widened by `delta` and rounded outward.
 void band_around(double T, double delta, float *lo, float *hi);
 
+// Bounding-volume-hierarchy neighbor query (aabb.cu).
+int aabb_build(fgb_nq *nq, cudaStream_t s);
+void aabb_free(fgb_nq *nq);
+int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
+                    cudaStream_t s, fgb_nlist *nl);
+// Sorts every segment of a list by point index in place (warp per segment, rows of at
+// most cap entries staged in shared memory); tile.cu.
+int sort_segments(const int64_t *seg, int64_t nq, int cap, int packable, int32_t *qi, int32_t *pj, float *dist,
+                  cudaStream_t s);
+
 // Cell-tile kernels (tile.cu): one warp per query cell, self queries on the shift route.
 bool tile_ok(const StencilPlan &p);
+// Whether the grid gives the warp-per-cell kernels enough warps and short enough rows:
+// at least 4 cells per SM and at most 64 points per cell on average (a small box with a
+// few crowded cells runs faster one thread per query).
+bool tile_worth(const fgb_nq *nq);
 bool force_thread_kernels();
+// FGB_TILE_KERNELS=1: the cell-tile kernels wherever they apply, however small the grid.
+bool force_tile_kernels();
 int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
                uint32_t *counts, cudaStream_t s);
 size_t tile_write_smem(int cap);

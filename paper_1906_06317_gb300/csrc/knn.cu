@@ -350,7 +350,7 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
         // self queries on the shift route: radius kernel over cell tiles first, the
         // thread-per-query kernel only for the queries it leaves
         const bool tile = Q.self && plan.mode == 0 && plan.s[0] == 1 && plan.s[1] == 1 && plan.s[2] == 1 &&
-                          m_uniform >= 1 && m_uniform <= 62 && !force_thread_kernels();
+                          m_uniform >= 1 && m_uniform <= 62 && tile_worth(nq) && !force_thread_kernels();
         if (tile && nqq > 0) {
             st = tile_knn(nq, plan, k, m_uniform, a.exclude, tqi, tpj, td, nl->counts, ctl + 4, ctl + 2, s);
             a.list = ctl + 4;

@@ -448,6 +448,7 @@ extern "C" void fgb_nq_destroy(fgb_nq *nq) {
     dfree(nq->sorted_cell, nq->stream);
     dfree(nq->cell_start, nq->stream);
     dfree(nq->origin_buf, nq->stream);
+    if (nq->kind == 1) aabb_free(nq);
     delete nq;
 }
 
@@ -462,6 +463,7 @@ extern "C" int fgb_nq_dims(const fgb_nq *nq, int32_t ncell[3], int64_t *n_points
 extern "C" int fgb_nq_cells(const fgb_nq *nq, const float **sorted, const uint32_t **sorted_cell,
                             const uint32_t **cell_start) {
     if (!nq) return fail(FGB_ERR_INVALID_ARG, "nq is NULL");
+    if (nq->kind != 0) return fail(FGB_ERR_UNSUPPORTED, "not a cell-list NeighborQuery");
     if (sorted) *sorted = reinterpret_cast<const float *>(nq->sorted);
     if (sorted_cell) *sorted_cell = nq->sorted_cell;
     if (cell_start) *cell_start = nq->cell_start;

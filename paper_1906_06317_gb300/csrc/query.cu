@@ -117,14 +117,14 @@ int launch_offset_table(const BoxHost &b, const GridHost &g, const StencilPlan &
     return FGB_OK;
 }
 
-double r2_error_bound(const StencilPlan &p, double R) {
+double r2_error_bound_eps(double e, double Lsum, double R) {
     const double u = std::ldexp(1.0, -24);
-    const double e = p.eps_d;
     // r2 = fma(dz,dz, fma(dy,dy, dx*dx)): |sum 2 d_k e| + 3 e^2 from the displacement,
     // 3 u r2 from the three roundings, plus slack for the FP64 reference's own rounding.
-    return 2.0 * std::sqrt(3.0) * R * e + 3.0 * e * e + 3.0 * u * (R + e) * (R + e) +
-           1e-12 * (R + p.Lsum) * (R + p.Lsum);
+    return 2.0 * std::sqrt(3.0) * R * e + 3.0 * e * e + 3.0 * u * (R + e) * (R + e) + 1e-12 * (R + Lsum) * (R + Lsum);
 }
+
+double r2_error_bound(const StencilPlan &p, double R) { return r2_error_bound_eps(p.eps_d, p.Lsum, R); }
 
 void band_around(double T, double delta, float *lo, float *hi) {
     double l = T - delta, h = T + delta;

@@ -416,6 +416,8 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                                const fgb_nlist *nlist, int32_t reset, void *stream) {
     clear_error();
     if (!r || !nq) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    if (nq->kind != 0 && !nlist)
+        return fail(FGB_ERR_UNSUPPORTED, "the fused RDF walks a cell list; pass a NeighborList from the tree query");
     cudaStream_t s = as_stream(stream);
     const double R = r->r_max;
     if (!(R < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
@@ -480,7 +482,7 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                 a.P = bin_params(r->bins, r->r_min, r->r_max, delta, r->band, r->T_host);
                 const int nfull = (2 * plan.s[0] + 1) * (2 * plan.s[1] + 1) * (2 * plan.s[2] + 1);
                 const int nhalf = (nfull + 1) / 2;
-                const bool tile = a.half && nhalf <= kTileMaxStencil && r->bins <= kRdfTileMaxBins &&
+                const bool tile = a.half && nhalf <= kTileMaxStencil && r->bins <= kRdfTileMaxBins && tile_worth(nq) &&
                                   !force_thread_kernels();
                 if (tile) {
                     st = launch_rdf_tile(nq, plan, R, r, a.P, nhalf, s);

@@ -255,6 +255,8 @@ extern "C" int fgb_steinhardt_compute(fgb_steinhardt *st, fgb_nq *nq, const fgb_
     } else {
         if (!qargs || !(qargs->r_max > 0.0))
             return fail(FGB_ERR_UNSUPPORTED, "without a NeighborList the neighbors must be a ball query (r_max > 0)");
+        if (nq->kind != 0)
+            return fail(FGB_ERR_UNSUPPORTED, "the fused query walks a cell list; pass a NeighborList from the tree query");
         const double R = qargs->r_max;
         if (!(R < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
             return fail(FGB_ERR_BOX_TOO_SMALL, "r_max must be below half the smallest box width");

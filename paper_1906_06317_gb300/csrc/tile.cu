@@ -480,6 +480,42 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_
                           counts, cap, packable != 0, qi_out, pj_out, d_out);
 }
 
+// Sorts each segment [seg[q], seg[q+1]) of (qi, pj, dist) by point index in place: one
+// warp per segment, staged as (index, distance) in shared memory, then the same network
+// (or ranking) and stores as the write kernels.
+__global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int cap, int packable,
+                                int32_t *__restrict__ qi, int32_t *__restrict__ pj, float *__restrict__ dist) {
+    extern __shared__ uint2 srows[];  // (blockDim / 32) * cap
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (q >= nq) return;
+    const int64_t b = seg[q];
+    const uint32_t n = (uint32_t)(seg[q + 1] - b);
+    if (n <= 1 || n > (uint32_t)cap) return;
+    uint2 *row = srows + (size_t)warp * cap;
+    for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
+    const int iq = qi[b];
+    __syncwarp();
+    sort_store_row(row, n, iq, b, packable != 0, qi, pj, dist);
+}
+
+int sort_segments(const int64_t *seg, int64_t nq, int cap, int packable, int32_t *qi, int32_t *pj, float *dist,
+                  cudaStream_t s) {
+    if (nq == 0 || cap <= 1) return FGB_OK;
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * cap * sizeof(uint2) > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * cap * sizeof(uint2);
+    if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tree query: more than %d neighbors of one point", 25600);
+    FGB_CUDA(cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        FGB_KSCOPE("k_sort_segments", s);
+        k_sort_segments<<<(unsigned)((nq + warps - 1) / warps), 32 * warps, smem, s>>>(seg, nq, cap, packable, qi, pj,
+                                                                                        dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
 // ------------------------------------------------------------------ k nearest
 
 // kNN by radius: every candidate within the stencil's covered radius r0 is collected as
@@ -628,6 +664,11 @@ bool tile_ok(const StencilPlan &p) {
     if (p.mode != 0) return false;
     const int n = (2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1);
     return n <= kTileMaxStencil;
+}
+
+bool tile_worth(const fgb_nq *nq) {
+    const int64_t cells = nq->grid.ncell;
+    return force_tile_kernels() || (cells >= 4 * (int64_t)num_sms() && nq->n <= 64 * cells);
 }
 
 TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude) {

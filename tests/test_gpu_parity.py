@@ -419,26 +419,46 @@ def test_full_c2_steinhardt_and_c4_gradient_sampled(fgb):
             assert abs(fd - g[k, c]) <= G_TOL * np.abs(g).max() + 1e-3 * abs(fd)
 
 
-def test_thread_per_query_kernels_via_env():
-    """Self ball queries default to the cell-tile kernels; FGB_THREAD_KERNELS=1 selects
-    the thread-per-query count and write kernels, which must agree as well."""
+# Small grids run one thread per query by default and large ones the cell-tile kernels;
+# each environment switch forces one family so that both stay covered at small sizes.
+KERNEL_SWITCH_CHECKS = r"""
+import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb
+dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+def ball(b, x, r, rc):
+    nl = fgb.NeighborQuery(b, dev(x), r_cell=rc).query(None, dict(r_max=r, exclude_ii=True)).toNeighborList()
+    _, off, pj, d = oracle.ball_query(b, x, r)
+    assert np.array_equal(nl.segments.cpu().numpy(), off)
+    assert np.array_equal(nl.point_indices.cpu().numpy(), pj)
+    assert np.allclose(nl.distances.cpu().numpy(), d, atol=1e-5)
+def rdf(b, x, bins, r, rc):
+    h = fgb.RDF(bins, r); h.compute(fgb.NeighborQuery(b, dev(x), r_cell=rc))
+    assert np.array_equal(h.bin_counts, oracle.rdf_counts(b, x, bins, r))
+b = W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15)
+x = W.small_random(90, 5000, b)
+ball(b, x, 2.0, 2.0); rdf(b, x, 60, 3.9, 2.0)
+w = W.c1()                                   # 3 x 3 x 3 cells, 150 points each
+ball(w.box, w.points, 4.0, 4.0); rdf(w.box, w.points, 100, 4.0, 4.0)
+c = W.Box.cube(20.0)
+blob = (np.random.default_rng(7).normal(size=(900, 3)) * 0.3).astype(np.float32)
+xd = np.concatenate([W.small_random(50, 2000, c), blob, blob[:50]]).astype(np.float32)
+ball(c, xd, 1.5, 1.5); rdf(c, xd, 100, 3.0, 3.0)
+k = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
+_, kj, _ = oracle.knn(b, x, 12)
+assert np.array_equal(k.point_indices.cpu().numpy().reshape(-1, 12), kj[:, :12])
+print('ok')
+"""
+
+
+@pytest.mark.parametrize("switch", ["FGB_THREAD_KERNELS", "FGB_TILE_KERNELS"])
+def test_kernel_family_switches(switch):
     import os
     import subprocess
     import sys
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    code = (
-        "import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb\n"
-        "b = W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15)\n"
-        "x = W.small_random(90, 5000, b)\n"
-        "nq = fgb.NeighborQuery(b, torch.from_numpy(x).cuda(), r_cell=2.0)\n"
-        "nl = nq.query(None, dict(r_max=2.0, exclude_ii=True)).toNeighborList()\n"
-        "_, off, pj, d = oracle.ball_query(b, x, 2.0)\n"
-        "assert np.array_equal(nl.segments.cpu().numpy(), off)\n"
-        "assert np.array_equal(nl.point_indices.cpu().numpy(), pj)\n"
-        "assert np.allclose(nl.distances.cpu().numpy(), d, atol=1e-5)\n"
-        "print('ok')\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, FGB_THREAD_KERNELS="1", PYTHONPATH=root)
-    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
-    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
+    env = dict(os.environ, PYTHONPATH=root)
+    env[switch] = "1"
+    r = subprocess.run([sys.executable, "-c", KERNEL_SWITCH_CHECKS], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]
