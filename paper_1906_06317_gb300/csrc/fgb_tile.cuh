@@ -173,6 +173,38 @@ __device__ __forceinline__ void tile_stage(const TileArgs &a, const TS &ts, int 
         default: CALL(1); break;      \
     }
 
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Bounding box of one point per lane (lanes with valid == false take no part), reduced
+// over the warp: every lane gets the box.
+__device__ __forceinline__ void warp_box(float x, float y, float z, bool valid, float3 &lo, float3 &hi) {
+    lo = valid ? make_float3(x, y, z) : make_float3(INFINITY, INFINITY, INFINITY);
+    hi = valid ? make_float3(x, y, z) : make_float3(-INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+}
+
+// Squared distance from a point to a box (0 inside), in FP32.  Used to drop candidates
+// that no query of a box can reach: for pairs that matter it is within a few ulps of the
+// exact distance, so a slack factor of 1 + 1e-5 on the reach keeps every one of them.
+__device__ __forceinline__ float box_dist2(float3 lo, float3 hi, float x, float y, float z) {
+    const float dx = fmaxf(fmaxf(lo.x - x, x - hi.x), 0.f);
+    const float dy = fmaxf(fmaxf(lo.y - y, y - hi.y), 0.f);
+    const float dz = fmaxf(fmaxf(lo.z - z, z - hi.z), 0.f);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 // Kernel arguments for a self query of radius R on plan p (host).
 TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude);
 

@@ -266,6 +266,7 @@ template <int NS>
 __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_constant__ RdfTileArgs a) {
     __shared__ TileStencilT<NS> sts[kRdfTileWarps];
     __shared__ float4 sq[kRdfTileWarps][kRdfTileQ];
+    __shared__ float4 sbuf[kRdfTileWarps][64];  // candidates kept after the box test
     extern __shared__ uint32_t shist[];  // kRdfTileWarps * bins
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *h = shist + warp * a.bins;
@@ -273,6 +274,11 @@ __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_co
     __syncwarp();
     TileStencilT<NS> &ts = sts[warp];
     float4 *qs = sq[warp];
+    float4 *buf = sbuf[warp];
+    const unsigned lt = lanemask_lt();
+    // a candidate farther than this (squared, FP32, with slack for the rounding of the
+    // box distance) from the queries' bounding box cannot be in range of any of them
+    const float reach2 = a.P.rmax_hi * (1.0f + 1e-5f);
     uint64_t tests = 0;  // pair tests since the last flush bound every private count
     for (;;) {
         unsigned A = 0;
@@ -292,18 +298,57 @@ __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_co
             __syncwarp();
             if (lane < nq) qs[lane] = __ldg(a.t.pts + begA + qb + lane);
             __syncwarp();
-            for (int base = 0; base < total; base += 32) {
+            float3 blo, bhi;
+            {
+                const float4 q = qs[lane < nq ? lane : 0];
+                warp_box(q.x, q.y, q.z, lane < nq, blo, bhi);
+            }
+            // A's own points first (they pair only with earlier queries)
+            for (int base = 0; base < nA; base += 32) {
                 if (tests > 0xffffffffull - 32 * kRdfTileQ) {
                     rdf_tile_flush(h, a.bins, a.hist, a.weight);
                     tests = 0;
                 }
                 tests += 32u * (unsigned)nq;
                 const int k = base + lane;
+                const TileCand c = tile_load(a.t, ts, n, nA, k);
+                rdf_tile_rounds<true>(a, qs, nq, c, k < nA ? k - qb : 0, h);
+            }
+            // the other cells: candidates out of reach of the whole pass are dropped, the
+            // rest are packed into full chunks (ballot + popc) before the query rounds
+            int cnt = 0;
+            for (int base = nA; base < total; base += 32) {
+                const int k = base + lane;
                 const TileCand c = tile_load(a.t, ts, n, total, k);
-                if (base < nA)
-                    rdf_tile_rounds<true>(a, qs, nq, c, k < nA ? k - qb : 0x7fffffff, h);
-                else
-                    rdf_tile_rounds<false>(a, qs, nq, c, 0, h);
+                const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) buf[cnt + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+                cnt += __popc(m);
+                if (cnt >= 32) {
+                    __syncwarp();
+                    if (tests > 0xffffffffull - 32 * kRdfTileQ) {
+                        rdf_tile_flush(h, a.bins, a.hist, a.weight);
+                        tests = 0;
+                    }
+                    tests += 32u * (unsigned)nq;
+                    const float4 e = buf[lane];
+                    TileCand ck;
+                    ck.x = e.x, ck.y = e.y, ck.z = e.z, ck.j = __float_as_int(e.w), ck.p = 0, ck.o = 0;
+                    rdf_tile_rounds<false>(a, qs, nq, ck, 0, h);
+                    const float4 rest = buf[32 + lane];
+                    __syncwarp();
+                    if (lane < cnt - 32) buf[lane] = rest;
+                    __syncwarp();
+                    cnt -= 32;
+                }
+            }
+            if (cnt > 0) {
+                __syncwarp();
+                tests += 32u * (unsigned)nq;
+                const float4 e = lane < cnt ? buf[lane] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+                TileCand ck;
+                ck.x = e.x, ck.y = e.y, ck.z = e.z, ck.j = __float_as_int(e.w), ck.p = 0, ck.o = 0;
+                rdf_tile_rounds<false>(a, qs, nq, ck, 0, h);
             }
         }
     }

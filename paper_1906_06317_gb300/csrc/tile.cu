@@ -55,7 +55,7 @@ __device__ __forceinline__ uint32_t count_chunk_exact(const TileArgs &a, const f
 template <int NS>
 __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, uint32_t *__restrict__ counts) {
     __shared__ TileStencilT<NS> sts[kTileWarps];
-    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ float4 sstage[kTileWarps][64];  // kept candidates, packed
     const int warp = threadIdx.x >> 5;
     const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
     const float lo = a.band.lo, hi = a.band.hi;
+    const float reach2 = hi * (1.0f + 1e-5f);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
     int nesc = 0;
     for (int qb = 0; qb < nA; qb += 32) {
         const int nq = min(32, nA - qb);
@@ -79,8 +82,23 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
         const int excl = a.exclude ? i : -1;
         const float4 *sp = stage + L.g;
         uint32_t cnt = 0;
-        for (int base = 0; base < total; base += 32) {
-            tile_stage(a, ts, n, total, base, stage);
+        // candidates out of reach of the pass's bounding box are dropped; the rest are
+        // packed into full chunks (ballot + popc) before the rounds
+        float3 blo, bhi;
+        warp_box(Q.x, Q.y, Q.z, qact, blo, bhi);
+        int kept = 0;
+        for (int base = 0; base < total || kept > 0; base += 32) {
+            if (base < total) {
+                const TileCand c = tile_load(a, ts, n, total, base + lane);
+                const bool keep = base + lane < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) stage[kept + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+                kept += __popc(m);
+                if (kept < 32 && base + 32 < total) continue;
+            }
+            // a full chunk, or the last partial one padded with far entries
+            if (kept < 32 && lane >= kept) stage[lane] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
+            __syncwarp();
             bool band = false;
 #define FGB_CNT(GV) cnt += count_chunk<GV>(sp, Q, lo, hi, band)
             FGB_TILE_DISPATCH_G(L.G, FGB_CNT)
@@ -90,7 +108,12 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
                 FGB_TILE_DISPATCH_G(L.G, FGB_CNTX)
 #undef FGB_CNTX
             }
+            const float4 rest = stage[32 + lane];
             __syncwarp();
+            if (lane < kept - 32) stage[lane] = rest;
+            __syncwarp();
+            kept = max(kept - 32, 0);
+            if (base >= total) break;
         }
         for (int o = L.qpl; o < 32; o <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (L.g == 0 && qact) {
@@ -314,46 +337,55 @@ __device__ __noinline__ void write_chunk_exact(const TileArgs &a, const float4 *
     }
 }
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 // FP64 decision of a pair inside the band: its stored distance, or -1 when outside.
 __device__ __noinline__ float write_band_pair(const TileArgs *ap, int i, int j) {
     const double e = exact_r2_idx(ap->bd, ap->p_orig, i, ap->p_orig, j);
     return e < ap->T ? (float)sqrt(e) : -1.f;
 }
 
-// Cells whose stencil holds at most kWriteStage candidates: all of them are staged once
-// (shifted into A's frame), then the queries of A are taken in pairs (two independent
-// chains for the scheduler) with one candidate per lane.  Hits take consecutive row
-// slots in candidate order (ballot + popc, no atomics); both rows are sorted by one
-// interleaved network and stored before the next pair, so the warp needs kWriteQN = 2
-// rows.  A's own points are the centre entry of the stencil, whose offset is zero, so
-// the staged copy is the query itself.
+// Cells whose stencil holds at most kWriteStage candidates: the candidates within reach
+// of the bounding box of A's points are staged once, packed and shifted into A's frame
+// (a quarter of a 27-cell stencil of width r_max lies beyond that reach); then the
+// queries of A are taken in pairs (two independent chains for the scheduler) with one
+// candidate per lane.  Hits take consecutive row slots in candidate order (ballot +
+// popc, no atomics); both rows are sorted by one interleaved network and stored before
+// the next pair, so the warp needs kWriteQN = 2 rows.
 template <class TS>
-__device__ __forceinline__ void write_cell_staged(const TileArgs &a, const TS &ts, int n, int total, int nA,
-                                                  float4 *stg, uint2 *row, const int64_t *__restrict__ seg,
+__device__ __forceinline__ void write_cell_staged(const TileArgs &a, const TS &ts, int n, int total, int begA,
+                                                  int nA, float4 *stg, uint2 *row, const int64_t *__restrict__ seg,
                                                   const uint32_t *__restrict__ counts, int cap, bool packable,
                                                   int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
                                                   float *__restrict__ d_out) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    // bounding box of A's points (the queries)
+    float3 blo = make_float3(INFINITY, INFINITY, INFINITY), bhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    for (int t0 = 0; t0 < nA; t0 += 32) {
+        const float4 q = __ldg(a.pts + begA + min(t0 + lane, nA - 1));
+        float3 l, h;
+        warp_box(q.x, q.y, q.z, t0 + lane < nA, l, h);
+        blo = make_float3(fminf(blo.x, l.x), fminf(blo.y, l.y), fminf(blo.z, l.z));
+        bhi = make_float3(fmaxf(bhi.x, h.x), fmaxf(bhi.y, h.y), fmaxf(bhi.z, h.z));
+    }
+    // stage the candidates within reach of that box, packed (ballot + popc)
+    const float reach2 = a.band.hi * (1.0f + 1e-5f);
+    int kept = 0;
     for (int base = 0; base < total; base += 32) {
         const TileCand c = tile_load(a, ts, n, total, base + lane);
-        stg[base + lane] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+        const bool keep = base + lane < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) stg[kept + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+        kept += __popc(m);
     }
+    for (int k = kept + lane; k < ((kept + 31) & ~31); k += 32) stg[k] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
     __syncwarp();
-    const int nch = (total + 31) >> 5;
-    const int centre = ts.pre[(n - 1) / 2];
+    const int nch = (kept + 31) >> 5;
     const float lo = a.band.lo, hi = a.band.hi;
-    const unsigned lt = lanemask_lt();
     uint2 *rowb = row + cap;
     for (int q = 0; q < nA; q += 2) {
         const bool two = q + 1 < nA;
-        const float4 Qa = stg[centre + q];
-        const float4 Qb = two ? stg[centre + q + 1] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const float4 Qa = __ldg(a.pts + begA + q);
+        const float4 Qb = two ? __ldg(a.pts + begA + q + 1) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
         const int ia = __float_as_int(Qa.w), ib = __float_as_int(Qb.w);
         const int xa = a.exclude ? ia : -1, xb = a.exclude ? ib : -1;
         uint32_t na = 0, nb = 0;
@@ -472,7 +504,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_
     const int total = ts.pre[n];
     unsigned char *region = tsm + (size_t)warp * write_warp_bytes(cap);
     if (total <= kWriteStage)
-        write_cell_staged(a, ts, n, total, nA, reinterpret_cast<float4 *>(region),
+        write_cell_staged(a, ts, n, total, begA, nA, reinterpret_cast<float4 *>(region),
                           reinterpret_cast<uint2 *>(region + kWriteStage * sizeof(float4)), seg, counts, cap,
                           packable != 0, qi_out, pj_out, d_out);
     else
