@@ -271,6 +271,45 @@ int fgb_steinhardt_state(const fgb_steinhardt *st, const float **qlm, const int3
 int fgb_steinhardt_backward(fgb_steinhardt *st, fgb_nq *nq, const fgb_nlist *nlist, const float *q,
                             float upstream, float *grad_out, void *stream);
 
+/*
+ * W_l, the third-order invariant of the Steinhardt order parameters (order module,
+ * Section "Analysis Modules"; Steinhardt, Nelson and Ronchetti 1983), from the Q_lm held
+ * by the last fgb_steinhardt_compute (or fgb_steinhardt_average):
+ *   w_l(i) = sum_{m1+m2+m3=0} (l l l; m1 m2 m3) Q_lm1(i) Q_lm2(i) Q_lm3(i)   (real),
+ * with Wigner 3j symbols and Q_{l,-m} = (-1)^m conj(Q_lm).  normalize != 0 divides by
+ * (sum_m |Q_lm(i)|^2)^{3/2} (0 for a particle without neighbors).  w_out: float32 (n)
+ * device.  Errors: INVALID_ARG (no compute yet).  Asynchronous on `stream` after the
+ * first call for a given l (which uploads the 3j table once).
+ */
+int fgb_steinhardt_wl(fgb_steinhardt *st, int32_t normalize, float *w_out, void *stream);
+
+/*
+ * Neighbor-averaged q_l (Lechner and Dellago 2008; freud's `average` option):
+ *   Qbar_lm(i) = (Q_lm(i) + sum_{k in nb(i)} Q_lm(k)) / (n_i + 1),
+ *   qbar_l(i) = sqrt(4 pi / (2l+1) sum_m |Qbar_lm(i)|^2),
+ * nb(i) from `nlist` (a self list over the points of the last compute).  The state then
+ * holds Qbar_lm: fgb_steinhardt_wl gives the averaged w_l, fgb_steinhardt_state returns
+ * Qbar_lm, and fgb_steinhardt_backward returns UNSUPPORTED until the next compute.
+ * q_out: float32 (n) device.  Asynchronous on `stream`.
+ */
+int fgb_steinhardt_average(fgb_steinhardt *st, const fgb_nlist *nlist, float *q_out, void *stream);
+
+/* ------------------------------------------------------------ LocalDescriptors */
+
+/*
+ * Spherical harmonics of every bond of a NeighborList (environment module's
+ * LocalDescriptors, Section "Analysis Modules"; global orientation): for pair e with
+ * query point i and point j, the minimum-image bond d = x_j - q_i and, for l = 0..l_max,
+ * Y_lm(d / |d|) with m = -l..l (negative_m != 0) or m = 0..l, in that order, the same
+ * orthonormal harmonics with the Condon-Shortley phase as the Steinhardt parameters
+ * (all zero for coincident points).  out: complex64 as float32 pairs, (n_pairs, n_sph, 2)
+ * device, n_sph = (l_max+1)^2 or (l_max+1)(l_max+2)/2.  query_points NULL means the
+ * points.  Errors: INVALID_ARG (l_max outside [0, 12], NULL arrays, degenerate box).
+ * Asynchronous on `stream`.
+ */
+int fgb_local_descriptors(const fgb_box *box, const float *points, const float *query_points,
+                          const fgb_nlist *nlist, int32_t l_max, int32_t negative_m, float *out, void *stream);
+
 /* -------------------------------------------------------------- batched frames */
 
 typedef struct fgb_batch_params {

@@ -49,6 +49,7 @@ def lib():
         L.orc_rdf.argtypes = [_P, _P, _I64, _P, _P, _P, _P, _I64, _I64, _I32, _D, _D, _I32, _P]
         L.orc_ylm.argtypes = [_I32, _I32, _D, _D, _D, _P, _P]
         L.orc_steinhardt_ylm.argtypes = [_P, _P, _I64, _P, _P, _I32, _P, _I64, _P, _P]
+        L.orc_descriptors.argtypes = [_P, _P, _P, _I64, _P, _P, _I32, _I32, _P]
         L.orc_steinhardt_legendre.argtypes = [_P, _P, _I64, _P, _P, _I32, _P, _I64, _P]
         L.orc_q_grad.argtypes = [_P, _P, _I64, _P, _P, _I32, _P]
         _lib = L
@@ -316,3 +317,100 @@ def q_grad(box, points, offsets, pj, l):
     g = np.zeros((len(pts), 3))
     _check(lib().orc_q_grad(_ptr(b), _ptr(pts), len(pts), _ptr(off), _ptr(j), int(l), _ptr(g)), "q_grad")
     return g
+
+
+# ------------------------------------------------------------- Steinhardt variants
+
+
+def wigner3j(j1, j2, j3, m1, m2, m3) -> float:
+    """Wigner 3j symbol from Racah's formula, summed exactly in rational arithmetic.
+
+    (j1 j2 j3; m1 m2 m3) = (-1)^(j1-j2-m3) sqrt(D (j1+m1)!(j1-m1)!(j2+m2)!(j2-m2)!(j3+m3)!(j3-m3)!)
+                           * sum_k (-1)^k / [k! (j3-j2+k+m1)! (j3-j1+k-m2)! (j1+j2-j3-k)! (j1-k-m1)! (j2-k+m2)!],
+    D = (j1+j2-j3)!(j1-j2+j3)!(-j1+j2+j3)!/(j1+j2+j3+1)!; zero unless m1+m2+m3 = 0 and the
+    triangle and |m| <= j conditions hold.
+    """
+    from fractions import Fraction
+    f = math.factorial
+    if m1 + m2 + m3 != 0 or j3 < abs(j1 - j2) or j3 > j1 + j2:
+        return 0.0
+    if abs(m1) > j1 or abs(m2) > j2 or abs(m3) > j3:
+        return 0.0
+    d = Fraction(f(j1 + j2 - j3) * f(j1 - j2 + j3) * f(-j1 + j2 + j3), f(j1 + j2 + j3 + 1))
+    pre2 = d * f(j1 + m1) * f(j1 - m1) * f(j2 + m2) * f(j2 - m2) * f(j3 + m3) * f(j3 - m3)
+    s = Fraction(0)
+    for k in range(0, j1 + j2 - j3 + 1):
+        args = (k, j3 - j2 + k + m1, j3 - j1 + k - m2, j1 + j2 - j3 - k, j1 - k - m1, j2 - k + m2)
+        if min(args) < 0:
+            continue
+        den = 1
+        for a in args:
+            den *= f(a)
+        s += Fraction((-1) ** k, den)
+    val2 = pre2 * s * s
+    sign = (-1) ** ((j1 - j2 - m3) % 2) * (1 if s >= 0 else -1)
+    return sign * math.sqrt(float(val2))
+
+
+def _full_qlm(Q, l):
+    """(n, l+1) complex Q_lm, m >= 0 -> (n, 2l+1) for m = -l..l."""
+    n = Q.shape[0]
+    F = np.zeros((n, 2 * l + 1), dtype=complex)
+    for m in range(l + 1):
+        F[:, l + m] = Q[:, m]
+        F[:, l - m] = (-1) ** m * np.conj(Q[:, m])
+    return F
+
+
+def wl_from_qlm(Q, l, normalize=True):
+    """W_l per particle from Q_lm (Steinhardt, Nelson and Ronchetti 1983), FP64."""
+    F = _full_qlm(np.asarray(Q), l)
+    w = np.zeros(F.shape[0])
+    for m1 in range(-l, l + 1):
+        for m2 in range(-l, l + 1):
+            m3 = -m1 - m2
+            if abs(m3) > l:
+                continue
+            c = wigner3j(l, l, l, m1, m2, m3)
+            w += c * np.real(F[:, l + m1] * F[:, l + m2] * F[:, l + m3])
+    if normalize:
+        s = np.sum(np.abs(F) ** 2, axis=1)
+        w = np.where(s > 0, w / np.where(s > 0, s, 1.0) ** 1.5, 0.0)
+    return w
+
+
+def wl(box, points, offsets, pj, l, normalize=True):
+    _, Q = steinhardt(box, points, offsets, pj, l, with_qlm=True)
+    return wl_from_qlm(Q, l, normalize)
+
+
+def steinhardt_average(box, points, offsets, pj, l, with_qlm=False):
+    """Neighbor-averaged q_l (Lechner and Dellago 2008): Qbar_lm(i) = (Q_lm(i) + sum over
+    the neighbors k of Q_lm(k)) / (n_i + 1), qbar = sqrt(4 pi/(2l+1) sum_m |Qbar_lm|^2)."""
+    _, Q = steinhardt(box, points, offsets, pj, l, with_qlm=True)
+    off, j = _nl(offsets, pj)
+    n = len(off) - 1
+    S = Q.copy()
+    for i in range(n):
+        a, z = off[i], off[i + 1]
+        if z > a:
+            S[i] += Q[j[a:z]].sum(axis=0)
+    S /= (np.diff(off) + 1)[:, None]
+    w = np.ones(l + 1)
+    w[1:] = 2.0
+    q = np.sqrt(4.0 * math.pi / (2 * l + 1) * np.sum(w * np.abs(S) ** 2, axis=1))
+    return (q, S) if with_qlm else q
+
+
+def local_descriptors(box, points, qi, pj, l_max, negative_m=True, query_points=None):
+    """(n_pairs, n_sph) complex Y_lm of every bond, l <= l_max (m = -l..l or 0..l)."""
+    b = _box(box)
+    pts = _pts(points)
+    qpts = pts if query_points is None else _pts(query_points)
+    qi = np.ascontiguousarray(np.asarray(qi, np.int64))
+    pj = np.ascontiguousarray(np.asarray(pj, np.int64))
+    nsph = (l_max + 1) ** 2 if negative_m else (l_max + 1) * (l_max + 2) // 2
+    out = np.zeros((len(qi), nsph, 2))
+    _check(lib().orc_descriptors(_ptr(b), _ptr(pts), _ptr(qpts), len(qi), _ptr(qi), _ptr(pj), int(l_max),
+                                 int(bool(negative_m)), _ptr(out)), "descriptors")
+    return out[..., 0] + 1j * out[..., 1]

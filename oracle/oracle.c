@@ -658,3 +658,29 @@ int orc_q_grad(const double *b, const double *pts, int64_t n, const int64_t *off
     free(rr);
     return ORC_OK;
 }
+
+/* Per-bond spherical harmonics (LocalDescriptors, global orientation): for each pair e,
+ * the minimum-image bond d = x_j - q_i and Y_lm(d) for l = 0..lmax with m = -l..l
+ * (negative_m) or m = 0..l, in that order, written as (re, im) pairs; coincident points
+ * give zeros. */
+int orc_descriptors(const double *b, const double *pts, const double *qpts, int64_t m, const int64_t *qi,
+                    const int64_t *pj, int lmax, int negative_m, double *out) {
+    if (lmax < 0 || lmax > 16) return ORC_ERR_ARG;
+    int nsph = negative_m ? (lmax + 1) * (lmax + 1) : (lmax + 1) * (lmax + 2) / 2;
+    for (int64_t e = 0; e < m; ++e) {
+        double d[3];
+        min_image(b, qpts + 3 * qi[e], pts + 3 * pj[e], d);
+        double r2 = r2_of(d);
+        int o = 0;
+        for (int l = 0; l <= lmax; ++l) {
+            for (int mm = negative_m ? -l : 0; mm <= l; ++mm) {
+                double yr = 0.0, yi = 0.0;
+                if (r2 > 0.0) orc_ylm(l, mm, d[0], d[1], d[2], &yr, &yi);
+                out[(e * nsph + o) * 2 + 0] = yr;
+                out[(e * nsph + o) * 2 + 1] = yi;
+                ++o;
+            }
+        }
+    }
+    return ORC_OK;
+}

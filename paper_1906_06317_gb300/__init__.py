@@ -88,6 +88,9 @@ _SIGS = {
     "fgb_steinhardt_compute": (_I32, [_P, _P, _P, ctypes.POINTER(fgb_query_args), _P, _P]),
     "fgb_steinhardt_state": (_I32, [_P, _PP, _PP]),
     "fgb_steinhardt_backward": (_I32, [_P, _P, _P, _P, _F, _P, _P]),
+    "fgb_steinhardt_wl": (_I32, [_P, _I32, _P, _P]),
+    "fgb_steinhardt_average": (_I32, [_P, _P, _P, _P]),
+    "fgb_local_descriptors": (_I32, [ctypes.POINTER(fgb_box), _P, _P, _P, _I32, _I32, _P, _P]),
     "fgb_batch_create": (_I32, [_I32, _P, ctypes.POINTER(fgb_box), ctypes.POINTER(fgb_batch_params), _P, _PP]),
     "fgb_batch_destroy": (None, [_P]),
     "fgb_batch_run": (_I32, [_P, _P, _P]),
@@ -395,7 +398,7 @@ class RDF:
         if query_points is not None:
             qpt = _need_cuda(query_points, name="query_points")
             qp, n_q = qpt.data_ptr(), qpt.shape[0]
-        _check(lib().fgb_rdf_compute(self._h, nq._h, qp, n_q, nl._h if nl else None, int(bool(reset)), _stream()))
+        _check(lib().fgb_rdf_compute(self._h, nq._h, qp, n_q, nl._h if nl is not None else None, int(bool(reset)), _stream()))
         self._nq = nq
         return self
 
@@ -434,7 +437,8 @@ class RDF:
 
 
 class Steinhardt:
-    """Steinhardt q_l per particle (freud order.Steinhardt, no averaging / no W_l)."""
+    """Steinhardt q_l per particle (freud order.Steinhardt); wl() gives W_l and average()
+    the neighbor-averaged q_l from the same Q_lm."""
 
     def __init__(self, l: int):
         self.l = int(l)
@@ -455,7 +459,7 @@ class Steinhardt:
             else:
                 qa = fgb_query_args(float(d.get("r_max", 0.0)), 0, int(bool(d.get("exclude_ii", True))))
         q = torch.empty(nq.n_points, dtype=torch.float32, device="cuda")
-        _check(lib().fgb_steinhardt_compute(self._h, nq._h, nl._h if nl else None,
+        _check(lib().fgb_steinhardt_compute(self._h, nq._h, nl._h if nl is not None else None,
                                             ctypes.byref(qa) if qa is not None else None, q.data_ptr(), _stream()))
         self.particle_order = q
         self._nq, self._nl = nq, nl
@@ -471,6 +475,22 @@ class Steinhardt:
         _check(lib().fgb_steinhardt_state(self._h, ctypes.byref(p), ctypes.byref(c)))
         return _view(c.value, (self._nq.n_points,), torch.int32, self._o)
 
+    def wl(self, normalize: bool = True) -> torch.Tensor:
+        """W_l per particle from the current Q_lm (normalised by |Q_l|^3 unless normalize=False)."""
+        w = torch.empty(self._nq.n_points, dtype=torch.float32, device="cuda")
+        _check(lib().fgb_steinhardt_wl(self._h, int(bool(normalize)), w.data_ptr(), _stream()))
+        return w
+
+    def average(self, neighbors: "NeighborList" = None) -> torch.Tensor:
+        """Neighbor-averaged q_l (Lechner-Dellago); the state then holds the averaged Q_lm."""
+        nl = neighbors if neighbors is not None else self._nl
+        if nl is None:
+            raise FGBError(ERR_UNSUPPORTED, "averaging needs the neighbors as a NeighborList")
+        q = torch.empty(self._nq.n_points, dtype=torch.float32, device="cuda")
+        _check(lib().fgb_steinhardt_average(self._h, nl._h, q.data_ptr(), _stream()))
+        self.particle_order = q
+        return q
+
     def backward(self, upstream: float = 1.0) -> torch.Tensor:
         """d(upstream * mean_i q_l(i)) / d positions, neighbor list of the last compute fixed."""
         if self._nl is None:
@@ -480,6 +500,30 @@ class Steinhardt:
                                              float(upstream), g.data_ptr(), _stream()))
         return g
 
+
+
+class LocalDescriptors:
+    """Spherical harmonics Y_lm (l <= l_max) of every bond of a NeighborList (freud
+    environment.LocalDescriptors, global orientation): sph is (n_pairs, n_sph) complex64,
+    m = -l..l per l when negative_m (else m = 0..l)."""
+
+    def __init__(self, l_max: int, negative_m: bool = True):
+        self.l_max, self.negative_m = int(l_max), bool(negative_m)
+        self.sph = None
+
+    @property
+    def num_sphs(self) -> int:
+        return (self.l_max + 1) ** 2 if self.negative_m else (self.l_max + 1) * (self.l_max + 2) // 2
+
+    def compute(self, system, neighbors: NeighborList, query_points=None):
+        nq = _as_nq(system)
+        out = torch.empty((neighbors.n_pairs, self.num_sphs, 2), dtype=torch.float32, device="cuda")
+        qp = None if query_points is None else _need_cuda(query_points, name="query_points")
+        b = nq.box._c()
+        _check(lib().fgb_local_descriptors(ctypes.byref(b), nq.points.data_ptr(), None if qp is None else qp.data_ptr(),
+                                           neighbors._h, self.l_max, int(self.negative_m), out.data_ptr(), _stream()))
+        self.sph = torch.view_as_complex(out)
+        return self
 
 
 class Q6Mean(torch.autograd.Function):

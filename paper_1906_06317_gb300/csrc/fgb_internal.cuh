@@ -133,6 +133,20 @@ struct fgb_nq {
     int bvh_moved;         // kind 1: wrapping moved some point
 };
 
+// Steinhardt state (steinhardt.cu, order.cu): per-particle Q_lm, m = 0..l, and the
+// neighbor counts of the last compute.
+struct fgb_steinhardt {
+    int l;
+    int64_t n;
+    float2 *Q;                  // (n, l+1): (1/n_i) sum_j Y_lm, or its neighbor average
+    int32_t *nn;
+    const fgb_nlist *last_nlist;
+    cudaStream_t stream;
+    int averaged;               // Q holds the neighbor-averaged Qbar_lm
+    float2 *Qtmp;               // (n, l+1) scratch of the averaging
+    float *w3j;                 // (2l+1)^2 Wigner 3j table (l l l; m1 m2 -m1-m2)
+};
+
 struct fgb_nlist {
     int64_t n_query, n_points, n_pairs;
     int32_t *qi, *pj, *counts;

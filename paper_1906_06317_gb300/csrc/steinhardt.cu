@@ -196,14 +196,6 @@ struct RunBwd {
 
 }  // namespace fgb
 
-struct fgb_steinhardt {
-    int l;
-    int64_t n;
-    float2 *Q;
-    int32_t *nn;
-    const fgb_nlist *last_nlist;
-    cudaStream_t stream;
-};
 
 using namespace fgb;
 
@@ -224,10 +216,13 @@ extern "C" void fgb_steinhardt_destroy(fgb_steinhardt *st) {
     if (!st) return;
     dfree(st->Q, st->stream);
     dfree(st->nn, st->stream);
+    dfree(st->Qtmp, st->stream);
+    dfree(st->w3j, st->stream);
     delete st;
 }
 
 static int st_ensure(fgb_steinhardt *st, int64_t n, cudaStream_t s) {
+    st->averaged = 0;
     if (st->n != n || !st->Q) {
         dfree(st->Q, s);
         dfree(st->nn, s);
@@ -304,6 +299,7 @@ extern "C" int fgb_steinhardt_backward(fgb_steinhardt *st, fgb_nq *nq, const fgb
     clear_error();
     if (!st || !nq || !nlist || (nq->n > 0 && (!q || !grad_out))) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
     if (!st->Q || st->n != nq->n) return fail(FGB_ERR_INVALID_ARG, "call fgb_steinhardt_compute first");
+    if (st->averaged) return fail(FGB_ERR_UNSUPPORTED, "the backward pass is for q_l, not the averaged q_l");
     if (nlist->n_query != nq->n || nlist->n_points != nq->n)
         return fail(FGB_ERR_INVALID_ARG, "backward needs a self neighbor list over the same points");
     cudaStream_t s = as_stream(stream);

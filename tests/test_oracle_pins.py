@@ -304,3 +304,135 @@ def test_q_gradient_finite_differences():
             fm = oracle.steinhardt(w.box, xm, o, pj, l, which=affected).sum() / n
             fd = (fp - fm) / (2 * h)
             assert fd == pytest.approx(g[k, c], rel=1e-4, abs=1e-4 * np.abs(g).max())
+
+
+# ------------------------------------------------- Wigner 3j, W_l, averaged q_l, Y_lm
+
+
+def _w3j_all_zero_m(l1, l2, l3):
+    """(l1 l2 l3; 0 0 0) by its closed form: 0 for odd L = l1+l2+l3, else
+    (-1)^(L/2) sqrt[(L-2l1)!(L-2l2)!(L-2l3)!/(L+1)!] (L/2)!/[(L/2-l1)!(L/2-l2)!(L/2-l3)!]."""
+    L = l1 + l2 + l3
+    if L % 2:
+        return 0.0
+    f = math.factorial
+    g = L // 2
+    return (-1) ** g * math.sqrt(f(L - 2 * l1) * f(L - 2 * l2) * f(L - 2 * l3) / f(L + 1)) * f(g) / (
+        f(g - l1) * f(g - l2) * f(g - l3))
+
+
+def test_wigner3j_closed_forms_and_symmetries():
+    for l in range(0, 9):
+        for m in range(-l, l + 1):  # (l l 0; m -m 0) = (-1)^(l-m) / sqrt(2l+1)
+            assert oracle.wigner3j(l, l, 0, m, -m, 0) == pytest.approx((-1) ** (l - m) / math.sqrt(2 * l + 1),
+                                                                        abs=1e-14)
+    for l1, l2, l3 in [(4, 4, 4), (6, 6, 6), (2, 3, 3), (5, 6, 7), (12, 12, 12), (3, 4, 5)]:
+        assert oracle.wigner3j(l1, l2, l3, 0, 0, 0) == pytest.approx(_w3j_all_zero_m(l1, l2, l3), abs=1e-14)
+    # column permutations: cyclic ones keep the value, odd ones and m -> -m give (-1)^L
+    rng = np.random.default_rng(1)
+    for _ in range(40):
+        l1, l2 = rng.integers(0, 7, 2)
+        l3 = int(rng.integers(abs(l1 - l2), l1 + l2 + 1))
+        m1 = int(rng.integers(-l1, l1 + 1))
+        m2 = int(rng.integers(-l2, l2 + 1))
+        m3 = -m1 - m2
+        if abs(m3) > l3:
+            continue
+        v = oracle.wigner3j(l1, l2, l3, m1, m2, m3)
+        sg = (-1) ** (l1 + l2 + l3)
+        assert oracle.wigner3j(l2, l3, l1, m2, m3, m1) == pytest.approx(v, abs=1e-14)
+        assert oracle.wigner3j(l2, l1, l3, m2, m1, m3) == pytest.approx(sg * v, abs=1e-14)
+        assert oracle.wigner3j(l1, l2, l3, -m1, -m2, -m3) == pytest.approx(sg * v, abs=1e-14)
+
+
+def test_wigner3j_orthogonality():
+    # sum_{m1,m2} (l1 l2 l3; m1 m2 m3)(l1 l2 l3'; m1 m2 m3') = delta delta / (2 l3 + 1)
+    for l1, l2 in [(3, 4), (6, 6)]:
+        for l3 in range(abs(l1 - l2), l1 + l2 + 1, 3):
+            for l3b in (l3, min(l1 + l2, l3 + 1)):
+                for m3 in (-min(l3, l3b), 0, min(l3, l3b)):
+                    s = sum(oracle.wigner3j(l1, l2, l3, m1, -m1 - m3, m3) * oracle.wigner3j(l1, l2, l3b, m1, -m1 - m3, m3)
+                            for m1 in range(-l1, l1 + 1) if abs(m1 + m3) <= l2)
+                    want = 1.0 / (2 * l3 + 1) if l3 == l3b else 0.0
+                    assert s == pytest.approx(want, abs=1e-13)
+
+
+def test_wl_single_bond_and_lattices():
+    # one bond: Q_lm = Y_lm(u), which rotates into delta_m0 sqrt((2l+1)/4pi), so the
+    # normalised W_l is (l l l; 0 0 0) for every direction
+    b = W.Box.cube(10.0)
+    rng = np.random.default_rng(4)
+    x = np.vstack([[0.0, 0.0, 0.0], rng.normal(size=(1, 3))])
+    off, pj = np.array([0, 1, 2]), np.array([1, 0])
+    for l in (2, 3, 4, 6, 8):
+        w = oracle.wl(b, x, off, pj, l)
+        assert np.allclose(w, _w3j_all_zero_m(l, l, l), atol=1e-12)
+    g = json.load(open(os.path.join(GOLDEN, "wl_lattices.json")))
+    bf = W.Box.cube(4 * 1.5874)
+    xf = W.lattice_points(None, bf, 4)
+    _, o, pj, _ = oracle.ball_query(bf, xf, 1.3)
+    for l in (4, 6):
+        assert np.allclose(oracle.wl(bf, xf, o, pj, l), g["fcc_12"][f"w{l}"], atol=g["fcc_12"]["tol"])
+    phi = (1 + 5 ** 0.5) / 2
+    v = np.array([p for s1 in (-1, 1) for s2 in (-1, 1) for p in ((0, s1, s2 * phi), (s1, s2 * phi, 0),
+                                                                  (s2 * phi, 0, s1))], np.float64)
+    v /= np.linalg.norm(v[0])
+    xi = np.vstack([[0.0, 0.0, 0.0], v])
+    oi, pi = np.array([0] + [12] * 13), np.arange(1, 13)
+    bi = W.Box.cube(20.0)
+    ico = g["icosahedral_12"]
+    assert oracle.wl(bi, xi, oi, pi, 6)[0] == pytest.approx(ico["w6"], abs=ico["tol"])
+    assert oracle.steinhardt(bi, xi, oi, pi, 6)[0] == pytest.approx(ico["q6"], abs=ico["tol"])
+
+
+def test_wl_rotation_invariant_and_unnormalised_scale():
+    b = W.Box.cube(30.0)
+    rng = np.random.default_rng(6)
+    bonds = rng.normal(size=(9, 3))
+    R = W.random_rotation(np.random.default_rng(7))
+    x1, x2 = np.vstack([[0, 0, 0], bonds]), np.vstack([[0, 0, 0], bonds @ R.T])
+    off, pj = np.array([0] + [9] * 10), np.arange(1, 10)
+    for l in (4, 6):
+        w1, w2 = oracle.wl(b, x1, off, pj, l), oracle.wl(b, x2, off, pj, l)
+        assert w1[0] == pytest.approx(w2[0], abs=1e-12)
+        _, Q = oracle.steinhardt(b, x1, off, pj, l, with_qlm=True)
+        s = np.abs(Q[0, 0]) ** 2 + 2 * np.sum(np.abs(Q[0, 1:]) ** 2)
+        assert oracle.wl(b, x1, off, pj, l, normalize=False)[0] == pytest.approx(w1[0] * s ** 1.5, abs=1e-12)
+
+
+def test_average_pair_lattice_and_isolated():
+    b = W.Box.cube(10.0)
+    # two points, each the other's only neighbor: Qbar = (Y(u) + Y(-u)) / 2, so qbar_l is
+    # 1 for even l (a single bond has q_l = 1) and 0 for odd l; a lone point gives 0
+    x = np.array([[0.0, 0.0, 0.0], [0.4, -1.0, 0.7], [4.0, 4.0, 4.0]])
+    off, pj = np.array([0, 1, 2, 2]), np.array([1, 0])
+    for l in (1, 2, 3, 4, 5, 6):
+        qb = oracle.steinhardt_average(b, x, off, pj, l)
+        want = 1.0 if l % 2 == 0 else 0.0
+        assert np.allclose(qb[:2], want, atol=1e-12) and qb[2] == 0.0
+    bf = W.Box.cube(4 * 1.5874)
+    xf = W.lattice_points(None, bf, 4)
+    _, o, pj, _ = oracle.ball_query(bf, xf, 1.3)
+    for l in (4, 6):  # every particle of a perfect crystal has the same Q_lm
+        assert np.allclose(oracle.steinhardt_average(bf, xf, o, pj, l), oracle.steinhardt(bf, xf, o, pj, l), atol=1e-12)
+
+
+def test_descriptors_addition_theorem_and_axes():
+    b = W.Box.cube(10.0)
+    x = W.small_random(8, 300, b).astype(np.float64)
+    _, o, pj, _ = oracle.ball_query(b, x, 2.0)
+    qi = np.repeat(np.arange(len(x)), np.diff(o))
+    Y = oracle.local_descriptors(b, x, qi, pj, 6)
+    k = 0
+    for l in range(7):  # sum_m |Y_lm|^2 = (2l+1)/(4 pi) for every bond
+        assert np.allclose(np.sum(np.abs(Y[:, k:k + 2 * l + 1]) ** 2, axis=1), (2 * l + 1) / (4 * math.pi),
+                           atol=1e-12)
+        k += 2 * l + 1
+    z = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 1.5], [1.5, 0.0, 0.0]])
+    Yz = oracle.local_descriptors(b, z, [0, 0], [1, 2], 3, negative_m=False)
+    k = 0
+    for l in range(4):  # along z only m = 0: sqrt((2l+1)/4pi); along x, Y_11 = -sqrt(3/8pi)
+        assert Yz[0, k] == pytest.approx(math.sqrt((2 * l + 1) / (4 * math.pi)), abs=1e-13)
+        assert np.allclose(Yz[0, k + 1:k + l + 1], 0, atol=1e-13)
+        k += l + 1
+    assert Yz[1, 2] == pytest.approx(-math.sqrt(3 / (8 * math.pi)), abs=1e-13)
