@@ -448,6 +448,24 @@ def extras(fgb, torch, dev, stream, flush):
         st6.compute(holder["nq"], neighbors=holder["nl"])
 
     comp["c2_q4_q6_ms"] = timed(c2_ql, stream, flush)
+    # Steinhardt variants on the same list: normalised W_6, q6 followed by its neighbor
+    # average, and LocalDescriptors with l_max = 6 (49 harmonics of 8 B per bond: an HBM
+    # roofline of output bytes + the 8 B index pair read per bond)
+    st6.compute(holder["nq"], neighbors=holder["nl"])
+    comp["c2_w6_ms"] = timed(lambda: st6.wl(), stream, flush)
+
+    def c2_avg():
+        st6.compute(holder["nq"], neighbors=holder["nl"])
+        st6.average(holder["nl"])
+
+    comp["c2_q6_plus_average_ms"] = timed(c2_avg, stream, flush)
+    ld = fgb.LocalDescriptors(6)
+    t_ld = timed(lambda: ld.compute(holder["nq"], holder["nl"]), stream, flush)
+    ld_bytes = holder["nl"].n_pairs * (49 * 8 + 8)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    comp["c2_descriptors_l6"] = {"ms": t_ld, "bytes": ld_bytes, "achieved_gbs": ld_bytes / t_ld / 1e6,
+                                 "frac_of_measured_hbm": ld_bytes / t_ld / 1e6 / peak}
+    ld.sph = None
     rdf2 = fgb.RDF(200, 5.0)
 
     def c2_rdf():
