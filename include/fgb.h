@@ -113,9 +113,10 @@ void fgb_nq_destroy(fgb_nq *nq);
  * subclass of NeighborQuery, benchmarked in Fig. 3): a bounding-volume hierarchy over the
  * points wrapped into the box, ordered by 30-bit Morton code (radix tree built in
  * parallel, boxes refit bottom-up).  The handle is an fgb_nq: fgb_nq_query answers ball
- * queries (r_max) with the same NeighborList, bit for bit, as the cell list (kNN returns
- * UNSUPPORTED), and fgb_rdf_compute / fgb_steinhardt_compute take it together with a
- * NeighborList.  The call synchronises `stream` once (it checks the coordinates).
+ * (r_max) and k-nearest (num_neighbors <= 32) queries with the same NeighborList, bit for
+ * bit in the pairs and their order, as the cell list (kNN with exclude_ii over separate
+ * query points needs more than k points: UNSUPPORTED otherwise), and fgb_rdf_compute /
+ * fgb_steinhardt_compute take it together with a NeighborList.  The call synchronises `stream` once (it checks the coordinates).
  * Points (and query points) must lie within two box lengths of the box centre
  * (|s - 1/2| <= 2 in fractional coordinates); points inside the box keep their exact
  * coordinates.  n may be 0.  Errors: INVALID_ARG (n < 0, points NULL with n > 0,

@@ -350,8 +350,8 @@ class NeighborQuery:
 
 class AABBQuery(NeighborQuery):
     """Tree NeighborQuery (freud locality.AABBQuery): a bounding-volume hierarchy over the
-    device points, answering ball queries (r_max) with the same NeighborList as the cell
-    list.  RDF and Steinhardt take it together with a NeighborList."""
+    device points, answering ball (r_max) and k-nearest queries with the same NeighborList
+    as the cell list.  RDF and Steinhardt take it together with a NeighborList."""
 
     def __init__(self, box, points: torch.Tensor):
         self.box = Box.from_box(box)

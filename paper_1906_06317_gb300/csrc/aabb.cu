@@ -330,6 +330,213 @@ __global__ void __launch_bounds__(128) k_bvh_write(BvhArgs a, const int64_t *__r
     if (k != want) atomicExch(a.err, 2);
 }
 
+// ------------------------------------------------------------------ k nearest
+
+// The same ranking rule as the cell-list kNN: the k+1 nearest by FP32 (r2, index) are
+// kept; the ranking is accepted when every neighbouring gap among them exceeds 2 delta
+// (delta = this route's FP32 error bound on r2 at the k-th distance, with 1.5x slack),
+// otherwise every candidate within the k-th FP32 r2 + 2 delta is ranked by its FP64 r2.
+struct BvhKnn {
+    BvhArgs b;
+    int k, m;                   // requested, per-row count (uniform)
+    float Lsum;
+    float half_wmin2;           // (w_min/2)^2, slightly reduced: a farther k-th neighbor is an error
+    int *flag_count;
+    int2 *flags;                // (query position t, threshold bits)
+    int flag_cap;
+    int32_t *qi_out, *pj_out;
+    float *d_out;
+};
+
+__device__ __forceinline__ float bvh_knn_delta(const BvhKnn &a, float R, bool moved) {
+    const float u = kU32;
+    const float e = 2.f * u * ((moved ? 59.5f : 5.5f) * a.Lsum + R);
+    const float d = 3.4641016f * R * e + 3.f * e * e + 3.f * u * (R + e) * (R + e) + 1e-12f * (R + a.Lsum) * (R + a.Lsum);
+    return 1.5f * d;
+}
+
+// Best-first walk over every reachable image: fn(j, r2) for each leaf whose node boxes
+// stayed within bound() (re-read after each leaf, so the bound may shrink).
+template <class B, class F>
+__device__ __forceinline__ void bvh_walk(const BvhArgs &a, float3 qw, float3 qf, B &&bound, F &&fn) {
+    if (a.n == 0) return;
+    int stack[kBvhStack];
+    for (int sz = -1; sz <= 1; ++sz)
+        for (int sy = -1; sy <= 1; ++sy)
+            for (int sx = -1; sx <= 1; ++sx) {
+                const float gx = qf.x + sx, gy = qf.y + sy, gz = qf.z + sz;
+                const float ex = fmaxf(fmaxf(-gx, gx - 1.f), 0.f) * a.w[0];
+                const float ey = fmaxf(fmaxf(-gy, gy - 1.f), 0.f) * a.w[1];
+                const float ez = fmaxf(fmaxf(-gz, gz - 1.f), 0.f) * a.w[2];
+                const float lb = fmaxf(ex, fmaxf(ey, ez)) * (1.f - 1e-5f);
+                if (lb * lb > bound()) continue;
+                const float qx = qw.x + (float)sx * a.bf.L[0] + (float)sy * a.bf.a2x + (float)sz * a.bf.a3x;
+                const float qy = qw.y + (float)sy * a.bf.L[1] + (float)sz * a.bf.a3y;
+                const float qz = qw.z + (float)sz * a.bf.L[2];
+                int sp = 0;
+                int node = a.n >= 2 ? 0 : ~0;
+                for (int64_t visits = 0;; ++visits) {
+                    if (visits > 2 * (int64_t)a.n) {
+                        atomicExch(a.err, 4);
+                        break;
+                    }
+                    if (node < 0) {
+                        const float4 c = __ldg(a.pts + ~node);
+                        fn(__float_as_int(c.w), r2_f32(c.x - qx, c.y - qy, c.z - qz));
+                    } else {
+                        const BvhNode *nd = a.nodes + node;
+                        const int c0 = __ldg(&nd->left), c1 = __ldg(&nd->right);
+                        float d0, d1;
+                        {
+                            float dx, dy, dz;
+                            if (c0 < 0) {
+                                const float4 p = __ldg(a.pts + ~c0);
+                                dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
+                            } else {
+                                const BvhNode *cn = a.nodes + c0;
+                                dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
+                                dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
+                                dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
+                            }
+                            d0 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
+                            if (c1 < 0) {
+                                const float4 p = __ldg(a.pts + ~c1);
+                                dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
+                            } else {
+                                const BvhNode *cn = a.nodes + c1;
+                                dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
+                                dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
+                                dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
+                            }
+                            d1 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
+                        }
+                        const float lim = bound();
+                        const bool t0 = d0 <= lim, t1 = d1 <= lim;
+                        if (t0 && t1) {
+                            const bool first0 = d0 <= d1;
+                            if (sp < kBvhStack)
+                                stack[sp++] = first0 ? c1 : c0;
+                            else
+                                atomicExch(a.err, 3);
+                            node = first0 ? c0 : c1;
+                            continue;
+                        }
+                        if (t0 || t1) {
+                            node = t0 ? c0 : c1;
+                            continue;
+                        }
+                    }
+                    // pop, skipping entries the shrinking bound has ruled out is left to the
+                    // child test of the next node (its box is re-tested when expanded)
+                    if (sp == 0) break;
+                    node = stack[--sp];
+                }
+            }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(128) k_bvh_knn(BvhKnn a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b.nq) return;
+    float3 qw, qf;
+    int fl;
+    const int i = bvh_query_point(a.b, t, qw, qf, fl);
+    if (fl & 2) {
+        atomicExch(a.b.err, 5);
+        return;
+    }
+    const int excl = a.b.exclude ? i : -1;
+    const int m = a.m;
+    float br[KT];
+    int bj[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        br[q] = INFINITY;
+        bj[q] = 0x7fffffff;
+    }
+    // bound: the (m+1)-th best so far (ties kept by the 1e-5 shrink of the box distances)
+    auto bound = [&]() { return pick<KT>(br, min(m, KT - 1)) * (1.f + 1e-5f); };
+    bvh_walk(a.b, qw, qf, bound, [&](int j, float r2) {
+        if (j == excl) return;
+        if (r2 < br[KT - 1] || (r2 == br[KT - 1] && j < bj[KT - 1])) topk_insert<KT>(br, bj, r2, j);
+    });
+    if (m == 0) return;
+    const bool moved = fl != 0 || a.b.pts_moved;
+    const float rm2 = pick<KT>(br, m - 1);
+    const float delta = bvh_knn_delta(a, sqrtf(rm2) + 1e-3f, moved);
+    if (rm2 + delta >= a.half_wmin2) {
+        atomicOr(a.b.err, 1);
+        return;
+    }
+    bool ambiguous = false;
+#pragma unroll
+    for (int q = 0; q + 1 < KT; ++q)
+        if (q < m && br[q + 1] - br[q] <= 2.f * delta) ambiguous = true;
+    const int64_t row = (int64_t)i * m;
+    if (ambiguous) {
+        const int slot = atomicAdd(a.flag_count, 1);
+        if (slot < a.flag_cap)
+            a.flags[slot] = make_int2((int)t, __float_as_int((rm2 + 2.f * delta) * 1.0000005f));
+        else
+            atomicOr(a.b.err, 2);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (q < m) {
+            a.qi_out[row + q] = i;
+            a.pj_out[row + q] = bj[q];
+            a.d_out[row + q] = sqrtf(br[q]);
+        }
+}
+
+// Flagged queries: every candidate within the threshold ranked by its FP64 r2.
+template <int KT>
+__global__ void __launch_bounds__(64) k_bvh_knn_exact(BvhKnn a) {
+    const int nflag = min(*a.flag_count, a.flag_cap);
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nflag; f += gridDim.x * blockDim.x) {
+        const int2 flg = a.flags[f];
+        float3 qw, qf;
+        int fl;
+        const int i = bvh_query_point(a.b, flg.x, qw, qf, fl);
+        const float thr = __int_as_float(flg.y);
+        const int excl = a.b.exclude ? i : -1;
+        double br[KT];
+        int bj[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            br[q] = INFINITY;
+            bj[q] = 0x7fffffff;
+        }
+        bvh_walk(a.b, qw, qf, [&]() { return thr * (1.f + 1e-5f); }, [&](int j, float r2) {
+            if (j == excl || r2 > thr) return;
+            const double e = exact_r2_idx(a.b.bd, a.b.q_orig, i, a.b.p_orig, j);
+            if (e < br[KT - 1] || (e == br[KT - 1] && j < bj[KT - 1])) {
+                double cr = e;
+                int cj = j;
+#pragma unroll
+                for (int q = 0; q < KT; ++q) {
+                    const bool less = cr < br[q] || (cr == br[q] && cj < bj[q]);
+                    const double tr = less ? br[q] : cr;
+                    const int tj = less ? bj[q] : cj;
+                    br[q] = less ? cr : br[q];
+                    bj[q] = less ? cj : bj[q];
+                    cr = tr;
+                    cj = tj;
+                }
+            }
+        });
+        const int64_t row = (int64_t)i * a.m;
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+            if (q < a.m) {
+                a.qi_out[row + q] = i;
+                a.pj_out[row + q] = bj[q];
+                a.d_out[row + q] = (float)sqrt(br[q]);
+            }
+    }
+}
+
 // ------------------------------------------------------------------ host
 
 static int grid1d(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -506,6 +713,116 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
     nl->symmetric = self && a.exclude ? 1 : 0;
     nl->kind = 0;
     dfree(dst, s);
+    return st;
+}
+
+__global__ void k_bvh_knn_rows(int64_t nq, int m, int64_t *__restrict__ seg, int32_t *__restrict__ counts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nq) seg[i] = i * (int64_t)m;
+    if (i < nq) counts[i] = m;
+}
+
+template <int KT>
+static void launch_bvh_knn(const BvhKnn &a, cudaStream_t s) {
+    {
+        FGB_KSCOPE("k_bvh_knn", s);
+        k_bvh_knn<KT><<<grid1d(a.b.nq, 128), 128, 0, s>>>(a);
+    }
+    {
+        FGB_KSCOPE("k_bvh_knn_exact", s);
+        k_bvh_knn_exact<KT><<<num_sms() * 2, 64, 0, s>>>(a);
+    }
+}
+
+int aabb_knn_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
+                   cudaStream_t s, fgb_nlist *nl) {
+    const int k = args->num_neighbors;
+    if (k > 32) return fail(FGB_ERR_UNSUPPORTED, "num_neighbors > 32 is not supported");
+    const bool self = query_points == nullptr || query_points == nq->points;
+    const bool excl = args->exclude_ii != 0;
+    const int64_t np = nq->n, nqq = self ? np : n_query;
+    if (!self && excl && np <= k)
+        return fail(FGB_ERR_UNSUPPORTED, "tree kNN with exclude_ii needs more than k points (uniform rows)");
+    const int m = (int)std::min<int64_t>(k, std::max<int64_t>(0, self && excl ? np - 1 : np));
+    const BoxHost &b = nq->box;
+    BvhKnn a;
+    memset(&a, 0, sizeof(a));
+    a.b.bf = b.f;
+    a.b.bd = b.d;
+    for (int q = 0; q < 3; ++q) a.b.w[q] = (float)b.w[q];
+    a.b.nodes = static_cast<const BvhNode *>(nq->bvh);
+    a.b.pts = nq->sorted;
+    a.b.n = (int)np;
+    a.b.p_orig = nq->points;
+    a.b.q_orig = self ? nq->points : query_points;
+    a.b.nq = nqq;
+    a.b.self = self ? 1 : 0;
+    a.b.exclude = excl ? 1 : 0;
+    a.b.pts_moved = nq->bvh_moved;
+    double Lsum = 0.0;
+    for (int c = 0; c < 3; ++c) Lsum += std::sqrt(b.M[0][c] * b.M[0][c] + b.M[1][c] * b.M[1][c] + b.M[2][c] * b.M[2][c]);
+    a.Lsum = (float)Lsum;
+    const double hw = 0.5 * b.wmin * (1.0 - 1e-4);
+    a.half_wmin2 = (float)(hw * hw);
+    a.k = k;
+    a.m = m;
+    struct Status {
+        int err;
+        int flags;
+    };
+    Status *dst = nullptr;
+    FGB_TRY(dalloc_n(&dst, 1, s));
+    FGB_CUDA(cudaMemsetAsync(dst, 0, sizeof(Status), s));
+    a.b.err = &dst->err;
+    a.flag_count = &dst->flags;
+    a.flag_cap = (int)std::max<int64_t>(1, nqq);
+    nl->n_query = nqq;
+    nl->n_points = np;
+    nl->n_pairs = nqq * m;
+    int st = dalloc_n(&nl->counts, nqq, s);
+    st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
+    st = st ? st : dalloc_n(&nl->qi, nl->n_pairs, s);
+    st = st ? st : dalloc_n(&nl->pj, nl->n_pairs, s);
+    st = st ? st : dalloc_n(&nl->dist, nl->n_pairs, s);
+    st = st ? st : dalloc_n(&a.flags, a.flag_cap, s);
+    if (st == FGB_OK) {
+        {
+            FGB_KSCOPE("k_bvh_knn_rows", s);
+            k_bvh_knn_rows<<<grid1d(nqq + 1, 256), 256, 0, s>>>(nqq, m, nl->segments, nl->counts);
+        }
+        a.qi_out = nl->qi;
+        a.pj_out = nl->pj;
+        a.d_out = nl->dist;
+        if (nqq > 0 && m > 0) {
+            if (m + 1 <= 2)
+                launch_bvh_knn<2>(a, s);
+            else if (m + 1 <= 4)
+                launch_bvh_knn<4>(a, s);
+            else if (m + 1 <= 8)
+                launch_bvh_knn<8>(a, s);
+            else if (m + 1 <= 16)
+                launch_bvh_knn<16>(a, s);
+            else if (m + 1 <= 32)
+                launch_bvh_knn<32>(a, s);
+            else
+                launch_bvh_knn<64>(a, s);
+        }
+        Status hs;
+        cudaMemcpyAsync(&hs, dst, sizeof(Status), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            st = fail(FGB_ERR_CUDA, "tree kNN failed: %s", cudaGetErrorString(e));
+        else if (hs.err & 1)
+            st = fail(FGB_ERR_BOX_TOO_SMALL, "a k-th neighbor lies at half the smallest box width or beyond");
+        else if (hs.err == 5)
+            st = fail(FGB_ERR_INVALID_ARG, "tree query: query points must lie within two box lengths of the box centre");
+        else if (hs.err)
+            st = fail(FGB_ERR_CUDA, "tree kNN: traversal failed (code %d)", hs.err);
+    }
+    dfree(a.flags, s);
+    dfree(dst, s);
+    nl->kind = 1;
+    nl->symmetric = 0;
     return st;
 }
 

@@ -315,13 +315,13 @@ extern "C" int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_que
     if (query_points && query_points != nq->points && n_query < 0)
         return fail(FGB_ERR_INVALID_ARG, "n_query must be >= 0");
     cudaStream_t s = as_stream(stream);
-    if (nq->kind == 1 && knn) return fail(FGB_ERR_UNSUPPORTED, "the tree query answers r_max queries only");
     fgb_nlist *nl = new fgb_nlist();
     memset(nl, 0, sizeof(*nl));
     nl->stream = s;
     int st = FGB_OK;
     if (nq->kind == 1) {
-        st = aabb_ball_query(nq, query_points, n_query, args, s, nl);
+        st = ball ? aabb_ball_query(nq, query_points, n_query, args, s, nl)
+                  : aabb_knn_query(nq, query_points, n_query, args, s, nl);
     } else {
         QueryPoints Q;
         st = prepare_queries(nq, query_points, n_query, s, &Q);

@@ -127,6 +127,33 @@ __device__ __forceinline__ float r2_f32(float dx, float dy, float dz) {
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// Top-KT list by (r2, index), kept sorted in registers (kNN kernels).
+template <int KT>
+__device__ __forceinline__ void topk_insert(float (&br)[KT], int (&bj)[KT], float r2, int j) {
+    float cr = r2;
+    int cj = j;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const bool less = cr < br[q] || (cr == br[q] && cj < bj[q]);
+        const float tr = less ? br[q] : cr;
+        const int tj = less ? bj[q] : cj;
+        br[q] = less ? cr : br[q];
+        bj[q] = less ? cj : bj[q];
+        cr = tr;
+        cj = tj;
+    }
+}
+
+// a[idx] for a runtime idx without dynamic register indexing (keeps the list in registers)
+template <int KT, class T>
+__device__ __forceinline__ T pick(const T (&v)[KT], int idx) {
+    T out = v[0];
+#pragma unroll
+    for (int q = 1; q < KT; ++q)
+        if (q == idx) out = v[q];
+    return out;
+}
+
 // Pair decision bands: r2 < lo is certainly inside the edge, r2 >= hi certainly outside;
 // anything between goes to exact_r2.
 struct Band {

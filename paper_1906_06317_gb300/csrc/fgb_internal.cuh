@@ -206,6 +206,8 @@ int aabb_build(fgb_nq *nq, cudaStream_t s);
 void aabb_free(fgb_nq *nq);
 int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
                     cudaStream_t s, fgb_nlist *nl);
+int aabb_knn_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
+                   cudaStream_t s, fgb_nlist *nl);
 // Sorts every segment of a list by point index in place (warp per segment, rows of at
 // most cap entries staged in shared memory); tile.cu.
 int sort_segments(const int64_t *seg, int64_t nq, int cap, int packable, int32_t *qi, int32_t *pj, float *dist,

@@ -69,32 +69,6 @@ __device__ __forceinline__ Stencil knn_stencil(const KnnArgs &a, int s, bool &al
 }
 
 template <int KT>
-__device__ __forceinline__ void topk_insert(float (&br)[KT], int (&bj)[KT], float r2, int j) {
-    float cr = r2;
-    int cj = j;
-#pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        const bool less = cr < br[q] || (cr == br[q] && cj < bj[q]);
-        const float tr = less ? br[q] : cr;
-        const int tj = less ? bj[q] : cj;
-        br[q] = less ? cr : br[q];
-        bj[q] = less ? cj : bj[q];
-        cr = tr;
-        cj = tj;
-    }
-}
-
-// a[idx] for a runtime idx without dynamic register indexing (keeps the list in registers)
-template <int KT, class T>
-__device__ __forceinline__ T pick(const T (&v)[KT], int idx) {
-    T out = v[0];
-#pragma unroll
-    for (int q = 1; q < KT; ++q)
-        if (q == idx) out = v[q];
-    return out;
-}
-
-template <int KT>
 __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a.list) {

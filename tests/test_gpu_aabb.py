@@ -127,7 +127,7 @@ def test_tree_unsupported_and_invalid(fgb):
     x = W.small_random(96, 500, b)
     aq = fgb.AABBQuery(b, dev(x))
     with pytest.raises(fgb.FGBError) as e:
-        aq.query(None, dict(num_neighbors=4)).toNeighborList()
+        aq.query(None, dict(num_neighbors=33)).toNeighborList()
     assert e.value.code == fgb.ERR_UNSUPPORTED
     with pytest.raises(fgb.FGBError) as e:
         fgb.RDF(10, 2.0).compute(aq)
@@ -143,3 +143,50 @@ def test_tree_unsupported_and_invalid(fgb):
     with pytest.raises(fgb.FGBError) as e:
         aq.query(dev(far[:5]), dict(r_max=1.0, exclude_ii=False)).toNeighborList()
     assert e.value.code == fgb.ERR_INVALID_ARG
+
+
+def assert_knn_equal(nl, ref):
+    n, j, r = ref
+    m = int(n[0])
+    assert np.all(n == m)
+    assert np.array_equal(nl.segments.cpu().numpy(), np.arange(len(n) + 1) * m)
+    assert np.array_equal(nl.point_indices.cpu().numpy().reshape(-1, m), j[:, :m])
+    assert np.allclose(nl.distances.cpu().numpy().reshape(-1, m), r[:, :m], rtol=2e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("bi", [0, 2, 3])
+@pytest.mark.parametrize("k", [1, 4, 12, 20, 32])
+def test_tree_knn_matches_oracle_and_cell_list(fgb, bi, k):
+    b = BOXES[bi]
+    x = W.small_random(100 + bi, 4000, b)
+    nl = fgb.AABBQuery(b, dev(x)).query(None, dict(num_neighbors=k, exclude_ii=True)).toNeighborList()
+    assert_knn_equal(nl, oracle.knn(b, x, k))
+    c = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=k, exclude_ii=True)).toNeighborList()
+    assert torch.equal(nl.point_indices, c.point_indices)
+
+
+def test_tree_knn_ties_outside_points_and_query_points(fgb):
+    # perfect FCC: 12 neighbors at one distance, decided by index through the FP64 path
+    b = W.Box.cube(4 * 1.5874)
+    xf = W.lattice_points(None, b, 4)
+    nl = fgb.AABBQuery(b, dev(xf)).query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
+    assert_knn_equal(nl, oracle.knn(b, xf, 12))
+    b3 = BOXES[3]
+    rng = np.random.default_rng(12)
+    x = W.small_random(110, 3000, b3)
+    x[:150] += (b3.matrix() @ rng.integers(-1, 2, size=(150, 3)).T).T.astype(np.float32)
+    y = W.small_random(111, 400, b3)
+    aq = fgb.AABBQuery(b3, dev(x))
+    for excl in (False, True):
+        nl = aq.query(dev(y), dict(num_neighbors=8, exclude_ii=excl)).toNeighborList()
+        assert_knn_equal(nl, oracle.knn(b3, x, 8, exclude_ii=excl, query_points=y))
+    nl = aq.query(None, dict(num_neighbors=6, exclude_ii=False)).toNeighborList()
+    assert_knn_equal(nl, oracle.knn(b3, x, 6, exclude_ii=False))
+    # fewer points than k: rows of n - 1 (a tight cluster, so every distance is valid)
+    xs = (np.random.default_rng(13).normal(size=(5, 3)) * 0.5).astype(np.float32)
+    few = fgb.AABBQuery(b3, dev(xs))
+    nl = few.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
+    assert_knn_equal(nl, oracle.knn(b3, xs, 12))
+    with pytest.raises(fgb.FGBError) as e:  # 5 points spread over the box: a 4th neighbor too far
+        fgb.AABBQuery(b3, dev(W.small_random(112, 5, b3))).query(None, dict(num_neighbors=4)).toNeighborList()
+    assert e.value.code == fgb.ERR_BOX_TOO_SMALL
