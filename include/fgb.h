@@ -66,6 +66,7 @@ typedef struct fgb_nq fgb_nq;
 typedef struct fgb_nlist fgb_nlist;
 typedef struct fgb_rdf fgb_rdf;
 typedef struct fgb_steinhardt fgb_steinhardt;
+typedef struct fgb_clusters fgb_clusters;
 typedef struct fgb_batch fgb_batch;
 
 /* ------------------------------------------------------------- library state */
@@ -294,6 +295,34 @@ int fgb_steinhardt_wl(fgb_steinhardt *st, int32_t normalize, float *w_out, void 
  * q_out: float32 (n) device.  Asynchronous on `stream`.
  */
 int fgb_steinhardt_average(fgb_steinhardt *st, const fgb_nlist *nlist, float *q_out, void *stream);
+
+/* -------------------------------------------------------------------- Clusters */
+
+/*
+ * Clusters of points joined by the bonds of a NeighborList (cluster module, Section
+ * "Analysis Modules": cluster membership defined by neighbor bonds): connected
+ * components over the n points (a point without bonds is a cluster of its own), bonds
+ * with bond_mask[e] == 0 ignored (bond_mask NULL: all).  Clusters are numbered by
+ * decreasing size, ties by their smallest member.  The call synchronises `stream` once
+ * (to size the outputs).  Errors: INVALID_ARG (NULL, n out of range, list indexes
+ * beyond n), OOM, CUDA.
+ */
+int fgb_cluster_compute(int64_t n, const fgb_nlist *nlist, const uint8_t *bond_mask, void *stream,
+                        fgb_clusters **out);
+/* Device views owned by the handle: cluster index per point (int32, n), sizes per
+ * cluster (int32, num_clusters, non-increasing). */
+int fgb_cluster_result(const fgb_clusters *c, int64_t *num_clusters, const int32_t **cluster_idx,
+                       const int32_t **sizes);
+/*
+ * Per-cluster properties (ClusterProperties): every member is unwrapped to the image
+ * nearest the cluster's smallest member; centers (num_clusters, 3) = that member plus the
+ * mean unwrapped offset, wrapped into the box; gyration (num_clusters, 3, 3) = mean outer
+ * product of the unwrapped offsets from the centre.  Meaningful for clusters smaller
+ * than half the box.  Device float32 outputs; asynchronous on `stream`.
+ */
+int fgb_cluster_properties(const fgb_clusters *c, const fgb_box *box, const float *points, float *centers,
+                           float *gyration, void *stream);
+void fgb_cluster_destroy(fgb_clusters *c);
 
 /* ------------------------------------------------------------ LocalDescriptors */
 

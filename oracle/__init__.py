@@ -414,3 +414,69 @@ def local_descriptors(box, points, qi, pj, l_max, negative_m=True, query_points=
     _check(lib().orc_descriptors(_ptr(b), _ptr(pts), _ptr(qpts), len(qi), _ptr(qi), _ptr(pj), int(l_max),
                                  int(bool(negative_m)), _ptr(out)), "descriptors")
     return out[..., 0] + 1j * out[..., 1]
+
+
+# ------------------------------------------------------------------------ clusters
+
+
+def clusters(n, qi, pj, mask=None):
+    """Connected components of the points joined by bonds (qi[e], pj[e]) with mask[e]
+    (all when None); numbered by decreasing size, ties by smallest member.  Returns
+    (cluster index per point, sizes)."""
+    parent = list(range(n))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    qi = np.asarray(qi, np.int64)
+    pj = np.asarray(pj, np.int64)
+    for e in range(len(qi)):
+        if mask is not None and not mask[e]:
+            continue
+        a, b = find(int(qi[e])), find(int(pj[e]))
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+    root = np.array([find(i) for i in range(n)], np.int64)
+    members = {}
+    for i in range(n):
+        members.setdefault(root[i], []).append(i)
+    order = sorted(members, key=lambda r: (-len(members[r]), min(members[r])))
+    idx = np.empty(n, np.int64)
+    for c, r in enumerate(order):
+        idx[members[r]] = c
+    return idx, np.array([len(members[r]) for r in order], np.int64)
+
+
+def cluster_properties(box, points, cluster_idx):
+    """Centers and gyration tensors: members unwrapped to the image nearest the
+    cluster's smallest member (the defining minimum image), centre = that member + mean
+    offset wrapped into the box, gyration = mean outer product of offsets from the centre."""
+    b = _box(box)
+    pts = _pts(points)
+    idx = np.asarray(cluster_idx, np.int64)
+    nc = int(idx.max()) + 1 if len(idx) else 0
+    L = lib()
+    centers = np.zeros((nc, 3))
+    gyr = np.zeros((nc, 3, 3))
+    M = np.asarray(box.matrix(), np.float64)
+    Minv = np.linalg.inv(M)
+    for c in range(nc):
+        mem = np.nonzero(idx == c)[0]
+        r = mem[0]
+        d = np.zeros((len(mem), 3))
+        for k, j in enumerate(mem):
+            out = np.zeros(3)
+            rr = np.zeros(1)
+            _check(L.orc_min_image(_ptr(b), _ptr(np.ascontiguousarray(pts[r])), _ptr(np.ascontiguousarray(pts[j])),
+                                   _ptr(out), _ptr(rr)), "min_image")
+            d[k] = out
+        mean = d.mean(axis=0)
+        p = pts[r] + mean
+        s = Minv @ p + 0.5
+        centers[c] = p - M @ np.floor(s)
+        e = d - mean
+        gyr[c] = e.T @ e / len(mem)
+    return centers, gyr

@@ -91,6 +91,10 @@ _SIGS = {
     "fgb_steinhardt_wl": (_I32, [_P, _I32, _P, _P]),
     "fgb_steinhardt_average": (_I32, [_P, _P, _P, _P]),
     "fgb_local_descriptors": (_I32, [ctypes.POINTER(fgb_box), _P, _P, _P, _I32, _I32, _P, _P]),
+    "fgb_cluster_compute": (_I32, [_I64, _P, _P, _P, _PP]),
+    "fgb_cluster_result": (_I32, [_P, ctypes.POINTER(_I64), _PP, _PP]),
+    "fgb_cluster_properties": (_I32, [_P, ctypes.POINTER(fgb_box), _P, _P, _P, _P]),
+    "fgb_cluster_destroy": (None, [_P]),
     "fgb_batch_create": (_I32, [_I32, _P, ctypes.POINTER(fgb_box), ctypes.POINTER(fgb_batch_params), _P, _PP]),
     "fgb_batch_destroy": (None, [_P]),
     "fgb_batch_run": (_I32, [_P, _P, _P]),
@@ -524,6 +528,42 @@ class LocalDescriptors:
                                            neighbors._h, self.l_max, int(self.negative_m), out.data_ptr(), _stream()))
         self.sph = torch.view_as_complex(out)
         return self
+
+
+class Cluster:
+    """Clusters of points joined by neighbor bonds (freud cluster.Cluster): cluster_idx per
+    point, clusters numbered by decreasing size (ties: smallest member first).  bond_mask
+    (uint8 per pair of the list) selects the bonds that join."""
+
+    def __init__(self):
+        self.cluster_idx = None
+        self.cluster_sizes = None
+        self.num_clusters = 0
+        self._o = None
+
+    def compute(self, system, neighbors: NeighborList, bond_mask: torch.Tensor = None):
+        nq = _as_nq(system)
+        m = None if bond_mask is None else _need_cuda(bond_mask, torch.uint8, "bond_mask")
+        h = ctypes.c_void_p()
+        _check(lib().fgb_cluster_compute(nq.n_points, neighbors._h, None if m is None else m.data_ptr(), _stream(),
+                                         ctypes.byref(h)))
+        self._o = _Owned(h.value, "fgb_cluster_destroy")
+        nc, ci, sz = _I64(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().fgb_cluster_result(self._o.ptr, ctypes.byref(nc), ctypes.byref(ci), ctypes.byref(sz)))
+        self.num_clusters = nc.value
+        self.cluster_idx = _view(ci.value, (nq.n_points,), torch.int32, self._o)
+        self.cluster_sizes = _view(sz.value, (nc.value,), torch.int32, self._o)
+        self._nq = nq
+        return self
+
+    def properties(self):
+        """(centers (num_clusters, 3), gyration tensors (num_clusters, 3, 3)) on the device."""
+        c = torch.empty((self.num_clusters, 3), dtype=torch.float32, device="cuda")
+        g = torch.empty((self.num_clusters, 3, 3), dtype=torch.float32, device="cuda")
+        b = self._nq.box._c()
+        _check(lib().fgb_cluster_properties(self._o.ptr, ctypes.byref(b), self._nq.points.data_ptr(), c.data_ptr(),
+                                            g.data_ptr(), _stream()))
+        return c, g
 
 
 class Q6Mean(torch.autograd.Function):

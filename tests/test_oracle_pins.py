@@ -436,3 +436,46 @@ def test_descriptors_addition_theorem_and_axes():
         assert np.allclose(Yz[0, k + 1:k + l + 1], 0, atol=1e-13)
         k += l + 1
     assert Yz[1, 2] == pytest.approx(-math.sqrt(3 / (8 * math.pi)), abs=1e-13)
+
+
+def test_clusters_match_connected_components_and_ordering():
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    b = W.Box(10.0, 9.0, 11.0, 0.1, 0.0, -0.1)
+    x = W.small_random(21, 1500, b)
+    _, o, pj, _ = oracle.ball_query(b, x, 0.55)
+    qi = np.repeat(np.arange(len(x)), np.diff(o))
+    rng = np.random.default_rng(2)
+    for mask in (None, rng.random(len(qi)) < 0.6):
+        idx, sizes = oracle.clusters(len(x), qi, pj, mask)
+        keep = np.ones(len(qi), bool) if mask is None else mask
+        g = coo_matrix((np.ones(keep.sum()), (qi[keep], pj[keep])), shape=(len(x), len(x)))
+        ncc, lab = connected_components(g, directed=True, connection="weak")
+        assert len(sizes) == ncc and sizes.sum() == len(x)
+        # same partition: the pairs of labels form a bijection
+        assert len(set(zip(idx.tolist(), lab.tolist()))) == ncc
+        assert np.all(np.diff(sizes) <= 0)
+        firsts = np.array([np.nonzero(idx == c)[0][0] for c in range(len(sizes))])
+        same = np.diff(sizes) == 0
+        assert np.all(np.diff(firsts)[same] > 0), "ties not ordered by smallest member"
+
+
+def test_cluster_properties_closed_forms_and_periodic_shift():
+    b = W.Box.cube(10.0)
+    # a pair 0.6 apart through the x face (x = 4.8 and -4.6): centre 5.1, wrapped to -4.9;
+    # offsets from it are -+0.3 along x, so the gyration tensor is diag(0.09, 0, 0)
+    x = np.array([[4.8, 1.0, -2.0], [-4.6, 1.0, -2.0], [0.0, 0.0, 0.0]])
+    c, g = oracle.cluster_properties(b, x, np.array([0, 0, 1]))
+    assert np.allclose(c[0], [-4.9, 1.0, -2.0], atol=1e-12)
+    assert np.allclose(g[0], np.diag([0.3 ** 2, 0.0, 0.0]), atol=1e-12)
+    assert np.allclose(g[1], 0.0) and np.allclose(c[1], 0.0)
+    # translating a cluster across the box moves its centre by the same amount (mod the
+    # box) and leaves its gyration tensor unchanged; the tensor is the population covariance
+    rng = np.random.default_rng(3)
+    blob = rng.normal(size=(30, 3)) * 0.5
+    t = np.array([4.7, -3.2, 4.9])
+    c1, g1 = oracle.cluster_properties(b, blob, np.zeros(30, np.int64))
+    c2, g2 = oracle.cluster_properties(b, blob + t, np.zeros(30, np.int64))
+    dc = (c2[0] - c1[0] - t + 5.0) % 10.0 - 5.0
+    assert np.allclose(dc, 0.0, atol=1e-10) and np.allclose(g1, g2, atol=1e-10)
+    assert np.allclose(g1[0], np.cov((blob - blob.mean(0)).T, bias=True), atol=1e-12)
