@@ -324,6 +324,24 @@ int fgb_cluster_properties(const fgb_clusters *c, const fgb_box *box, const floa
                            float *gyration, void *stream);
 void fgb_cluster_destroy(fgb_clusters *c);
 
+/*
+ * Solid-liquid order parameter (order module, Section "Analysis Modules": a solid-liquid
+ * order parameter for generic ordered phases, after ten Wolde, Ruiz-Montero and Frenkel
+ * 1996) over a self NeighborList of `points`:
+ *   s_ij = Re sum_{m=-l..l} Q_lm(i) conj(Q_lm(j)) / (|Q_l(i)| |Q_l(j)|)  per bond
+ * (unnormalised dot product when normalize_q == 0; 0 for a particle without bonds),
+ * with Q_lm(i) = (1/n_i) sum_j Y_lm over the list's bonds; a bond is solid-like when
+ * s_ij > q_threshold, a particle is solid with at least solid_threshold solid-like bonds,
+ * and *clusters_out joins solid particles through solid-like bonds (as
+ * fgb_cluster_compute; every other particle is a cluster of its own).  Decided in FP64
+ * on the device.  ql_ij: float32 (n_pairs) device or NULL; num_connections: int32 (n)
+ * device.  Synchronises `stream` once (in the clustering).  Errors: INVALID_ARG (l
+ * outside [0, 12], not a self list, NULL arrays, degenerate box), OOM, CUDA.
+ */
+int fgb_solid_liquid(const fgb_box *box, const float *points, const fgb_nlist *nlist, int32_t l, double q_threshold,
+                     int32_t solid_threshold, int32_t normalize_q, float *ql_ij, int32_t *num_connections,
+                     void *stream, fgb_clusters **clusters_out);
+
 /* ------------------------------------------------------------ LocalDescriptors */
 
 /*

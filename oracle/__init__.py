@@ -480,3 +480,28 @@ def cluster_properties(box, points, cluster_idx):
         e = d - mean
         gyr[c] = e.T @ e / len(mem)
     return centers, gyr
+
+
+def solid_liquid(box, points, offsets, pj, l, q_threshold, solid_threshold, normalize_q=True):
+    """Solid-liquid order parameter (ten Wolde, Ruiz-Montero and Frenkel 1996) in FP64:
+    bond scores s_ij = Re sum_m Q_lm(i) conj(Q_lm(j)) (normalised by |Q_l(i)| |Q_l(j)|),
+    solid-like bonds s_ij > q_threshold, solid particles with >= solid_threshold of them,
+    clusters of solid particles joined by solid-like bonds.  Returns (s_ij, connections,
+    cluster index, cluster sizes)."""
+    _, Q = steinhardt(box, points, offsets, pj, l, with_qlm=True)
+    F = _full_qlm(Q, l)
+    off, j = _nl(offsets, pj)
+    qi = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    dot = np.real(np.sum(F[qi] * np.conj(F[j]), axis=1))
+    if normalize_q:
+        na = np.sqrt(np.sum(np.abs(F) ** 2, axis=1))
+        den = na[qi] * na[j]
+        s = np.where(den > 0, dot / np.where(den > 0, den, 1.0), 0.0)
+    else:
+        s = dot
+    solid_bond = s > q_threshold
+    conn = np.zeros(len(off) - 1, np.int64)
+    np.add.at(conn, qi, solid_bond.astype(np.int64))
+    join = solid_bond & (conn[qi] >= solid_threshold) & (conn[j] >= solid_threshold)
+    idx, sizes = clusters(len(off) - 1, qi, j, join)
+    return s, conn, idx, sizes

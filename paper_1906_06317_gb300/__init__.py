@@ -95,6 +95,7 @@ _SIGS = {
     "fgb_cluster_result": (_I32, [_P, ctypes.POINTER(_I64), _PP, _PP]),
     "fgb_cluster_properties": (_I32, [_P, ctypes.POINTER(fgb_box), _P, _P, _P, _P]),
     "fgb_cluster_destroy": (None, [_P]),
+    "fgb_solid_liquid": (_I32, [ctypes.POINTER(fgb_box), _P, _P, _I32, _D, _I32, _I32, _P, _P, _P, _PP]),
     "fgb_batch_create": (_I32, [_I32, _P, ctypes.POINTER(fgb_box), ctypes.POINTER(fgb_batch_params), _P, _PP]),
     "fgb_batch_destroy": (None, [_P]),
     "fgb_batch_run": (_I32, [_P, _P, _P]),
@@ -564,6 +565,39 @@ class Cluster:
         _check(lib().fgb_cluster_properties(self._o.ptr, ctypes.byref(b), self._nq.points.data_ptr(), c.data_ptr(),
                                             g.data_ptr(), _stream()))
         return c, g
+
+
+class SolidLiquid:
+    """Solid-liquid order parameter (freud order.SolidLiquid): per bond the normalised
+    q_lm dot product ql_ij, per particle the number of solid-like bonds (ql_ij >
+    q_threshold), and clusters of solid particles (>= solid_threshold solid-like bonds)
+    joined by solid-like bonds."""
+
+    def __init__(self, l: int, q_threshold: float, solid_threshold: int, normalize_q: bool = True):
+        self.l, self.q_threshold = int(l), float(q_threshold)
+        self.solid_threshold, self.normalize_q = int(solid_threshold), bool(normalize_q)
+
+    def compute(self, system, neighbors: NeighborList):
+        nq = _as_nq(system)
+        self.ql_ij = torch.empty(neighbors.n_pairs, dtype=torch.float32, device="cuda")
+        self.num_connections = torch.empty(nq.n_points, dtype=torch.int32, device="cuda")
+        b = nq.box._c()
+        h = ctypes.c_void_p()
+        _check(lib().fgb_solid_liquid(ctypes.byref(b), nq.points.data_ptr(), neighbors._h, self.l, self.q_threshold,
+                                      self.solid_threshold, int(self.normalize_q), self.ql_ij.data_ptr(),
+                                      self.num_connections.data_ptr(), _stream(), ctypes.byref(h)))
+        c = Cluster()
+        c._o = _Owned(h.value, "fgb_cluster_destroy")
+        nc, ci, sz = _I64(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().fgb_cluster_result(c._o.ptr, ctypes.byref(nc), ctypes.byref(ci), ctypes.byref(sz)))
+        c.num_clusters = nc.value
+        c.cluster_idx = _view(ci.value, (nq.n_points,), torch.int32, c._o)
+        c.cluster_sizes = _view(sz.value, (nc.value,), torch.int32, c._o)
+        c._nq = nq
+        self.clusters = c
+        self.cluster_idx = c.cluster_idx
+        self.largest_cluster_size = int(c.cluster_sizes[0]) if nc.value > 0 else 0
+        return self
 
 
 class Q6Mean(torch.autograd.Function):

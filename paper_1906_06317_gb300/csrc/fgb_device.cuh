@@ -43,6 +43,27 @@ __device__ __forceinline__ double exact_r2(const BoxD &b, float xi0, float xi1, 
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// The minimum-image displacement x_j - x_i itself, by the same FP64 sequence as exact_r2.
+__device__ __forceinline__ double3 exact_disp(const BoxD &b, const float *xi, const float *xj) {
+    double dx = __dsub_rn((double)__ldg(xj), (double)__ldg(xi));
+    double dy = __dsub_rn((double)__ldg(xj + 1), (double)__ldg(xi + 1));
+    double dz = __dsub_rn((double)__ldg(xj + 2), (double)__ldg(xi + 2));
+    double nz = rint_quot(dz, b.L[2], b.invL[2]);
+    if (nz != 0.0) {
+        dx = __dsub_rn(dx, __dmul_rn(nz, b.a3x));
+        dy = __dsub_rn(dy, __dmul_rn(nz, b.a3y));
+        dz = __dsub_rn(dz, __dmul_rn(nz, b.L[2]));
+    }
+    double ny = rint_quot(dy, b.L[1], b.invL[1]);
+    if (ny != 0.0) {
+        dx = __dsub_rn(dx, __dmul_rn(ny, b.a2x));
+        dy = __dsub_rn(dy, __dmul_rn(ny, b.L[1]));
+    }
+    double nx = rint_quot(dx, b.L[0], b.invL[0]);
+    if (nx != 0.0) dx = __dsub_rn(dx, __dmul_rn(nx, b.L[0]));
+    return make_double3(dx, dy, dz);
+}
+
 __device__ __forceinline__ double exact_r2_idx(const BoxD &b, const float *xi_arr, int64_t i, const float *xj_arr,
                                                int64_t j) {
     return exact_r2(b, __ldg(xi_arr + 3 * i), __ldg(xi_arr + 3 * i + 1), __ldg(xi_arr + 3 * i + 2),

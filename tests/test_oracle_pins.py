@@ -479,3 +479,34 @@ def test_cluster_properties_closed_forms_and_periodic_shift():
     dc = (c2[0] - c1[0] - t + 5.0) % 10.0 - 5.0
     assert np.allclose(dc, 0.0, atol=1e-10) and np.allclose(g1, g2, atol=1e-10)
     assert np.allclose(g1[0], np.cov((blob - blob.mean(0)).T, bias=True), atol=1e-12)
+
+
+def test_solid_liquid_crystal_pair_and_symmetry():
+    # perfect FCC: every particle has the same Q_lm, so s_ij = 1 on every bond, all 12
+    # bonds are solid-like and the crystal is one cluster; unnormalised, s_ij = sum_m
+    # |Q_lm|^2 = (2l+1)/(4 pi) q_l^2
+    b = W.Box.cube(4 * 1.5874)
+    x = W.lattice_points(None, b, 4)
+    _, o, pj, _ = oracle.ball_query(b, x, 1.3)
+    s, conn, idx, sizes = oracle.solid_liquid(b, x, o, pj, 6, 0.7, 7)
+    assert np.allclose(s, 1.0, atol=1e-12) and np.all(conn == 12)
+    assert len(sizes) == 1 and sizes[0] == len(x)
+    q6 = oracle.steinhardt(b, x, o, pj, 6)
+    su, _, _, _ = oracle.solid_liquid(b, x, o, pj, 6, 0.0, 1, normalize_q=False)
+    assert np.allclose(su, 13 / (4 * math.pi) * q6[0] ** 2, atol=1e-12)
+    # two points, each the other's only neighbor: Q(2) = Y(-u) = (-1)^l Y(u), s = (-1)^l
+    b2 = W.Box.cube(10.0)
+    x2 = np.array([[0.0, 0.0, 0.0], [0.3, -0.8, 0.5], [4.0, 4.0, 4.0]])
+    o2, pj2 = np.array([0, 1, 2, 2]), np.array([1, 0])
+    for l in (3, 4, 6):
+        s2, conn2, idx2, _ = oracle.solid_liquid(b2, x2, o2, pj2, l, 0.5, 1)
+        assert np.allclose(s2, (-1) ** l, atol=1e-12)
+        assert list(conn2) == ([1, 1, 0] if l % 2 == 0 else [0, 0, 0])
+        assert (idx2[0] == idx2[1]) == (l % 2 == 0)
+    # symmetric list: s_ij = s_ji
+    xr = W.small_random(31, 800, b2)
+    _, o3, pj3, _ = oracle.ball_query(b2, xr, 1.5)
+    s3, _, _, _ = oracle.solid_liquid(b2, xr, o3, pj3, 6, 0.7, 7)
+    qi3 = np.repeat(np.arange(len(xr)), np.diff(o3))
+    fwd = dict(zip(zip(qi3.tolist(), pj3.tolist()), s3.tolist()))
+    assert all(fwd[(j, i)] == v for (i, j), v in fwd.items())
