@@ -466,6 +466,11 @@ def extras(fgb, torch, dev, stream, flush):
     comp["c2_descriptors_l6"] = {"ms": t_ld, "bytes": ld_bytes, "achieved_gbs": ld_bytes / t_ld / 1e6,
                                  "frac_of_measured_hbm": ld_bytes / t_ld / 1e6 / peak}
     ld.sph = None
+    # clusters of the whole list, and the solid-liquid parameter (l = 6, 0.7, 7 bonds)
+    comp["c2_cluster_ms"] = timed(lambda: fgb.Cluster().compute(holder["nq"], holder["nl"]), stream, flush)
+    sl = fgb.SolidLiquid(6, 0.7, 7)
+    comp["c2_solid_liquid_ms"] = timed(lambda: sl.compute(holder["nq"], holder["nl"]), stream, flush)
+    comp["c2_largest_solid_cluster"] = sl.largest_cluster_size
     rdf2 = fgb.RDF(200, 5.0)
 
     def c2_rdf():
