@@ -111,9 +111,9 @@ class ClockSampler:
 # so it is scaled to the bench's N; once the source changes the figure is stale and is
 # reported as null.
 MEASURED_TRAFFIC = {
-    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "0dc5c46fb493e927", 556.983808e6 + 1537.264e6, 2097152),
-    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "0dc5c46fb493e927", 34.419456e6 + 0.015e6, 2097152),
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "902b1d7eb3c7e3f6", 34.194944e6 + 0.014e6, 2097152),
+    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "49c024a3625fcf66", 559.168256e6 + 1537.259e6, 2097152),
+    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "49c024a3625fcf66", 34.414336e6 + 0.018e6, 2097152),
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "54d9b313d5161218", 34.20928e6 + 0.079e6, 2097152),
 }
 
 
