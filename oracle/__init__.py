@@ -52,6 +52,7 @@ def lib():
         L.orc_descriptors.argtypes = [_P, _P, _P, _I64, _P, _P, _I32, _I32, _P]
         L.orc_steinhardt_legendre.argtypes = [_P, _P, _I64, _P, _P, _I32, _P, _I64, _P]
         L.orc_q_grad.argtypes = [_P, _P, _I64, _P, _P, _I32, _P]
+        L.orc_pmftxy.argtypes = [_P, _P, _P, _P, _I64, _P, _P, _D, _D, _I32, _I32, _P, _P]
         _lib = L
     return _lib
 
@@ -183,8 +184,11 @@ def knn(box, points, k, exclude_ii=True, query_points=None, brute=False, queries
     cells = None
     if not brute:
         if r_cell is None:
-            vol = abs(np.prod(b[:3]))
-            r_cell = 1.2 * (3.0 * (k + 1) * vol / (4.0 * math.pi * max(1, len(pts)))) ** (1.0 / 3.0)
+            if b[2] == 0.0:  # 2D box: disc holding about k+1 points
+                r_cell = 1.2 * ((k + 1) * b[0] * b[1] / (math.pi * max(1, len(pts)))) ** 0.5
+            else:
+                vol = abs(np.prod(b[:3]))
+                r_cell = 1.2 * (3.0 * (k + 1) * vol / (4.0 * math.pi * max(1, len(pts)))) ** (1.0 / 3.0)
         cells = Cells(b, pts, r_cell)
     q0, q1 = (0, len(qpts)) if queries is None else queries
     nq = q1 - q0
@@ -243,12 +247,16 @@ def rdf_counts(box, points, bins, r_max, r_min=0.0, exclude_ii=True, query_point
     return total
 
 
-def rdf_normalize(counts, n_query, n_points, volume, bins, r_min, r_max):
+def rdf_normalize(counts, n_query, n_points, volume, bins, r_min, r_max, dim=3):
     """g_b = counts_b / (N_q (N_p / V) (4 pi / 3)(R_{b+1}^3 - R_b^3)) and the bin centres
     r_min + (b + 1/2) (r_max - r_min)/bins.  With several frames accumulated, pass
-    n_query * n_points / volume summed over frames as `n_query` and n_points = volume = 1."""
+    n_query * n_points / volume summed over frames as `n_query` and n_points = volume = 1.
+    dim=2: V is the box area and the shell the annulus pi (R_{b+1}^2 - R_b^2)."""
     e = rdf_edges(bins, r_min, r_max)
-    shell = 4.0 / 3.0 * math.pi * (e[1:] ** 3 - e[:-1] ** 3)
+    if dim == 2:
+        shell = math.pi * (e[1:] ** 2 - e[:-1] ** 2)
+    else:
+        shell = 4.0 / 3.0 * math.pi * (e[1:] ** 3 - e[:-1] ** 3)
     g = np.asarray(counts, dtype=np.float64) / (n_query * (n_points / volume) * shell)
     delta = (r_max - r_min) / bins
     centers = r_min + (np.arange(bins) + 0.5) * delta
@@ -505,3 +513,43 @@ def solid_liquid(box, points, offsets, pj, l, q_threshold, solid_threshold, norm
     join = solid_bond & (conn[qi] >= solid_threshold) & (conn[j] >= solid_threshold)
     idx, sizes = clusters(len(off) - 1, qi, j, join)
     return s, conn, idx, sizes
+
+
+def pmftxy(box, points, theta, x_max, y_max, bins_x, bins_y, query_points=None, qi=None, pj=None,
+           with_xy=False):
+    """PMFT(x, y) bin counts (int64, (bins_x, bins_y), x major): every bond (i, j) of the
+    list in the frame of query particle i (orientation angle theta[i] about z), counted in
+    [-x_max, x_max) x [-y_max, y_max).  Without a list the bonds are those of the ball
+    query with r_max = sqrt(x_max^2 + y_max^2) (exclude_ii when query_points is None),
+    which holds every bond that can land in a bin.  with_xy also returns the rotated bond
+    (x', y') per bond and the bonds (qi, pj)."""
+    b = _box(box)
+    pts = _pts(points)
+    qpts = pts if query_points is None else _pts(query_points)
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    assert th.shape == (len(qpts),)
+    if qi is None:
+        r = math.sqrt(x_max * x_max + y_max * y_max)
+        _, off, pj, _ = ball_query(b, pts, r, exclude_ii=query_points is None, query_points=query_points)
+        qi = np.repeat(np.arange(len(qpts), dtype=np.int64), np.diff(off))
+    qi = np.ascontiguousarray(np.asarray(qi, dtype=np.int64))
+    pj = np.ascontiguousarray(np.asarray(pj, dtype=np.int64))
+    counts = np.zeros((bins_x, bins_y), dtype=np.int64)
+    xy = np.zeros((len(qi), 2)) if with_xy else None
+    _check(lib().orc_pmftxy(_ptr(b), _ptr(pts), _ptr(qpts), _ptr(th), len(qi), _ptr(qi), _ptr(pj), float(x_max),
+                            float(y_max), int(bins_x), int(bins_y), _ptr(counts), _ptr(xy)), "pmftxy")
+    return (counts, xy, qi, pj) if with_xy else counts
+
+
+def pmft_normalize(counts, norm, x_max, y_max):
+    """pcf = counts / (norm * bin area), norm = sum over frames of N_query N_points / A
+    (A the box area), and PMFT = -log(pcf) in units of k_B T (Section "Potentials of Mean
+    Force and Torque": the negative logarithm of the accumulated histogram; +inf where a
+    bin is empty)."""
+    c = np.asarray(counts, dtype=np.float64)
+    bx, by = c.shape
+    area = (2.0 * x_max / bx) * (2.0 * y_max / by)
+    pcf = c / (norm * area) if norm > 0 else np.zeros_like(c)
+    with np.errstate(divide="ignore"):
+        pmft = np.where(pcf > 0, -np.log(np.where(pcf > 0, pcf, 1.0)), np.inf)
+    return pcf, pmft

@@ -11,7 +11,9 @@
  *
  * Box (Section "Implementation": triclinic box with three independent vectors, centred
  * at the origin): params (Lx, Ly, Lz, xy, xz, yz), a1 = (Lx,0,0), a2 = (xy Ly, Ly, 0),
- * a3 = (xz Lz, yz Lz, Lz).
+ * a3 = (xz Lz, yz Lz, Lz).  Lz = 0 is a 2D box (Section "Implementation": boxes are
+ * two- or three-dimensional): xz = yz = 0, points have z = 0, there is no periodicity
+ * along z, and the widths are those of the parallelogram (w_z = infinity).
  *
  * Readings of the paper (it gives no formulas for these):
  *  - minimum image: reduce along a3, then a2, then a1 by rint of the Cartesian
@@ -46,8 +48,18 @@ static void box_vectors(const double *b, double a2x[1], double a3x[1], double a3
     a3y[0] = b[5] * b[2]; /* yz * Lz */
 }
 
-/* Perpendicular widths w_k = V / |a_i x a_j| (distance between opposite faces). */
+static int is_2d(const double *b) { return b[2] == 0.0; }
+
+/* Perpendicular widths w_k = V / |a_i x a_j| (distance between opposite faces); in 2D
+ * the parallelogram's heights A / |a_other| (A = Lx Ly) and w_z = infinity. */
 int orc_box_widths(const double *b, double *w) {
+    if (is_2d(b)) {
+        double A = b[0] * b[1];
+        w[0] = A / sqrt((b[3] * b[1]) * (b[3] * b[1]) + b[1] * b[1]);
+        w[1] = A / b[0];
+        w[2] = INFINITY;
+        return ORC_OK;
+    }
     double a1[3] = {b[0], 0.0, 0.0};
     double a2[3] = {b[3] * b[1], b[1], 0.0};
     double a3[3] = {b[4] * b[2], b[5] * b[2], b[2]};
@@ -81,10 +93,12 @@ static void min_image(const double *b, const double *xi, const double *xj, doubl
     double dx = xj[0] - xi[0];
     double dy = xj[1] - xi[1];
     double dz = xj[2] - xi[2];
-    double nz = rint(dz / b[2]);
-    dx = dx - nz * a3x;
-    dy = dy - nz * a3y;
-    dz = dz - nz * b[2];
+    if (!is_2d(b)) { /* a 2D box has no z period */
+        double nz = rint(dz / b[2]);
+        dx = dx - nz * a3x;
+        dy = dy - nz * a3y;
+        dz = dz - nz * b[2];
+    }
     double ny = rint(dy / b[1]);
     dx = dx - ny * a2x;
     dy = dy - ny * b[1];
@@ -106,7 +120,7 @@ int orc_min_image(const double *b, const double *xi, const double *xj, double *d
 /* Fractional coordinate in [0,1) of a point: s = M^{-1} x + 1/2, wrapped.  Used only to
  * pick cells (pruning), never to decide a pair. */
 static void frac_wrapped(const double *b, const double *x, double *f) {
-    double sz = x[2] / b[2];
+    double sz = is_2d(b) ? 0.0 : x[2] / b[2];
     double sy = (x[1] - sz * b[5] * b[2]) / b[1];
     double sx = (x[0] - sy * b[3] * b[1] - sz * b[4] * b[2]) / b[0];
     double s[3] = {sx + 0.5, sy + 0.5, sz + 0.5};
@@ -129,7 +143,7 @@ int orc_cells_dims(const double *b, double r_cell, int32_t *nc) {
     for (int k = 0; k < 3; ++k) {
         double q = floor(w[k] / (r_cell * (1.0 + 1e-9)));
         int n = q > 512.0 ? 512 : (int)q;
-        if (n < 3) n = 1;
+        if (n < 3 || (k == 2 && is_2d(b))) n = 1;
         nc[k] = n;
         tot *= n;
     }
@@ -681,6 +695,41 @@ int orc_descriptors(const double *b, const double *pts, const double *qpts, int6
                 ++o;
             }
         }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ PMFT */
+
+/* PMFT in the plane (Section "Potentials of Mean Force and Torque", Fig. 6): each bond
+ * e = (i, j) is the minimum-image d = x_j - q_i written in the frame of query particle
+ * i, whose orientation is the angle theta_i about z (the bond turned by -theta_i):
+ *   x' = cos(theta_i) d_x + sin(theta_i) d_y,   y' = cos(theta_i) d_y - sin(theta_i) d_x,
+ * counted in bin (floor((x' + x_max) / dx), floor((y' + y_max) / dy)) with
+ * dx = 2 x_max / bx, dy = 2 y_max / by (an index of bx clamps to bx - 1) when
+ * -x_max <= x' < x_max and -y_max <= y' < y_max.  counts (bx, by), x major, are added
+ * to; xy_out (NULL or m pairs) receives (x', y'). */
+int orc_pmftxy(const double *b, const double *pts, const double *qpts, const double *theta, int64_t m,
+               const int64_t *qi, const int64_t *pj, double x_max, double y_max, int bx, int by, int64_t *counts,
+               double *xy_out) {
+    if (!(x_max > 0.0) || !(y_max > 0.0) || bx <= 0 || by <= 0) return ORC_ERR_ARG;
+    const double dx = 2.0 * x_max / bx, dy = 2.0 * y_max / by;
+    for (int64_t e = 0; e < m; ++e) {
+        double d[3];
+        min_image(b, qpts + 3 * qi[e], pts + 3 * pj[e], d);
+        const double c = cos(theta[qi[e]]), s = sin(theta[qi[e]]);
+        const double xr = c * d[0] + s * d[1];
+        const double yr = c * d[1] - s * d[0];
+        if (xy_out) {
+            xy_out[2 * e] = xr;
+            xy_out[2 * e + 1] = yr;
+        }
+        if (!(xr >= -x_max && xr < x_max && yr >= -y_max && yr < y_max)) continue;
+        int ix = (int)floor((xr + x_max) / dx);
+        int iy = (int)floor((yr + y_max) / dy);
+        if (ix > bx - 1) ix = bx - 1;
+        if (iy > by - 1) iy = by - 1;
+        counts[(int64_t)ix * by + iy] += 1;
     }
     return ORC_OK;
 }

@@ -46,3 +46,24 @@ def q_from_bonds(bonds: np.ndarray, l: int) -> float:
 
 def nl_sets(offsets, pj):
     return [set(pj[offsets[i]:offsets[i + 1]].tolist()) for i in range(len(offsets) - 1)]
+
+
+def image_vectors_2d(b, xi: np.ndarray, xj: np.ndarray, reach: int = 2) -> np.ndarray:
+    """Nearest-image vectors x_j - x_i + a1 n1 + a2 n2 (|n_k| <= reach) of a 2D box
+    (Lz = 0), all pairs (i, j), shape (len(xi), len(xj), 2), by enumerating images."""
+    Lx, Ly, _, xy, _, _ = np.asarray(b.params() if hasattr(b, "params") else b, np.float64)
+    M = np.array([[Lx, xy * Ly], [0.0, Ly]])
+    xi = np.asarray(xi, np.float64)[:, :2]
+    xj = np.asarray(xj, np.float64)[:, :2]
+    d = xj[None, :, :] - xi[:, None, :]
+    s = d @ np.linalg.inv(M).T
+    d = (s - np.round(s)) @ M.T
+    best = np.full(d.shape[:2], np.inf)
+    vec = np.zeros_like(d)
+    for n in itertools.product(range(-reach, reach + 1), repeat=2):
+        c = d + M @ np.array(n, np.float64)
+        r = np.linalg.norm(c, axis=-1)
+        better = r < best
+        best = np.where(better, r, best)
+        vec[better] = c[better]
+    return vec

@@ -19,6 +19,10 @@ r = 1, Fig. 3 and Fig. 6; the sizes below scale that recipe):
   c3  cubic rho=0.85, N=4,194,304 uniform; ball r=2.5 + RDF 500 bins [0,5]; kNN k=12
   c4  cubic L=64a, N=2^20: half perturbed FCC slab, half uniform liquid slab at density 1
   c5  256 frames, N log-uniform in [1e3, 2e5], cubic/triclinic, uniform/FCC
+  p6  2D (Lz = 0) square box, 10 frames x 20,000 uniform points at 12 neighbours per
+      unit disc, orientation angles uniform in [-pi, pi): the PMFT-vs-RDF system of Fig. 6
+
+A 2D box has Lz = 0 (and xz = yz = 0); its points have z = 0.
 """
 from __future__ import annotations
 
@@ -44,6 +48,18 @@ class Box:
     @staticmethod
     def cube(L: float) -> "Box":
         return Box(L, L, L)
+
+    @staticmethod
+    def square(L: float, xy: float = 0.0) -> "Box":
+        return Box(L, L, 0.0, xy)
+
+    @property
+    def is2D(self) -> bool:
+        return self.Lz == 0.0
+
+    @property
+    def area(self) -> float:
+        return self.Lx * self.Ly
 
     def matrix(self) -> np.ndarray:
         return np.array([[self.Lx, self.xy * self.Ly, self.xz * self.Lz],
@@ -181,6 +197,31 @@ def c5(seed: int = 5, n_frames: int = 256, n_lo: int = 1000, n_hi: int = 200_000
 
 
 C5_PARAMS = dict(r_max=1.5, rdf_bins=200, rdf_r_max=3.0, rdf_r_min=0.0, l=6)
+
+
+@dataclass
+class OrientedFrame:
+    box: Box
+    points: np.ndarray   # (N, 3) float32, z = 0
+    theta: np.ndarray    # (N,) float32 orientation angles about z
+
+
+def p6(seed: int = 6, n: int = 20_000, n_frames: int = 10, neighbors: float = 12.0, r: float = 1.0,
+       xy: float = 0.0) -> list[OrientedFrame]:
+    """2D frames of uniform points with `neighbors` expected points inside radius r of a
+    point (density neighbors / (pi r^2)) and uniform orientation angles."""
+    rng = np.random.default_rng(seed)
+    L = math.sqrt(n * math.pi * r * r / neighbors)
+    box = Box.square(L, xy)
+    out = []
+    for _ in range(n_frames):
+        pts = uniform_points(rng, box, n)
+        theta = rng.uniform(-math.pi, math.pi, size=n).astype(np.float32)
+        out.append(OrientedFrame(box, pts, theta))
+    return out
+
+
+P6_PARAMS = dict(x_max=1.0, y_max=1.0, bins_x=100, bins_y=100, rdf_bins=100, rdf_r_max=1.0)
 
 
 def small_random(seed: int, n: int, box: Box) -> np.ndarray:
