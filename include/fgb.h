@@ -10,12 +10,18 @@
  *     the lowest level, NeighborList as stored query results).
  *   - RDF: the density module ("Analysis Modules"), histogram accumulated over frames
  *     with reset=False ("Implementation", Compute classes).
+ *   - PMFT(x, y): the pmft module (Section "Potentials of Mean Force and Torque").
  *   - Steinhardt q_l: the order module ("Analysis Modules", bond-orientational order
  *     parameters of Steinhardt et al. 1983).
  *
  * Conventions for every call:
  *   - Box params (Lx, Ly, Lz, xy, xz, yz): a1 = (Lx,0,0), a2 = (xy Ly, Ly, 0),
  *     a3 = (xz Lz, yz Lz, Lz); the box spans M (s - 1/2) for s in [0,1)^3.
+ *     Lz = 0 is a 2D box (Section "Implementation": two- or three-dimensional boxes):
+ *     xz = yz = 0 (INVALID_ARG otherwise), there is no periodicity along z, the
+ *     smallest width is the parallelogram's, and every point and query point must have
+ *     z = 0 (results for other z are unspecified but memory-safe).  The RDF of a 2D
+ *     system uses the box area and annulus shells.
  *   - Points are device pointers to float32 arrays of shape (n, 3), row-major
  *     (x0 y0 z0 x1 ...), owned by the caller; they must stay valid and unchanged for
  *     the lifetime of any handle built from them.  Points may lie outside the box.
@@ -68,6 +74,7 @@ typedef struct fgb_rdf fgb_rdf;
 typedef struct fgb_steinhardt fgb_steinhardt;
 typedef struct fgb_clusters fgb_clusters;
 typedef struct fgb_batch fgb_batch;
+typedef struct fgb_pmft fgb_pmft;
 
 /* ------------------------------------------------------------- library state */
 
@@ -198,14 +205,16 @@ void fgb_rdf_destroy(fgb_rdf *rdf);
  * nlist == NULL: fused cell-list query; pairs are never stored; query_points == NULL
  * means the NeighborQuery's own points with exclude_ii (each unordered pair is visited
  * once and counted twice).  nlist != NULL: histogram of the list's pairs (distances
- * recomputed and decided exactly).  Asynchronous on `stream`.
+ * recomputed and decided exactly).  Frames of one accumulation share a dimension (2D or
+ * 3D; INVALID_ARG otherwise).  Asynchronous on `stream`.
  */
 int fgb_rdf_compute(fgb_rdf *rdf, fgb_nq *nq, const float *query_points, int64_t n_query,
                     const fgb_nlist *nlist, int32_t reset, void *stream);
 
 /*
  * Copies the accumulated counts (uint64, bins), g(r) (float64, bins; counts divided by
- * sum over frames of N_query (N_points / V) (4 pi/3)(R_{b+1}^3 - R_b^3)) and bin centres
+ * sum over frames of N_query (N_points / V) (4 pi/3)(R_{b+1}^3 - R_b^3); for 2D frames
+ * V is the box area and the shell pi (R_{b+1}^2 - R_b^2)) and bin centres
  * r_min + (b + 1/2) (r_max - r_min)/bins to host arrays (any may be NULL).  Synchronises
  * `stream`.
  */
@@ -239,6 +248,52 @@ int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
  */
 int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t n, int32_t bins, double r_max, double r_min,
                     uint64_t *counts, void *stream);
+
+/* ------------------------------------------------------------------------ PMFT */
+
+/*
+ * Potential of mean force and torque in the plane, PMFT(x, y) (pmft module; Section
+ * "Potentials of Mean Force and Torque": the PMFT relation, a histogram of the relative
+ * configurations accumulated over frames and its negative logarithm; Fig. 6 benchmarks
+ * it against the RDF on a 2D system).  Bins cover [-x_max, x_max) x [-y_max, y_max)
+ * with bins_x x bins_y cells (x major).  Errors: INVALID_ARG for non-positive or
+ * non-finite extents, bin counts <= 0 or more than 2^26 bins.
+ */
+int fgb_pmftxy_create(double x_max, double y_max, int32_t bins_x, int32_t bins_y, fgb_pmft **out);
+void fgb_pmftxy_destroy(fgb_pmft *pmft);
+
+/*
+ * Adds one frame: every bond (i, j), d = x_j - q_i (minimum image), turned by -theta_i
+ * into the frame of query particle i:
+ *   x' = cos(theta_i) d_x + sin(theta_i) d_y,   y' = cos(theta_i) d_y - sin(theta_i) d_x,
+ * is counted in bin (floor((x' + x_max)/dx), floor((y' + y_max)/dy)), dx = 2 x_max/bins_x,
+ * dy = 2 y_max/bins_y, when it lies inside the bin rectangle; every bond is decided in
+ * FP64 from the defining displacement (cos and sin of the float32 angle in FP64).
+ *   nq: a NeighborQuery over a 2D box (INVALID_ARG otherwise).
+ *   query_points: device float32 (n_query, 3), or NULL for nq's own points (then
+ *     n_query must equal the point count and bonds exclude i == j).
+ *   query_orientations: device float32 (n_query) angles theta_i about z, in radians.
+ *   nlist: the bonds (query indices address the query points, point indices nq's
+ *     points), or NULL for the ball query with r_max = sqrt(x_max^2 + y_max^2), which
+ *     holds every bond that can land in a bin.
+ *   reset != 0 clears the histogram first (freud's compute(..., reset=False) otherwise).
+ * Errors: BOX_TOO_SMALL when sqrt(x_max^2 + y_max^2) >= half the smallest box width;
+ * INVALID_ARG for NULL or mismatched arguments.  Asynchronous on `stream` with a list;
+ * without one the internal ball query synchronises it once.
+ */
+int fgb_pmftxy_compute(fgb_pmft *pmft, fgb_nq *nq, const float *query_points, const float *query_orientations,
+                       int64_t n_query, const fgb_nlist *nlist, int32_t reset, void *stream);
+
+/*
+ * Host copies (any may be NULL) of the accumulated counts (uint64), the pair
+ * correlation pcf = counts / (norm * bin area), norm = sum over frames of
+ * N_query N_points / (box area), and PMFT = -log(pcf) in units of k_B T (+infinity for
+ * an empty bin); each bins_x * bins_y, x major.  Synchronises `stream`.
+ */
+int fgb_pmftxy_result(const fgb_pmft *pmft, uint64_t *counts, double *pcf, double *pmft_values, void *stream);
+
+/* Device pointer of the uint64 accumulator (bins_x * bins_y entries, x major). */
+int fgb_pmftxy_counts_device(const fgb_pmft *pmft, const uint64_t **counts);
 
 /* ----------------------------------------------------------------- Steinhardt */
 

@@ -83,6 +83,11 @@ _SIGS = {
     "fgb_rdf_counts_device": (_I32, [_P, _PP]),
     "fgb_rdf_escalations": (_I32, [_P, ctypes.POINTER(_I64), _P]),
     "fgb_rdf_noalloc": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _I32, _D, _D, _P, _P]),
+    "fgb_pmftxy_create": (_I32, [_D, _D, _I32, _I32, _PP]),
+    "fgb_pmftxy_destroy": (None, [_P]),
+    "fgb_pmftxy_compute": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P]),
+    "fgb_pmftxy_result": (_I32, [_P, _P, _P, _P, _P]),
+    "fgb_pmftxy_counts_device": (_I32, [_P, _PP]),
     "fgb_steinhardt_create": (_I32, [_I32, _PP]),
     "fgb_steinhardt_destroy": (None, [_P]),
     "fgb_steinhardt_compute": (_I32, [_P, _P, _P, ctypes.POINTER(fgb_query_args), _P, _P]),
@@ -211,7 +216,8 @@ def _view(ptr, shape, dtype, owner) -> torch.Tensor:
 
 @dataclass
 class Box:
-    """Triclinic periodic box (Lx, Ly, Lz, xy, xz, yz), centred on the origin."""
+    """Triclinic periodic box (Lx, Ly, Lz, xy, xz, yz), centred on the origin.  Lz = 0 is
+    a 2D box (xz = yz = 0, every point at z = 0)."""
     Lx: float
     Ly: float
     Lz: float
@@ -241,6 +247,14 @@ class Box:
     @property
     def volume(self) -> float:
         return self.Lx * self.Ly * self.Lz
+
+    @property
+    def is2D(self) -> bool:
+        return self.Lz == 0.0
+
+    @property
+    def area(self) -> float:
+        return self.Lx * self.Ly
 
 
 # ------------------------------------------------------------------- NeighborQuery
@@ -305,7 +319,10 @@ class NeighborQuery:
             raise ValueError("points must have shape (N, 3)")
         if r_cell is None:
             n = max(1, self.points.shape[0])
-            r_cell = 1.5 * (self.box.volume / n) ** (1.0 / 3.0)
+            if self.box.is2D:
+                r_cell = 1.5 * (self.box.area / n) ** 0.5
+            else:
+                r_cell = 1.5 * (self.box.volume / n) ** (1.0 / 3.0)
         self.r_cell = float(r_cell)
         h = ctypes.c_void_p()
         b = self.box._c()
@@ -436,6 +453,69 @@ class RDF:
         _check(lib().fgb_rdf_escalations(self._h, ctypes.byref(n), _stream()))
         return n.value
 
+
+# ------------------------------------------------------------------------------ PMFT
+
+
+class PMFTXY:
+    """PMFT(x, y) of a 2D system accumulated over frames (freud pmft.PMFTXY): every bond
+    in the frame of its query particle (orientation angle about z), binned on
+    [-x_max, x_max) x [-y_max, y_max); `bins` is one count or (bins_x, bins_y)."""
+
+    def __init__(self, x_max: float, y_max: float, bins):
+        bx, by = (bins, bins) if np.isscalar(bins) else bins
+        self.x_max, self.y_max, self.bins = float(x_max), float(y_max), (int(bx), int(by))
+        h = ctypes.c_void_p()
+        _check(lib().fgb_pmftxy_create(self.x_max, self.y_max, self.bins[0], self.bins[1], ctypes.byref(h)))
+        self._o = _Owned(h.value, "fgb_pmftxy_destroy")
+        self._h = self._o.ptr
+
+    def compute(self, system, query_orientations, query_points=None, neighbors=None, reset=True):
+        reach = (self.x_max ** 2 + self.y_max ** 2) ** 0.5
+        nq = _as_nq(system, reach)
+        nl = neighbors if isinstance(neighbors, NeighborList) else None
+        th = _need_cuda(query_orientations, name="query_orientations")
+        qp, n_q = None, nq.n_points
+        if query_points is not None:
+            qpt = _need_cuda(query_points, name="query_points")
+            qp, n_q = qpt.data_ptr(), qpt.shape[0]
+        if th.numel() != n_q:
+            raise ValueError("one orientation per query point")
+        _check(lib().fgb_pmftxy_compute(self._h, nq._h, qp, th.data_ptr(), n_q, nl._h if nl is not None else None,
+                                        int(bool(reset)), _stream()))
+        self._nq = nq
+        return self
+
+    def _result(self):
+        shape = self.bins
+        c = np.zeros(shape, np.uint64)
+        g = np.zeros(shape, np.float64)
+        f = np.zeros(shape, np.float64)
+        _check(lib().fgb_pmftxy_result(self._h, c.ctypes.data, g.ctypes.data, f.ctypes.data, _stream()))
+        return c, g, f
+
+    @property
+    def bin_counts(self) -> np.ndarray:
+        return self._result()[0]
+
+    @property
+    def pcf(self) -> np.ndarray:
+        return self._result()[1]
+
+    @property
+    def pmft(self) -> np.ndarray:
+        return self._result()[2]
+
+    @property
+    def bin_centers(self):
+        bx, by = self.bins
+        dx, dy = 2 * self.x_max / bx, 2 * self.y_max / by
+        return (-self.x_max + (np.arange(bx) + 0.5) * dx, -self.y_max + (np.arange(by) + 0.5) * dy)
+
+    def counts_device(self) -> torch.Tensor:
+        p = ctypes.c_void_p()
+        _check(lib().fgb_pmftxy_counts_device(self._h, ctypes.byref(p)))
+        return _view(p.value, self.bins, torch.int64, self._o)
 
 
 # ------------------------------------------------------------------------ Steinhardt

@@ -84,6 +84,10 @@ struct BoxHost {
     double Minv[3][3];
     double w[3];  // perpendicular widths
     double wmin;
+    // 2D box (Lz = 0 on input, xz = yz = 0, every z coordinate 0): p[2] then holds an
+    // internal thickness of twice the in-plane width, so no z image is ever within a
+    // legal r_max, and the grid gets three z layers with the points in the middle one.
+    int is2d;
     BoxF f;
     BoxD d;
 };

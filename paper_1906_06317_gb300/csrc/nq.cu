@@ -17,11 +17,20 @@ static void split(double v, float &hi, float &lo) {
 
 int make_box(const fgb_box *in, BoxHost *b) {
     if (!in) return fail(FGB_ERR_INVALID_ARG, "box is NULL");
-    const double p[6] = {in->Lx, in->Ly, in->Lz, in->xy, in->xz, in->yz};
+    double p[6] = {in->Lx, in->Ly, in->Lz, in->xy, in->xz, in->yz};
     for (int k = 0; k < 6; ++k)
         if (!std::isfinite(p[k])) return fail(FGB_ERR_INVALID_ARG, "box parameter %d is not finite", k);
-    if (!(p[0] > 0 && p[1] > 0 && p[2] > 0))
-        return fail(FGB_ERR_INVALID_ARG, "box lengths must be positive (2D boxes are not supported)");
+    b->is2d = p[2] == 0.0;
+    if (b->is2d) {
+        // freud's 2D box: Lz = 0.  The plane's widths are Lx Ly / |a2| (across a1's
+        // faces) and Ly; the internal thickness is twice the smaller one.
+        if (p[4] != 0.0 || p[5] != 0.0) return fail(FGB_ERR_INVALID_ARG, "a 2D box (Lz = 0) must have xz = yz = 0");
+        if (!(p[0] > 0 && p[1] > 0)) return fail(FGB_ERR_INVALID_ARG, "box lengths must be positive");
+        const double w0 = p[0] * p[1] / std::sqrt(p[3] * p[1] * p[3] * p[1] + p[1] * p[1]);
+        p[2] = 2.0 * std::fmin(w0, p[1]);
+    } else if (!(p[0] > 0 && p[1] > 0 && p[2] > 0)) {
+        return fail(FGB_ERR_INVALID_ARG, "box lengths must be positive (Lz = 0 for a 2D box)");
+    }
     memcpy(b->p, p, sizeof(p));
     const double a2x = p[3] * p[1], a3x = p[4] * p[2], a3y = p[5] * p[2];
     double M[3][3] = {{p[0], a2x, a3x}, {0.0, p[1], a3y}, {0.0, 0.0, p[2]}};
@@ -41,7 +50,7 @@ int make_box(const fgb_box *in, BoxHost *b) {
         for (int j = 0; j < 3; ++j) s += Mi[k][j] * Mi[k][j];
         b->w[k] = 1.0 / std::sqrt(s);
     }
-    b->wmin = std::fmin(b->w[0], std::fmin(b->w[1], b->w[2]));
+    b->wmin = b->is2d ? std::fmin(b->w[0], b->w[1]) : std::fmin(b->w[0], std::fmin(b->w[1], b->w[2]));
     BoxF &f = b->f;
     for (int k = 0; k < 3; ++k) {
         f.L[k] = (float)p[k];
@@ -96,6 +105,7 @@ int grid_for(const BoxHost &box, double r_cell, int64_t n, GridHost *g) {
             double q = std::floor(box.w[k] / (rc * (1.0 + kCellMargin)));
             int nk = q > 1024.0 ? 1024 : (int)q;
             if (nk < 1) nk = 1;
+            if (k == 2 && box.is2d) nk = 3;  // z layers below, at and above the plane
             g->nc[k] = nk;
             tot *= nk;
         }
@@ -104,8 +114,11 @@ int grid_for(const BoxHost &box, double r_cell, int64_t n, GridHost *g) {
     }
     g->ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
     for (int k = 0; k < 3; ++k) g->wc[k] = box.w[k] / g->nc[k];
+    // Largest cell-local component.  In a 2D box every point has z = 0 and lies in the
+    // middle layer with the same local z, so candidates of the same layer give dz = 0
+    // exactly and the z row adds no error.
     double ext = 0;
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < (box.is2d ? 2 : 3); ++r) {
         double e = 0;
         for (int c = 0; c < 3; ++c) e += std::fabs(box.M[r][c]) * (1.0 / g->nc[c] + 1e-5);
         ext = std::fmax(ext, e);

@@ -55,7 +55,7 @@ int plan_stencil_host(const BoxHost &b, const GridHost &g, double R, int s_table
         for (int k = 0; k < 3; ++k)
             p->ts[k] = std::max(p->s[k], std::min(std::min(s_table_min, kMaxStencil), (g.nc[k] - 1) / 2));
         double offmax = 0;
-        for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < (b.is2d ? 2 : 3); ++r) {  // 2D: pairs come from the z = 0 layer only
             double e = 0;
             for (int c = 0; c < 3; ++c) e += std::fabs(b.M[r][c]) * p->ts[c] / g.nc[c];
             offmax = std::max(offmax, e);

@@ -21,7 +21,8 @@ struct fgb_rdf {
     unsigned long long *hist;  // device, bins
     double *T;                 // device, exact r2 thresholds of the bins+1 edges
     std::vector<double> T_host;
-    double norm;               // sum over frames of N_query * N_points / V
+    double norm;               // sum over frames of N_query * N_points / V (area in 2D)
+    int dim;                   // 2 or 3 once a frame is accumulated, 0 before
     float2 *band;              // device, FP32 bands around the edges
     double band_delta;
     int2 *esc;
@@ -468,6 +469,9 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
     if (!(R < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
         return fail(FGB_ERR_BOX_TOO_SMALL, "RDF r_max=%g must be below half the smallest box width (%g)", R,
                     0.5 * nq->box.wmin);
+    const int dim = nq->box.is2d ? 2 : 3;
+    if (!reset && r->dim != 0 && r->dim != dim)
+        return fail(FGB_ERR_INVALID_ARG, "an RDF accumulates frames of one dimension (reset to switch)");
     QueryPoints Q;
     FGB_TRY(prepare_queries(nq, nlist ? nullptr : query_points, n_query, s, &Q));
     const int64_t nqq = nlist ? nlist->n_query : Q.n;
@@ -553,7 +557,11 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
             dfree(plan.table, s);
         }
     }
-    if (st == FGB_OK) r->norm += (double)nqq * (double)nq->n / (nq->box.p[0] * nq->box.p[1] * nq->box.p[2]);
+    if (st == FGB_OK) {
+        const double V = nq->box.p[0] * nq->box.p[1] * (dim == 2 ? 1.0 : nq->box.p[2]);
+        r->norm += (double)nqq * (double)nq->n / V;
+        r->dim = dim;
+    }
     release_queries(&Q, s);
     return st;
 }
@@ -572,7 +580,7 @@ extern "C" int fgb_rdf_result(fgb_rdf *r, uint64_t *counts, double *rdf_values, 
         if (counts) counts[b] = h[b];
         const double R0 = r->r_min + b * delta;
         const double R1 = b + 1 < r->bins ? r->r_min + (b + 1) * delta : r->r_max;
-        const double shell = 4.0 / 3.0 * M_PI * (R1 * R1 * R1 - R0 * R0 * R0);
+        const double shell = r->dim == 2 ? M_PI * (R1 * R1 - R0 * R0) : 4.0 / 3.0 * M_PI * (R1 * R1 * R1 - R0 * R0 * R0);
         if (rdf_values) rdf_values[b] = r->norm > 0 ? (double)h[b] / (r->norm * shell) : 0.0;
         if (bin_centers) bin_centers[b] = r->r_min + (b + 0.5) * delta;
     }
