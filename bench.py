@@ -376,6 +376,53 @@ def timed(fn, stream, flush, reps=5, warm=2):
     return statistics.median(out)
 
 
+def pmft_components(fgb, torch, dev, stream, flush):
+    """PMFT(x, y) next to the RDF on 2D systems (the comparison of Fig. 6): the paper's
+    10 frames x 20,000 points at 12 neighbours per unit disc, PMFT on [-1, 1)^2 with
+    100 x 100 bins and the RDF with 100 bins out to the PMFT's reach sqrt(2), each frame
+    with its own cell list; then one 4,194,304-point frame at the same density."""
+    comp = {}
+    prm = W.P6_PARAMS
+    xm, ym, bx, by = prm["x_max"], prm["y_max"], prm["bins_x"], prm["bins_y"]
+    reach = math.hypot(xm, ym)
+    frames = W.p6()
+    fx = [(f.box, torch.from_numpy(f.points).to(dev), torch.from_numpy(f.theta).to(dev)) for f in frames]
+    pm = fgb.PMFTXY(xm, ym, (bx, by))
+    rdf = fgb.RDF(bx, reach)
+
+    def p6_pmft():
+        for k, (b, x, t) in enumerate(fx):
+            pm.compute(fgb.NeighborQuery(b, x, r_cell=reach), t, reset=(k == 0))
+
+    def p6_rdf():
+        for k, (b, x, t) in enumerate(fx):
+            rdf.compute(fgb.NeighborQuery(b, x, r_cell=reach), reset=(k == 0))
+
+    t_pm, t_rdf = timed(p6_pmft, stream, flush), timed(p6_rdf, stream, flush)
+    comp["p6_fig6_10x20000_pmft_ms"] = t_pm
+    comp["p6_fig6_10x20000_rdf_ms"] = t_rdf
+    comp["p6_pmft_over_rdf"] = t_pm / t_rdf
+    # one large 2D frame: the fused kernels' throughput in bonds within reach per second
+    n = 4_194_304
+    big = W.p6(seed=61, n=n, n_frames=1)[0]
+    xb, tb = torch.from_numpy(big.points).to(dev), torch.from_numpy(big.theta).to(dev)
+    nqb = fgb.NeighborQuery(big.box, xb, r_cell=reach)
+    bonds = nqb.query(None, dict(r_max=reach, exclude_ii=True)).toNeighborList().n_pairs
+    t_big = timed(lambda: pm.compute(nqb, tb, reset=True), stream, flush)
+    esc = pm.escalations()
+    t_bigr = timed(lambda: rdf.compute(nqb, reset=True), stream, flush)
+    nl_holder = {}
+
+    def list_route():
+        nl_holder["nl"] = nqb.query(None, dict(r_max=reach * (1 + 1e-6), exclude_ii=True)).toNeighborList()
+        pm.compute(nqb, tb, neighbors=nl_holder["nl"], reset=True)
+
+    t_list = timed(list_route, stream, flush, reps=3, warm=1)
+    comp["pmft_2d_4M"] = {"pmft_ms": t_big, "rdf_ms": t_bigr, "pmft_list_route_ms": t_list, "bonds": bonds,
+                          "pmft_bonds_per_s": bonds / t_big * 1e3, "escalated": esc}
+    return comp
+
+
 def extras(fgb, torch, dev, stream, flush):
     comp = {}
     # kNN k=12 on the same 4M-point workload; cells about 1.35x the mean 12th-neighbor
@@ -478,6 +525,7 @@ def extras(fgb, torch, dev, stream, flush):
 
     comp["c2_rdf_ms"] = timed(c2_rdf, stream, flush)
     comp["c2_nl_pairs"] = holder["nl"].n_pairs
+    comp.update(pmft_components(fgb, torch, dev, stream, flush))
     holder.clear()
     # batched frames
     if hasattr(fgb.lib(), "fgb_batch_run"):

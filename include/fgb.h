@@ -274,12 +274,14 @@ void fgb_pmftxy_destroy(fgb_pmft *pmft);
  *     n_query must equal the point count and bonds exclude i == j).
  *   query_orientations: device float32 (n_query) angles theta_i about z, in radians.
  *   nlist: the bonds (query indices address the query points, point indices nq's
- *     points), or NULL for the ball query with r_max = sqrt(x_max^2 + y_max^2), which
- *     holds every bond that can land in a bin.
+ *     points), or NULL for every pair (i != j for self queries): all bonds within
+ *     R = (1 + 1e-6) sqrt(x_max^2 + y_max^2), which holds every bond that can land in a
+ *     bin.  Self queries on a cell list take a fused kernel (pairs never stored; FP32
+ *     with a proven margin from every edge, the rest in FP64); others build that list
+ *     internally (which synchronises `stream` once).
  *   reset != 0 clears the histogram first (freud's compute(..., reset=False) otherwise).
- * Errors: BOX_TOO_SMALL when sqrt(x_max^2 + y_max^2) >= half the smallest box width;
- * INVALID_ARG for NULL or mismatched arguments.  Asynchronous on `stream` with a list;
- * without one the internal ball query synchronises it once.
+ * Errors: BOX_TOO_SMALL when R >= half the smallest box width; INVALID_ARG for NULL or
+ * mismatched arguments.  Asynchronous on `stream` otherwise.
  */
 int fgb_pmftxy_compute(fgb_pmft *pmft, fgb_nq *nq, const float *query_points, const float *query_orientations,
                        int64_t n_query, const fgb_nlist *nlist, int32_t reset, void *stream);
@@ -294,6 +296,10 @@ int fgb_pmftxy_result(const fgb_pmft *pmft, uint64_t *counts, double *pcf, doubl
 
 /* Device pointer of the uint64 accumulator (bins_x * bins_y entries, x major). */
 int fgb_pmftxy_counts_device(const fgb_pmft *pmft, const uint64_t **counts);
+
+/* Bonds the last compute's fused kernel left to its FP64 pass (0 for the list route);
+ * synchronises `stream`. */
+int fgb_pmftxy_escalations(fgb_pmft *pmft, int64_t *n, void *stream);
 
 /* ----------------------------------------------------------------- Steinhardt */
 

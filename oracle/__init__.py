@@ -519,9 +519,10 @@ def pmftxy(box, points, theta, x_max, y_max, bins_x, bins_y, query_points=None, 
            with_xy=False):
     """PMFT(x, y) bin counts (int64, (bins_x, bins_y), x major): every bond (i, j) of the
     list in the frame of query particle i (orientation angle theta[i] about z), counted in
-    [-x_max, x_max) x [-y_max, y_max).  Without a list the bonds are those of the ball
-    query with r_max = sqrt(x_max^2 + y_max^2) (exclude_ii when query_points is None),
-    which holds every bond that can land in a bin.  with_xy also returns the rotated bond
+    [-x_max, x_max) x [-y_max, y_max).  Without a list the bonds are every pair (i != j
+    when query_points is None); only those within sqrt(x_max^2 + y_max^2) can land in a
+    bin, so the ball query at (1 + 1e-6) times that radius supplies them (the factor
+    keeps a bond at the corner whatever the rounding of its rotation).  with_xy also returns the rotated bond
     (x', y') per bond and the bonds (qi, pj)."""
     b = _box(box)
     pts = _pts(points)
@@ -529,7 +530,7 @@ def pmftxy(box, points, theta, x_max, y_max, bins_x, bins_y, query_points=None, 
     th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
     assert th.shape == (len(qpts),)
     if qi is None:
-        r = math.sqrt(x_max * x_max + y_max * y_max)
+        r = math.sqrt(x_max * x_max + y_max * y_max) * (1.0 + 1e-6)
         _, off, pj, _ = ball_query(b, pts, r, exclude_ii=query_points is None, query_points=query_points)
         qi = np.repeat(np.arange(len(qpts), dtype=np.int64), np.diff(off))
     qi = np.ascontiguousarray(np.asarray(qi, dtype=np.int64))

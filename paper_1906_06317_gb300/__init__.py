@@ -88,6 +88,7 @@ _SIGS = {
     "fgb_pmftxy_compute": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P]),
     "fgb_pmftxy_result": (_I32, [_P, _P, _P, _P, _P]),
     "fgb_pmftxy_counts_device": (_I32, [_P, _PP]),
+    "fgb_pmftxy_escalations": (_I32, [_P, ctypes.POINTER(_I64), _P]),
     "fgb_steinhardt_create": (_I32, [_I32, _PP]),
     "fgb_steinhardt_destroy": (None, [_P]),
     "fgb_steinhardt_compute": (_I32, [_P, _P, _P, ctypes.POINTER(fgb_query_args), _P, _P]),
@@ -471,7 +472,7 @@ class PMFTXY:
         self._h = self._o.ptr
 
     def compute(self, system, query_orientations, query_points=None, neighbors=None, reset=True):
-        reach = (self.x_max ** 2 + self.y_max ** 2) ** 0.5
+        reach = (self.x_max ** 2 + self.y_max ** 2) ** 0.5 * (1.0 + 1e-6)
         nq = _as_nq(system, reach)
         nl = neighbors if isinstance(neighbors, NeighborList) else None
         th = _need_cuda(query_orientations, name="query_orientations")
@@ -516,6 +517,11 @@ class PMFTXY:
         p = ctypes.c_void_p()
         _check(lib().fgb_pmftxy_counts_device(self._h, ctypes.byref(p)))
         return _view(p.value, self.bins, torch.int64, self._o)
+
+    def escalations(self) -> int:
+        n = _I64()
+        _check(lib().fgb_pmftxy_escalations(self._h, ctypes.byref(n), _stream()))
+        return n.value
 
 
 # ------------------------------------------------------------------------ Steinhardt

@@ -10,20 +10,27 @@
 // accumulates over calls (reset = 0) like the RDF; pcf = counts / (norm * bin area) with
 // norm = sum over frames of N_query N_points / A, and the PMFT is -log(pcf).
 //
-// Binning turns real numbers into integers, so every bond is decided in FP64 from the
-// defining FP64 displacement (exact_disp) with (cos, sin) of the FP32 angle in FP64.
+// The definition is FP64: the defining minimum-image displacement (exact_disp), cos and
+// sin of the float32 angle in FP64, then the rotation and the bin index above, each
+// operation rounded once.  The fused kernel decides a bond in FP32 only when a proven
+// error bound keeps it clear of every bin edge, and hands the rest to that FP64 sequence.
 #include <cmath>
 #include <cstring>
 #include <vector>
 
-#include "fgb_device.cuh"
+#include "fgb_tile.cuh"
 
 struct fgb_pmft {
     double x_max, y_max;
     int bx, by;
     unsigned long long *hist;  // device, bx * by, x major
-    double2 *trig;             // device, (cos, sin) of the query orientations
+    double2 *trig;             // device, (cos, sin) of the query orientations, FP64
+    float2 *trig32;            // device, the same rounded to FP32, in cell-sorted order
     int64_t trig_cap;
+    int2 *esc;                 // bonds (query, point) left to the FP64 pass
+    int esc_cap;
+    unsigned *ctl;             // device [0] escalated bonds, [1] work counter
+    int64_t last_esc;
     double norm;               // sum over frames of N_query * N_points / area
     cudaStream_t stream;
 };
@@ -53,6 +60,19 @@ __device__ __forceinline__ int pmft_bin64(const PmftBins &B, double2 cs, double3
     return ix * B.by + iy;
 }
 
+// (cos, sin) of every orientation in FP64 by original index, and rounded to FP32 by
+// sorted position of the cell list (the fused kernel reads them next to the records).
+__global__ void k_pmft_trig_sorted(const float4 *__restrict__ sorted, const float *__restrict__ theta, int64_t n,
+                                   double2 *__restrict__ out64, float2 *__restrict__ out32) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int i = __float_as_int(__ldg(&sorted[p].w));
+    double s, c;
+    sincos((double)__ldg(theta + i), &s, &c);
+    out64[i] = make_double2(c, s);
+    out32[p] = make_float2((float)c, (float)s);
+}
+
 // One thread per bond of a NeighborList (query_point_indices address qp and trig).
 __global__ void k_pmft_list(BoxD bd, const float *__restrict__ p, const float *__restrict__ qp,
                             const double2 *__restrict__ trig, const int32_t *__restrict__ qi,
@@ -63,6 +83,226 @@ __global__ void k_pmft_list(BoxD bd, const float *__restrict__ p, const float *_
         const double3 d = exact_disp(bd, qp + 3 * (int64_t)i, p + 3 * (int64_t)j);
         const int b = pmft_bin64(B, __ldg(trig + i), d);
         if (b >= 0) atomicAdd(hist + b, 1ull);
+    }
+}
+
+// ------------------------------------------------------------------ fused cell tiles
+//
+// Self bonds on the cell list's shift route, in the scheme of the RDF tile kernel:
+// persistent warps take query cells A from a work counter (2D grids: only the layer
+// holding the points), the half stencil's candidates stream through the lanes while the
+// warp loops over A's queries, and every unordered pair within reach is binned twice:
+// q -> c in q's frame and c -> q (the negated bond) in c's frame.  The block's warps
+// share one shared histogram of 32-bit counts.
+
+constexpr int kPmftTileWarps = 8;
+constexpr int kPmftTileQ = 32;
+constexpr int kPmftTileMaxBins = 16384;
+
+struct PmftTileArgs {
+    TileArgs t;
+    PmftBins B;
+    const float2 *cs32;        // sorted position -> (cos, sin) FP32
+    const double2 *cs64;       // original index -> (cos, sin) FP64
+    float reach2;              // FP32 bound: a bond beyond it lands in no bin
+    float inv_dx, inv_dy, off_x, off_y;
+    float mx, my;              // decision margins, in bins
+    int bins;
+    int cell_lo, cell_hi;      // query cells walked
+    unsigned long long *hist;
+    int2 *esc;
+    int esc_cap;
+    unsigned *ctl;             // [0] escalated, [1] work
+};
+
+// A bond the fast test left open: listed for the FP64 pass, or decided here in FP64 when
+// the list is full.
+__device__ __noinline__ void pmft_tile_slow(const PmftTileArgs *ap, int i, int j) {
+    const PmftTileArgs &a = *ap;
+    const unsigned slot = atomicAdd(a.ctl, 1u);
+    if (slot < (unsigned)a.esc_cap) {
+        a.esc[slot] = make_int2(i, j);
+    } else {
+        const double3 d = exact_disp(a.t.bd, a.t.p_orig + 3 * (int64_t)i, a.t.p_orig + 3 * (int64_t)j);
+        const int b = pmft_bin64(a.B, __ldg(a.cs64 + i), d);
+        if (b >= 0) atomicAdd(a.hist + b, 1ull);
+    }
+}
+
+// Bin of a bond at (tx, ty) in bin units (t = (x' + x_max) / dx in FP32): >= 0 decided
+// inside, -1 decided outside, -2 open.  An axis is decided when the fraction of t keeps
+// the margin from both edges; a decided axis outside the range settles the bond.
+__device__ __forceinline__ int pmft_fast_bin(const PmftTileArgs &a, float tx, float ty) {
+    const float fx = floorf(tx), fy = floorf(ty);
+    const float rx = tx - fx, ry = ty - fy;
+    const bool okx = rx > a.mx && rx < 1.f - a.mx, oky = ry > a.my && ry < 1.f - a.my;
+    const bool inx = fx >= 0.f && fx < (float)a.B.bx, iny = fy >= 0.f && fy < (float)a.B.by;
+    if ((okx && !inx) || (oky && !iny)) return -1;
+    if (okx && oky) return (int)fx * a.B.by + (int)fy;
+    return -2;
+}
+
+// One staged candidate (x, y, index j, its (cos, sin)) against the queries [0, nq) of
+// the pass.  CENTER: the candidate may be one of A's own points, valid only against
+// queries before it (tl < lim).  Returns nothing; counts go to the shared histogram.
+template <bool CENTER>
+__device__ __forceinline__ void pmft_tile_rounds(const PmftTileArgs &a, const float4 *qs, const float2 *qcs, int nq,
+                                                 float cx, float cy, int cj, float2 ccs, int lim, uint32_t *h) {
+    const float r2hi = a.reach2;
+#pragma unroll 2
+    for (int tl = 0; tl < nq; ++tl) {
+        const float4 q = qs[tl];
+        const float dx = cx - q.x, dy = cy - q.y;
+        const float r2 = fmaf(dx, dx, dy * dy);
+        bool in = r2 < r2hi;
+        if (CENTER) in = in && tl < lim;
+        if (in) {
+            const float2 cq = qcs[tl];
+            // q -> c in q's frame
+            const float xq = fmaf(cq.x, dx, cq.y * dy), yq = fmaf(cq.x, dy, -(cq.y * dx));
+            const int b1 = pmft_fast_bin(a, fmaf(xq, a.inv_dx, a.off_x), fmaf(yq, a.inv_dy, a.off_y));
+            if (b1 >= 0)
+                atomicAdd(h + b1, 1u);
+            else if (b1 == -2)
+                pmft_tile_slow(&a, __float_as_int(q.w), cj);
+            // c -> q: the bond -d in c's frame
+            const float xc = -fmaf(ccs.x, dx, ccs.y * dy), yc = -fmaf(ccs.x, dy, -(ccs.y * dx));
+            const int b2 = pmft_fast_bin(a, fmaf(xc, a.inv_dx, a.off_x), fmaf(yc, a.inv_dy, a.off_y));
+            if (b2 >= 0)
+                atomicAdd(h + b2, 1u);
+            else if (b2 == -2)
+                pmft_tile_slow(&a, cj, __float_as_int(q.w));
+        }
+    }
+}
+
+// Adds the shared counts to the global histogram and clears them.  atomicExch takes each
+// count whole while other warps keep adding, so no block barrier is needed.
+__device__ __forceinline__ void pmft_tile_flush(uint32_t *h, int bins, unsigned long long *hist) {
+    const int lane = threadIdx.x & 31;
+    for (int b = lane; b < bins; b += 32) {
+        const uint32_t v = atomicExch(h + b, 0u);
+        if (v) atomicAdd(hist + b, (unsigned long long)v);
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kPmftTileWarps * 32) k_pmft_tile(const __grid_constant__ PmftTileArgs a) {
+    __shared__ TileStencilT<NS> sts[kPmftTileWarps];
+    __shared__ float4 sq[kPmftTileWarps][kPmftTileQ];
+    __shared__ float2 sqcs[kPmftTileWarps][kPmftTileQ];
+    __shared__ float4 sbuf[kPmftTileWarps][64];  // candidates kept after the box test
+    __shared__ float2 sbcs[kPmftTileWarps][64];
+    extern __shared__ uint32_t shist[];          // bins, shared by the block's warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = threadIdx.x; b < a.bins; b += blockDim.x) shist[b] = 0;
+    __syncthreads();
+    TileStencilT<NS> &ts = sts[warp];
+    float4 *qs = sq[warp];
+    float2 *qcs = sqcs[warp];
+    float4 *buf = sbuf[warp];
+    float2 *bcs = sbcs[warp];
+    const unsigned lt = lanemask_lt();
+    // a candidate farther than this from the queries' bounding box reaches none of them
+    const float reach2 = a.reach2 * (1.0f + 1e-5f);
+    // this warp's additions since its last flush bound every shared count's share from
+    // it; flushing at 2^28 keeps the sum over the block's warps below 2^32
+    uint32_t adds = 0;
+    const uint32_t kFlushAt = 1u << 28;
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(a.ctl + 1, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const int64_t A = (int64_t)a.cell_lo + w;
+        if (A >= a.cell_hi) break;
+        const int begA = (int)__ldg(a.t.cell_start + A);
+        const int nA = (int)__ldg(a.t.cell_start + A + 1) - begA;
+        if (nA == 0) continue;
+        int cx, cy, cz;
+        cell_coords((uint32_t)A, a.t.nc, cx, cy, cz);
+        __syncwarp();
+        const int n = tile_stencil(a.t, cx, cy, cz, true, ts);
+        const int total = ts.pre[n];
+        for (int qb = 0; qb < nA; qb += kPmftTileQ) {
+            const int nq = min(kPmftTileQ, nA - qb);
+            __syncwarp();
+            if (lane < nq) {
+                qs[lane] = __ldg(a.t.pts + begA + qb + lane);
+                qcs[lane] = __ldg(a.cs32 + begA + qb + lane);
+            }
+            __syncwarp();
+            float3 blo, bhi;
+            {
+                const float4 q = qs[lane < nq ? lane : 0];
+                warp_box(q.x, q.y, q.z, lane < nq, blo, bhi);
+            }
+            // at most two additions per pair test of this pass
+            const uint32_t pass_adds = 64u * (uint32_t)nq * (uint32_t)((nA + 31) / 32 + (total + 31) / 32 + 1);
+            if (adds > kFlushAt - pass_adds) {
+                pmft_tile_flush(shist, a.bins, a.hist);
+                adds = 0;
+            }
+            adds += pass_adds;
+            // A's own points first (they pair only with earlier queries)
+            for (int base = 0; base < nA; base += 32) {
+                const int k = base + lane;
+                const TileCand c = tile_load(a.t, ts, n, nA, k);
+                const float2 ccs = k < nA ? __ldg(a.cs32 + c.p) : make_float2(0.f, 0.f);
+                pmft_tile_rounds<true>(a, qs, qcs, nq, c.x, c.y, c.j, ccs, k < nA ? k - qb : 0, shist);
+            }
+            // the other cells: candidates out of reach of the whole pass are dropped, the
+            // rest are packed into full chunks (ballot + popc) before the query rounds
+            int cnt = 0;
+            for (int base = nA; base < total; base += 32) {
+                const int k = base + lane;
+                const TileCand c = tile_load(a.t, ts, n, total, k);
+                const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = cnt + __popc(m & lt);
+                    buf[slot] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+                    bcs[slot] = __ldg(a.cs32 + c.p);
+                }
+                cnt += __popc(m);
+                if (cnt >= 32) {
+                    __syncwarp();
+                    const float4 e = buf[lane];
+                    const float2 ecs = bcs[lane];
+                    pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, shist);
+                    const float4 rest = buf[32 + lane];
+                    const float2 rcs = bcs[32 + lane];
+                    __syncwarp();
+                    if (lane < cnt - 32) {
+                        buf[lane] = rest;
+                        bcs[lane] = rcs;
+                    }
+                    __syncwarp();
+                    cnt -= 32;
+                }
+            }
+            if (cnt > 0) {
+                __syncwarp();
+                const float4 e = lane < cnt ? buf[lane] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+                const float2 ecs = lane < cnt ? bcs[lane] : make_float2(0.f, 0.f);
+                pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, shist);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+        const uint32_t v = shist[b];
+        if (v) atomicAdd(a.hist + b, (unsigned long long)v);
+    }
+}
+
+// The bonds the fused kernel left open, decided by the FP64 sequence.
+__global__ void k_pmft_escalated(const __grid_constant__ PmftTileArgs a) {
+    const int m = min((int)min(*a.ctl, (unsigned)a.esc_cap), a.esc_cap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        const int2 ij = a.esc[e];
+        const double3 d = exact_disp(a.t.bd, a.t.p_orig + 3 * (int64_t)ij.x, a.t.p_orig + 3 * (int64_t)ij.y);
+        const int b = pmft_bin64(a.B, __ldg(a.cs64 + ij.x), d);
+        if (b >= 0) atomicAdd(a.hist + b, 1ull);
     }
 }
 
@@ -91,7 +331,101 @@ extern "C" void fgb_pmftxy_destroy(fgb_pmft *P) {
     if (!P) return;
     dfree(P->hist, P->stream);
     dfree(P->trig, P->stream);
+    dfree(P->trig32, P->stream);
+    dfree(P->esc, P->stream);
+    dfree(P->ctl, P->stream);
     delete P;
+}
+
+// Queries and bonds farther than this reach no bin (the corner bond at exactly
+// sqrt(x_max^2 + y_max^2) included, whatever the rounding of its rotation).
+static double pmft_query_radius(const fgb_pmft *P) {
+    return std::sqrt(P->x_max * P->x_max + P->y_max * P->y_max) * (1.0 + 1e-6);
+}
+
+static int pmft_launch_tile(fgb_pmft *P, fgb_nq *nq, const StencilPlan &plan, double R, const PmftBins &B, int nhalf,
+                            cudaStream_t s) {
+    PmftTileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.t = tile_args(nq, plan, R, 1);
+    a.B = B;
+    a.cs32 = P->trig32;
+    a.cs64 = P->trig;
+    const double delta = r2_error_bound(plan, R);
+    float lo, hi;
+    band_around(R * R, delta, &lo, &hi);
+    a.reach2 = std::nextafter(hi * (1.0f + 1e-6f), INFINITY);
+    a.inv_dx = (float)(1.0 / B.dx);
+    a.inv_dy = (float)(1.0 / B.dy);
+    a.off_x = 0.5f * (float)B.bx;  // x_max / dx, exact
+    a.off_y = 0.5f * (float)B.by;
+    // Error of x' = cos d_x + sin d_y in FP32 against the FP64 definition, for |d| <= R:
+    // (cos, sin) rounded from FP64 (u each), the displacement (eps_d per component, times
+    // |cos| + |sin| <= sqrt 2), the product and the fused add (u |d| each): at most
+    // 3.5 u R + 1.5 eps_d, doubled, plus the FP64 sequence's own rounding.  In bin units
+    // the index t = x' / dx + bins / 2 adds the rounding of 1/dx and of the fused add.
+    const double u = std::ldexp(1.0, -24);
+    const double E = 2.0 * (3.5 * u * R + 1.5 * plan.eps_d) + 1e-12 * (R + plan.Lsum);
+    a.mx = (float)(2.0 * (E / B.dx + u * B.bx * (R / B.x_max + 1.0)) + 1e-7);
+    a.my = (float)(2.0 * (E / B.dy + u * B.by * (R / B.y_max + 1.0)) + 1e-7);
+    a.bins = B.bx * B.by;
+    const int64_t layer = (int64_t)nq->grid.nc[0] * nq->grid.nc[1];
+    a.cell_lo = nq->box.is2d ? (int)layer : 0;  // 2D: the points sit in the middle layer
+    a.cell_hi = nq->box.is2d ? (int)(2 * layer) : (int)nq->grid.ncell;
+    a.hist = P->hist;
+    a.esc = P->esc;
+    a.esc_cap = P->esc_cap;
+    a.ctl = P->ctl;
+    FGB_CUDA(cudaMemsetAsync(P->ctl, 0, 2 * sizeof(unsigned), s));
+    const size_t smem = (size_t)a.bins * sizeof(uint32_t);
+    auto go = [&](auto kern) -> int {
+        // static + dynamic shared memory above 48 KB needs the opt-in
+        FGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPmftTileWarps * 32, smem));
+        const int64_t want = ((int64_t)a.cell_hi - a.cell_lo + kPmftTileWarps - 1) / kPmftTileWarps;
+        const unsigned grid =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * std::max(per_sm, 1)));
+        {
+            FGB_KSCOPE("k_pmft_tile", s);
+            kern<<<grid, kPmftTileWarps * 32, smem, s>>>(a);
+        }
+        FGB_LAUNCH_CHECK();
+        {
+            FGB_KSCOPE("k_pmft_escalated", s);
+            k_pmft_escalated<<<num_sms() * 2, 256, 0, s>>>(a);
+        }
+        FGB_LAUNCH_CHECK();
+        return FGB_OK;
+    };
+    if (nhalf <= 32) return go(k_pmft_tile<32>);
+    if (nhalf <= 64) return go(k_pmft_tile<64>);
+    return go(k_pmft_tile<kTileMaxStencil>);
+}
+
+static int pmft_ensure(fgb_pmft *P, int64_t n, bool sorted, cudaStream_t s) {
+    if (P->trig_cap < n || (sorted && !P->trig32)) {
+        dfree(P->trig, P->stream);
+        dfree(P->trig32, P->stream);
+        P->trig = nullptr;
+        P->trig32 = nullptr;
+        P->trig_cap = 0;
+        FGB_TRY(dalloc_n(&P->trig, n, s));
+        FGB_TRY(dalloc_n(&P->trig32, n, s));
+        P->trig_cap = n;
+    }
+    if (sorted) {
+        const int64_t want = std::min<int64_t>(std::max<int64_t>(n / 8, 1 << 16), 1 << 26);
+        if (P->esc_cap < want) {
+            dfree(P->esc, P->stream);
+            P->esc = nullptr;
+            P->esc_cap = 0;
+            FGB_TRY(dalloc_n(&P->esc, want, s));
+            P->esc_cap = (int)want;
+        }
+        if (!P->ctl) FGB_TRY(dalloc_n(&P->ctl, 2, s));
+    }
+    return FGB_OK;
 }
 
 extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_points, const float *query_orientations,
@@ -104,10 +438,10 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
     if (n_query > 0 && !query_orientations) return fail(FGB_ERR_INVALID_ARG, "query_orientations is NULL");
     if (nlist && (nlist->n_query != n_query || nlist->n_points != nq->n))
         return fail(FGB_ERR_INVALID_ARG, "the neighbor list does not match the query and point counts");
-    const double reach = std::sqrt(P->x_max * P->x_max + P->y_max * P->y_max);
-    if (!(reach < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
+    const double R = pmft_query_radius(P);
+    if (!(R < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
         return fail(FGB_ERR_BOX_TOO_SMALL, "sqrt(x_max^2 + y_max^2) = %g must be below half the smallest box width (%g)",
-                    reach, 0.5 * nq->box.wmin);
+                    R, 0.5 * nq->box.wmin);
     cudaStream_t s = as_stream(stream);
     const size_t nb = (size_t)P->bx * P->by;
     if (!P->hist) {
@@ -119,48 +453,85 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
         FGB_CUDA(cudaMemsetAsync(P->hist, 0, sizeof(unsigned long long) * nb, s));
         P->norm = 0.0;
     }
+    P->last_esc = -1;
+    PmftBins B;
+    B.x_max = P->x_max;
+    B.y_max = P->y_max;
+    B.dx = 2.0 * P->x_max / P->bx;
+    B.dy = 2.0 * P->y_max / P->by;
+    B.bx = P->bx;
+    B.by = P->by;
     if (n_query > 0 && nq->n > 0) {
-        if (P->trig_cap < n_query) {
-            dfree(P->trig, P->stream);
-            P->trig = nullptr;
-            P->trig_cap = 0;
-            FGB_TRY(dalloc_n(&P->trig, n_query, s));
-            P->trig_cap = n_query;
+        // fused route: self bonds on the cell list's shift route, histogram in shared memory
+        bool fused = false;
+        StencilPlan plan;
+        memset(&plan, 0, sizeof(plan));
+        if (!nlist && !query_points && nq->kind == 0 && nb <= (size_t)kPmftTileMaxBins && tile_worth(nq) &&
+            !force_thread_kernels()) {
+            FGB_TRY(plan_stencil(nq, R, 0, s, &plan));
+            const int nfull = (2 * plan.s[0] + 1) * (2 * plan.s[1] + 1) * (2 * plan.s[2] + 1);
+            const int nhalf = (nfull + 1) / 2;
+            fused = plan.mode == 0 && nhalf <= kTileMaxStencil;
+            int st = fused ? pmft_ensure(P, nq->n, true, s) : FGB_OK;
+            if (st == FGB_OK && fused) {
+                {
+                    FGB_KSCOPE("k_pmft_trig_sorted", s);
+                    k_pmft_trig_sorted<<<(unsigned)((nq->n + 255) / 256), 256, 0, s>>>(nq->sorted, query_orientations,
+                                                                                       nq->n, P->trig, P->trig32);
+                }
+                st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "pmft trig launch failed");
+                if (st == FGB_OK) st = pmft_launch_tile(P, nq, plan, R, B, nhalf, s);
+            }
+            dfree(plan.table, s);
+            if (st != FGB_OK) return st;
         }
-        {
-            FGB_KSCOPE("k_pmft_trig", s);
-            k_pmft_trig<<<(unsigned)((n_query + 255) / 256), 256, 0, s>>>(query_orientations, n_query, P->trig);
+        if (!fused) {
+            FGB_TRY(pmft_ensure(P, n_query, false, s));
+            {
+                FGB_KSCOPE("k_pmft_trig", s);
+                k_pmft_trig<<<(unsigned)((n_query + 255) / 256), 256, 0, s>>>(query_orientations, n_query, P->trig);
+            }
+            FGB_LAUNCH_CHECK();
+            fgb_nlist *own = nullptr;
+            if (!nlist) {
+                fgb_query_args qa;
+                qa.r_max = R;
+                qa.num_neighbors = 0;
+                qa.exclude_ii = query_points ? 0 : 1;
+                FGB_TRY(fgb_nq_query(nq, query_points, n_query, &qa, stream, &own));
+                nlist = own;
+            }
+            int st = FGB_OK;
+            if (nlist->n_pairs > 0) {
+                const unsigned grid =
+                    (unsigned)std::min<int64_t>((nlist->n_pairs + 255) / 256, (int64_t)num_sms() * 16);
+                FGB_KSCOPE("k_pmft_list", s);
+                k_pmft_list<<<grid, 256, 0, s>>>(nq->box.d, nq->points, query_points ? query_points : nq->points,
+                                                 P->trig, nlist->qi, nlist->pj, nlist->n_pairs, B, P->hist);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "pmft launch failed: %s", cudaGetErrorString(e));
+            }
+            if (own) fgb_nlist_destroy(own);
+            if (st != FGB_OK) return st;
+        } else {
+            P->last_esc = -2;  // read from the device on request
         }
-        FGB_LAUNCH_CHECK();
-        fgb_nlist *own = nullptr;
-        if (!nlist) {
-            fgb_query_args qa;
-            qa.r_max = reach;
-            qa.num_neighbors = 0;
-            qa.exclude_ii = query_points ? 0 : 1;
-            FGB_TRY(fgb_nq_query(nq, query_points, n_query, &qa, stream, &own));
-            nlist = own;
-        }
-        PmftBins B;
-        B.x_max = P->x_max;
-        B.y_max = P->y_max;
-        B.dx = 2.0 * P->x_max / P->bx;
-        B.dy = 2.0 * P->y_max / P->by;
-        B.bx = P->bx;
-        B.by = P->by;
-        int st = FGB_OK;
-        if (nlist->n_pairs > 0) {
-            const unsigned grid = (unsigned)std::min<int64_t>((nlist->n_pairs + 255) / 256, (int64_t)num_sms() * 16);
-            FGB_KSCOPE("k_pmft_list", s);
-            k_pmft_list<<<grid, 256, 0, s>>>(nq->box.d, nq->points, query_points ? query_points : nq->points, P->trig,
-                                             nlist->qi, nlist->pj, nlist->n_pairs, B, P->hist);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "pmft launch failed: %s", cudaGetErrorString(e));
-        }
-        if (own) fgb_nlist_destroy(own);
-        if (st != FGB_OK) return st;
     }
     P->norm += (double)n_query * (double)nq->n / (nq->box.p[0] * nq->box.p[1]);
+    return FGB_OK;
+}
+
+extern "C" int fgb_pmftxy_escalations(fgb_pmft *P, int64_t *n, void *stream) {
+    clear_error();
+    if (!P || !n) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    *n = 0;
+    if (P->last_esc == -2 && P->ctl) {
+        unsigned v = 0;
+        cudaStream_t s = as_stream(stream);
+        FGB_CUDA(cudaMemcpyAsync(&v, P->ctl, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        FGB_CUDA(cudaStreamSynchronize(s));
+        *n = v;
+    }
     return FGB_OK;
 }
 

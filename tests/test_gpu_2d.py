@@ -206,6 +206,35 @@ def test_pmft_accumulates_fig6_frames(fgb):
     assert np.array_equal(p.counts_device().cpu().numpy(), total)
 
 
+def test_pmft_fused_edges_escalate(fgb):
+    # square lattice of spacing 0.5 with theta = 0 and bins of 0.5: every bond lies on a
+    # bin edge, so the fused kernel must leave them to its FP64 pass
+    g = np.arange(80) * 0.5 - 20.0
+    x = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    x = np.concatenate([x, np.zeros((len(x), 1))], 1).astype(np.float32)
+    b = W.Box.square(40.0)
+    th = np.zeros(len(x), np.float32)
+    p = fgb.PMFTXY(1.5, 1.5, 6)
+    p.compute((b, dev(x)), dev(th))
+    assert p.escalations() > 0
+    assert np.array_equal(p.bin_counts, oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64))
+    # the same lattice turned by 90 degrees per particle: cos is -4.4e-8, not 0
+    th = np.full(len(x), np.pi / 2, np.float32)
+    p.compute((b, dev(x)), dev(th))
+    assert np.array_equal(p.bin_counts, oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64))
+
+
+@pytest.mark.parametrize("bins", [(7, 3), (128, 128), (200, 100)])
+def test_pmft_bin_counts_across_routes(fgb, bins):
+    # the fused kernel keeps at most 16384 bins in shared memory; more take the list route
+    f = W.p6(seed=525, n=20000, n_frames=1)[0]
+    bx, by = bins
+    want, _, _ = pmft_ref(f.box, f.points, f.theta, 1.3, 0.9, bx, by)
+    p = fgb.PMFTXY(1.3, 0.9, bins)
+    p.compute((f.box, dev(f.points)), dev(f.theta))
+    assert np.array_equal(p.bin_counts, want.astype(np.uint64))
+
+
 def test_pmft_errors_and_empty(fgb):
     b3 = W.Box.cube(12.0)
     x3 = dev(W.small_random(530, 100, b3))

@@ -221,7 +221,7 @@ def p6(seed: int = 6, n: int = 20_000, n_frames: int = 10, neighbors: float = 12
     return out
 
 
-P6_PARAMS = dict(x_max=1.0, y_max=1.0, bins_x=100, bins_y=100, rdf_bins=100, rdf_r_max=1.0)
+P6_PARAMS = dict(x_max=1.0, y_max=1.0, bins_x=100, bins_y=100, rdf_bins=100, rdf_r_max=math.sqrt(2.0))
 
 
 def small_random(seed: int, n: int, box: Box) -> np.ndarray:
