@@ -200,6 +200,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=4_194_304,
                     help="points of the uniform workload (smaller cases are for profiling only)")
+    ap.add_argument("--only", choices=["pmft"], default=None,
+                    help="time one group of components alone and print them (profiling runs)")
+    ap.add_argument("--pmft-points", type=int, default=4_194_304, help="points of the large 2D PMFT frame")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -209,6 +212,12 @@ def main():
     import paper_1906_06317_gb300 as fgb
 
     torch.cuda.set_device(local)
+    if args.only == "pmft":
+        dev = torch.device("cuda", local)
+        flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+        comp = pmft_components(fgb, torch, dev, torch.cuda.current_stream(), flush, n_big=args.pmft_points)
+        print(json.dumps({"components": comp}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -376,7 +385,7 @@ def timed(fn, stream, flush, reps=5, warm=2):
     return statistics.median(out)
 
 
-def pmft_components(fgb, torch, dev, stream, flush):
+def pmft_components(fgb, torch, dev, stream, flush, n_big=4_194_304):
     """PMFT(x, y) next to the RDF on 2D systems (the comparison of Fig. 6): the paper's
     10 frames x 20,000 points at 12 neighbours per unit disc, PMFT on [-1, 1)^2 with
     100 x 100 bins and the RDF with 100 bins out to the PMFT's reach sqrt(2), each frame
@@ -403,13 +412,35 @@ def pmft_components(fgb, torch, dev, stream, flush):
     comp["p6_fig6_10x20000_rdf_ms"] = t_rdf
     comp["p6_pmft_over_rdf"] = t_pm / t_rdf
     # one large 2D frame: the fused kernels' throughput in bonds within reach per second
-    n = 4_194_304
+    n = n_big
     big = W.p6(seed=61, n=n, n_frames=1)[0]
     xb, tb = torch.from_numpy(big.points).to(dev), torch.from_numpy(big.theta).to(dev)
     nqb = fgb.NeighborQuery(big.box, xb, r_cell=reach)
     bonds = nqb.query(None, dict(r_max=reach, exclude_ii=True)).toNeighborList().n_pairs
     t_big = timed(lambda: pm.compute(nqb, tb, reset=True), stream, flush)
     esc = pm.escalations()
+    # per-kernel device time of the fused route (CUDA events around each launch)
+    fgb.timing_reset()
+    fgb.timing_enable(True)
+    for _ in range(3):
+        flush.zero_()
+        pm.compute(nqb, tb, reset=True)
+    torch.cuda.synchronize()
+    fgb.timing_enable(False)
+    per = {}
+    for k in ("k_pmft_trig_sorted", "k_pmft_tile", "k_pmft_escalated"):
+        t, c = fgb.timing_read(k)
+        per[k] = t / max(c, 1)
+    peaks = measured_peaks()
+    sm_clock = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12
+    # 32 FP32 operations per unordered pair within reach: displacement 2, r^2 2, and per
+    # direction rotation 4, bin index 2, floor 2, fraction 2, margin tests 4
+    ops = 32.0 * (bonds / 2) / 1e12
+    tile_s = per["k_pmft_tile"] * 1e-3
+    roof = {"kernel": "k_pmft_tile", "bound": "alu", "achieved": ops / tile_s, "peak": alu_peak, "unit": "TOP/s",
+            "frac": ops / tile_s / alu_peak, "ms": per["k_pmft_tile"],
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
     t_bigr = timed(lambda: rdf.compute(nqb, reset=True), stream, flush)
     nl_holder = {}
 
@@ -418,8 +449,9 @@ def pmft_components(fgb, torch, dev, stream, flush):
         pm.compute(nqb, tb, neighbors=nl_holder["nl"], reset=True)
 
     t_list = timed(list_route, stream, flush, reps=3, warm=1)
-    comp["pmft_2d_4M"] = {"pmft_ms": t_big, "rdf_ms": t_bigr, "pmft_list_route_ms": t_list, "bonds": bonds,
-                          "pmft_bonds_per_s": bonds / t_big * 1e3, "escalated": esc}
+    comp["pmft_2d_%dk" % (n // 1024)] = {"points": n, "pmft_ms": t_big, "rdf_ms": t_bigr, "pmft_list_route_ms": t_list, "bonds": bonds,
+                          "pmft_bonds_per_s": bonds / t_big * 1e3, "escalated": esc,
+                                               "kernel_ms": per, "roofline": roof}
     return comp
 
 

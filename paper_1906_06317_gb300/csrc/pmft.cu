@@ -24,9 +24,10 @@ struct fgb_pmft {
     double x_max, y_max;
     int bx, by;
     unsigned long long *hist;  // device, bx * by, x major
-    double2 *trig;             // device, (cos, sin) of the query orientations, FP64
-    float2 *trig32;            // device, the same rounded to FP32, in cell-sorted order
+    double2 *trig;             // device, FP64 (cos, sin) of the query orientations (list route)
     int64_t trig_cap;
+    float2 *trig32;            // device, FP32 (cos, sin) in cell-sorted order (fused route)
+    int64_t trig32_cap;
     int2 *esc;                 // bonds (query, point) left to the FP64 pass
     int esc_cap;
     unsigned *ctl;             // device [0] escalated bonds, [1] work counter
@@ -60,17 +61,23 @@ __device__ __forceinline__ int pmft_bin64(const PmftBins &B, double2 cs, double3
     return ix * B.by + iy;
 }
 
-// (cos, sin) of every orientation in FP64 by original index, and rounded to FP32 by
-// sorted position of the cell list (the fused kernel reads them next to the records).
+// FP32 (cos, sin) of every orientation by sorted position of the cell list (the fused
+// kernel reads them next to the records).  sincosf is within 2 ulp of the exact values.
 __global__ void k_pmft_trig_sorted(const float4 *__restrict__ sorted, const float *__restrict__ theta, int64_t n,
-                                   double2 *__restrict__ out64, float2 *__restrict__ out32) {
+                                   float2 *__restrict__ out32) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int i = __float_as_int(__ldg(&sorted[p].w));
+    float s, c;
+    sincosf(__ldg(theta + i), &s, &c);
+    out32[p] = make_float2(c, s);
+}
+
+// FP64 (cos, sin) of one orientation, as the definition takes them.
+__device__ __forceinline__ double2 trig64(const float *theta, int i) {
     double s, c;
     sincos((double)__ldg(theta + i), &s, &c);
-    out64[i] = make_double2(c, s);
-    out32[p] = make_float2((float)c, (float)s);
+    return make_double2(c, s);
 }
 
 // One thread per bond of a NeighborList (query_point_indices address qp and trig).
@@ -103,7 +110,7 @@ struct PmftTileArgs {
     TileArgs t;
     PmftBins B;
     const float2 *cs32;        // sorted position -> (cos, sin) FP32
-    const double2 *cs64;       // original index -> (cos, sin) FP64
+    const float *theta;        // original index -> orientation angle
     float reach2;              // FP32 bound: a bond beyond it lands in no bin
     float inv_dx, inv_dy, off_x, off_y;
     float mx, my;              // decision margins, in bins
@@ -124,7 +131,7 @@ __device__ __noinline__ void pmft_tile_slow(const PmftTileArgs *ap, int i, int j
         a.esc[slot] = make_int2(i, j);
     } else {
         const double3 d = exact_disp(a.t.bd, a.t.p_orig + 3 * (int64_t)i, a.t.p_orig + 3 * (int64_t)j);
-        const int b = pmft_bin64(a.B, __ldg(a.cs64 + i), d);
+        const int b = pmft_bin64(a.B, trig64(a.theta, i), d);
         if (b >= 0) atomicAdd(a.hist + b, 1ull);
     }
 }
@@ -142,13 +149,56 @@ __device__ __forceinline__ int pmft_fast_bin(const PmftTileArgs &a, float tx, fl
     return -2;
 }
 
+// Rotates and bins one queued pair (both directions).  The pair tests of the rounds
+// leave most lanes out of reach, so pairs within reach are first packed into a per-warp
+// queue and binned 32 at a time with every lane busy.
+__device__ __forceinline__ void pmft_bin_pair(const PmftTileArgs &a, const float4 *qs, const float2 *qcs, float4 e,
+                                              int2 ix, uint32_t *h) {
+    const float dx = e.x, dy = e.y;
+    const float2 cq = qcs[ix.x];
+    // q -> c in q's frame
+    const float xq = fmaf(cq.x, dx, cq.y * dy), yq = fmaf(cq.x, dy, -(cq.y * dx));
+    const int b1 = pmft_fast_bin(a, fmaf(xq, a.inv_dx, a.off_x), fmaf(yq, a.inv_dy, a.off_y));
+    if (b1 >= 0)
+        atomicAdd(h + b1, 1u);
+    else if (b1 == -2)
+        pmft_tile_slow(&a, __float_as_int(qs[ix.x].w), ix.y);
+    // c -> q: the bond -d in c's frame
+    const float xc = -fmaf(e.z, dx, e.w * dy), yc = -fmaf(e.z, dy, -(e.w * dx));
+    const int b2 = pmft_fast_bin(a, fmaf(xc, a.inv_dx, a.off_x), fmaf(yc, a.inv_dy, a.off_y));
+    if (b2 >= 0)
+        atomicAdd(h + b2, 1u);
+    else if (b2 == -2)
+        pmft_tile_slow(&a, ix.y, __float_as_int(qs[ix.x].w));
+}
+
+// Per-warp queue of pairs within reach: (dx, dy, cos c, sin c) and (query slot, c's
+// index); qn entries pending (warp-uniform), at most 31 between rounds.
+struct PmftQueue {
+    float4 *d;
+    int2 *x;
+    int qn;
+};
+
+__device__ __forceinline__ void pmft_queue_drain(const PmftTileArgs &a, const float4 *qs, const float2 *qcs,
+                                                 PmftQueue &Q, uint32_t *h) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane < Q.qn) pmft_bin_pair(a, qs, qcs, Q.d[lane], Q.x[lane], h);
+    __syncwarp();
+    Q.qn = 0;
+}
+
 // One staged candidate (x, y, index j, its (cos, sin)) against the queries [0, nq) of
 // the pass.  CENTER: the candidate may be one of A's own points, valid only against
-// queries before it (tl < lim).  Returns nothing; counts go to the shared histogram.
+// queries before it (tl < lim).  Pairs within reach join the queue.
 template <bool CENTER>
 __device__ __forceinline__ void pmft_tile_rounds(const PmftTileArgs &a, const float4 *qs, const float2 *qcs, int nq,
-                                                 float cx, float cy, int cj, float2 ccs, int lim, uint32_t *h) {
+                                                 float cx, float cy, int cj, float2 ccs, int lim, PmftQueue &Q,
+                                                 uint32_t *h) {
     const float r2hi = a.reach2;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
 #pragma unroll 2
     for (int tl = 0; tl < nq; ++tl) {
         const float4 q = qs[tl];
@@ -156,22 +206,25 @@ __device__ __forceinline__ void pmft_tile_rounds(const PmftTileArgs &a, const fl
         const float r2 = fmaf(dx, dx, dy * dy);
         bool in = r2 < r2hi;
         if (CENTER) in = in && tl < lim;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {
-            const float2 cq = qcs[tl];
-            // q -> c in q's frame
-            const float xq = fmaf(cq.x, dx, cq.y * dy), yq = fmaf(cq.x, dy, -(cq.y * dx));
-            const int b1 = pmft_fast_bin(a, fmaf(xq, a.inv_dx, a.off_x), fmaf(yq, a.inv_dy, a.off_y));
-            if (b1 >= 0)
-                atomicAdd(h + b1, 1u);
-            else if (b1 == -2)
-                pmft_tile_slow(&a, __float_as_int(q.w), cj);
-            // c -> q: the bond -d in c's frame
-            const float xc = -fmaf(ccs.x, dx, ccs.y * dy), yc = -fmaf(ccs.x, dy, -(ccs.y * dx));
-            const int b2 = pmft_fast_bin(a, fmaf(xc, a.inv_dx, a.off_x), fmaf(yc, a.inv_dy, a.off_y));
-            if (b2 >= 0)
-                atomicAdd(h + b2, 1u);
-            else if (b2 == -2)
-                pmft_tile_slow(&a, cj, __float_as_int(q.w));
+            const int slot = Q.qn + __popc(m & lt);  // <= 31 + 31
+            Q.d[slot] = make_float4(dx, dy, ccs.x, ccs.y);
+            Q.x[slot] = make_int2(tl, cj);
+        }
+        Q.qn += __popc(m);
+        if (Q.qn >= 32) {
+            __syncwarp();
+            pmft_bin_pair(a, qs, qcs, Q.d[lane], Q.x[lane], h);
+            const float4 rd = Q.d[32 + lane];
+            const int2 rx = Q.x[32 + lane];
+            __syncwarp();
+            if (lane < Q.qn - 32) {
+                Q.d[lane] = rd;
+                Q.x[lane] = rx;
+            }
+            __syncwarp();
+            Q.qn -= 32;
         }
     }
 }
@@ -187,12 +240,13 @@ __device__ __forceinline__ void pmft_tile_flush(uint32_t *h, int bins, unsigned 
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kPmftTileWarps * 32) k_pmft_tile(const __grid_constant__ PmftTileArgs a) {
+__global__ void __launch_bounds__(kPmftTileWarps * 32, 3) k_pmft_tile(const __grid_constant__ PmftTileArgs a) {
     __shared__ TileStencilT<NS> sts[kPmftTileWarps];
     __shared__ float4 sq[kPmftTileWarps][kPmftTileQ];
     __shared__ float2 sqcs[kPmftTileWarps][kPmftTileQ];
-    __shared__ float4 sbuf[kPmftTileWarps][64];  // candidates kept after the box test
-    __shared__ float2 sbcs[kPmftTileWarps][64];
+    __shared__ float4 sbuf[kPmftTileWarps][64];  // kept candidates: x, y, sorted position, index
+    __shared__ float4 sqd[kPmftTileWarps][64];   // queued pairs
+    __shared__ int2 sqx[kPmftTileWarps][64];
     extern __shared__ uint32_t shist[];          // bins, shared by the block's warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int b = threadIdx.x; b < a.bins; b += blockDim.x) shist[b] = 0;
@@ -201,7 +255,10 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32) k_pmft_tile(const __grid_
     float4 *qs = sq[warp];
     float2 *qcs = sqcs[warp];
     float4 *buf = sbuf[warp];
-    float2 *bcs = sbcs[warp];
+    PmftQueue Q;
+    Q.d = sqd[warp];
+    Q.x = sqx[warp];
+    Q.qn = 0;
     const unsigned lt = lanemask_lt();
     // a candidate farther than this from the queries' bounding box reaches none of them
     const float reach2 = a.reach2 * (1.0f + 1e-5f);
@@ -248,7 +305,7 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32) k_pmft_tile(const __grid_
                 const int k = base + lane;
                 const TileCand c = tile_load(a.t, ts, n, nA, k);
                 const float2 ccs = k < nA ? __ldg(a.cs32 + c.p) : make_float2(0.f, 0.f);
-                pmft_tile_rounds<true>(a, qs, qcs, nq, c.x, c.y, c.j, ccs, k < nA ? k - qb : 0, shist);
+                pmft_tile_rounds<true>(a, qs, qcs, nq, c.x, c.y, c.j, ccs, k < nA ? k - qb : 0, Q, shist);
             }
             // the other cells: candidates out of reach of the whole pass are dropped, the
             // rest are packed into full chunks (ballot + popc) before the query rounds
@@ -258,34 +315,29 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32) k_pmft_tile(const __grid_
                 const TileCand c = tile_load(a.t, ts, n, total, k);
                 const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int slot = cnt + __popc(m & lt);
-                    buf[slot] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
-                    bcs[slot] = __ldg(a.cs32 + c.p);
-                }
+                if (keep) buf[cnt + __popc(m & lt)] = make_float4(c.x, c.y, __int_as_float(c.p), __int_as_float(c.j));
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
                     const float4 e = buf[lane];
-                    const float2 ecs = bcs[lane];
-                    pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, shist);
+                    const float2 ecs = __ldg(a.cs32 + __float_as_int(e.z));
+                    pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, Q, shist);
                     const float4 rest = buf[32 + lane];
-                    const float2 rcs = bcs[32 + lane];
                     __syncwarp();
-                    if (lane < cnt - 32) {
-                        buf[lane] = rest;
-                        bcs[lane] = rcs;
-                    }
+                    if (lane < cnt - 32) buf[lane] = rest;
                     __syncwarp();
                     cnt -= 32;
                 }
             }
             if (cnt > 0) {
                 __syncwarp();
-                const float4 e = lane < cnt ? buf[lane] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
-                const float2 ecs = lane < cnt ? bcs[lane] : make_float2(0.f, 0.f);
-                pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, shist);
+                const bool v = lane < cnt;
+                const float4 e = v ? buf[lane] : make_float4(kFar, kFar, 0.f, __int_as_float(-1));
+                const float2 ecs = v ? __ldg(a.cs32 + __float_as_int(e.z)) : make_float2(0.f, 0.f);
+                pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, Q, shist);
             }
+            // the queue refers to this pass's staged queries: empty it before they change
+            pmft_queue_drain(a, qs, qcs, Q, shist);
         }
     }
     __syncthreads();
@@ -301,7 +353,7 @@ __global__ void k_pmft_escalated(const __grid_constant__ PmftTileArgs a) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
         const int2 ij = a.esc[e];
         const double3 d = exact_disp(a.t.bd, a.t.p_orig + 3 * (int64_t)ij.x, a.t.p_orig + 3 * (int64_t)ij.y);
-        const int b = pmft_bin64(a.B, __ldg(a.cs64 + ij.x), d);
+        const int b = pmft_bin64(a.B, trig64(a.theta, ij.x), d);
         if (b >= 0) atomicAdd(a.hist + b, 1ull);
     }
 }
@@ -344,13 +396,13 @@ static double pmft_query_radius(const fgb_pmft *P) {
 }
 
 static int pmft_launch_tile(fgb_pmft *P, fgb_nq *nq, const StencilPlan &plan, double R, const PmftBins &B, int nhalf,
-                            cudaStream_t s) {
+                            const float *theta, cudaStream_t s) {
     PmftTileArgs a;
     memset(&a, 0, sizeof(a));
     a.t = tile_args(nq, plan, R, 1);
     a.B = B;
     a.cs32 = P->trig32;
-    a.cs64 = P->trig;
+    a.theta = theta;
     const double delta = r2_error_bound(plan, R);
     float lo, hi;
     band_around(R * R, delta, &lo, &hi);
@@ -360,12 +412,12 @@ static int pmft_launch_tile(fgb_pmft *P, fgb_nq *nq, const StencilPlan &plan, do
     a.off_x = 0.5f * (float)B.bx;  // x_max / dx, exact
     a.off_y = 0.5f * (float)B.by;
     // Error of x' = cos d_x + sin d_y in FP32 against the FP64 definition, for |d| <= R:
-    // (cos, sin) rounded from FP64 (u each), the displacement (eps_d per component, times
+    // sincosf (2 ulp, taken as 4u each), the displacement (eps_d per component, times
     // |cos| + |sin| <= sqrt 2), the product and the fused add (u |d| each): at most
-    // 3.5 u R + 1.5 eps_d, doubled, plus the FP64 sequence's own rounding.  In bin units
+    // 8 u R + 1.5 eps_d, doubled, plus the FP64 sequence's own rounding.  In bin units
     // the index t = x' / dx + bins / 2 adds the rounding of 1/dx and of the fused add.
     const double u = std::ldexp(1.0, -24);
-    const double E = 2.0 * (3.5 * u * R + 1.5 * plan.eps_d) + 1e-12 * (R + plan.Lsum);
+    const double E = 2.0 * (8.0 * u * R + 1.5 * plan.eps_d) + 1e-12 * (R + plan.Lsum);
     a.mx = (float)(2.0 * (E / B.dx + u * B.bx * (R / B.x_max + 1.0)) + 1e-7);
     a.my = (float)(2.0 * (E / B.dy + u * B.by * (R / B.y_max + 1.0)) + 1e-7);
     a.bins = B.bx * B.by;
@@ -404,15 +456,19 @@ static int pmft_launch_tile(fgb_pmft *P, fgb_nq *nq, const StencilPlan &plan, do
 }
 
 static int pmft_ensure(fgb_pmft *P, int64_t n, bool sorted, cudaStream_t s) {
-    if (P->trig_cap < n || (sorted && !P->trig32)) {
+    if (!sorted && P->trig_cap < n) {
         dfree(P->trig, P->stream);
-        dfree(P->trig32, P->stream);
         P->trig = nullptr;
-        P->trig32 = nullptr;
         P->trig_cap = 0;
         FGB_TRY(dalloc_n(&P->trig, n, s));
-        FGB_TRY(dalloc_n(&P->trig32, n, s));
         P->trig_cap = n;
+    }
+    if (sorted && P->trig32_cap < n) {
+        dfree(P->trig32, P->stream);
+        P->trig32 = nullptr;
+        P->trig32_cap = 0;
+        FGB_TRY(dalloc_n(&P->trig32, n, s));
+        P->trig32_cap = n;
     }
     if (sorted) {
         const int64_t want = std::min<int64_t>(std::max<int64_t>(n / 8, 1 << 16), 1 << 26);
@@ -477,10 +533,10 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
                 {
                     FGB_KSCOPE("k_pmft_trig_sorted", s);
                     k_pmft_trig_sorted<<<(unsigned)((nq->n + 255) / 256), 256, 0, s>>>(nq->sorted, query_orientations,
-                                                                                       nq->n, P->trig, P->trig32);
+                                                                                       nq->n, P->trig32);
                 }
                 st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "pmft trig launch failed");
-                if (st == FGB_OK) st = pmft_launch_tile(P, nq, plan, R, B, nhalf, s);
+                if (st == FGB_OK) st = pmft_launch_tile(P, nq, plan, R, B, nhalf, query_orientations, s);
             }
             dfree(plan.table, s);
             if (st != FGB_OK) return st;
