@@ -449,7 +449,9 @@ def pmft_components(fgb, torch, dev, stream, flush, n_big=4_194_304):
         pm.compute(nqb, tb, neighbors=nl_holder["nl"], reset=True)
 
     t_list = timed(list_route, stream, flush, reps=3, warm=1)
-    comp["pmft_2d_%dk" % (n // 1024)] = {"points": n, "pmft_ms": t_big, "rdf_ms": t_bigr, "pmft_list_route_ms": t_list, "bonds": bonds,
+    t_list_only = timed(lambda: pm.compute(nqb, tb, neighbors=nl_holder["nl"], reset=True), stream, flush, reps=3,
+                        warm=1)
+    comp["pmft_2d_%dk" % (n // 1024)] = {"points": n, "pmft_ms": t_big, "rdf_ms": t_bigr, "pmft_list_route_ms": t_list, "pmft_from_stored_list_ms": t_list_only, "bonds": bonds,
                           "pmft_bonds_per_s": bonds / t_big * 1e3, "escalated": esc,
                                                "kernel_ms": per, "roofline": roof}
     return comp

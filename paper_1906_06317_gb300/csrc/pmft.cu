@@ -12,8 +12,9 @@
 //
 // The definition is FP64: the defining minimum-image displacement (exact_disp), cos and
 // sin of the float32 angle in FP64, then the rotation and the bin index above, each
-// operation rounded once.  The fused kernel decides a bond in FP32 only when a proven
-// error bound keeps it clear of every bin edge, and hands the rest to that FP64 sequence.
+// operation rounded once.  Both routes (the fused cell-tile kernel and the list kernel)
+// decide a bond in FP32 only when a proven error bound keeps it clear of every bin edge,
+// and bin the rest by that FP64 sequence.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -24,9 +25,7 @@ struct fgb_pmft {
     double x_max, y_max;
     int bx, by;
     unsigned long long *hist;  // device, bx * by, x major
-    double2 *trig;             // device, FP64 (cos, sin) of the query orientations (list route)
-    int64_t trig_cap;
-    float2 *trig32;            // device, FP32 (cos, sin) in cell-sorted order (fused route)
+    float2 *trig32;            // device, FP32 (cos, sin): by query (list route) or sorted position
     int64_t trig32_cap;
     int2 *esc;                 // bonds (query, point) left to the FP64 pass
     int esc_cap;
@@ -43,12 +42,13 @@ struct PmftBins {
     int bx, by;
 };
 
-__global__ void k_pmft_trig(const float *__restrict__ theta, int64_t n, double2 *__restrict__ out) {
+// FP32 (cos, sin) of the query orientations by query index (list route).
+__global__ void k_pmft_trig(const float *__restrict__ theta, int64_t n, float2 *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s, c;
-    sincos((double)theta[i], &s, &c);
-    out[i] = make_double2(c, s);
+    float s, c;
+    sincosf(theta[i], &s, &c);
+    out[i] = make_float2(c, s);
 }
 
 // Bin index of one bond in the frame (FP64, the defining sequence); -1 outside.
@@ -73,6 +73,20 @@ __global__ void k_pmft_trig_sorted(const float4 *__restrict__ sorted, const floa
     out32[p] = make_float2(c, s);
 }
 
+// Bin of a bond at (tx, ty) in bin units (t = (x' + x_max) / dx in FP32) given decision
+// margins (mx, my) in bins: >= 0 decided inside, -1 decided outside, -2 open.  An axis
+// is decided when the fraction of t keeps the margin from both edges; a decided axis
+// outside the range settles the bond.
+__device__ __forceinline__ int pmft_decide(float tx, float ty, float mx, float my, int bx, int by) {
+    const float fx = floorf(tx), fy = floorf(ty);
+    const float rx = tx - fx, ry = ty - fy;
+    const bool okx = rx > mx && rx < 1.f - mx, oky = ry > my && ry < 1.f - my;
+    const bool inx = fx >= 0.f && fx < (float)bx, iny = fy >= 0.f && fy < (float)by;
+    if ((okx && !inx) || (oky && !iny)) return -1;
+    if (okx && oky) return (int)fx * by + (int)fy;
+    return -2;
+}
+
 // FP64 (cos, sin) of one orientation, as the definition takes them.
 __device__ __forceinline__ double2 trig64(const float *theta, int i) {
     double s, c;
@@ -80,16 +94,72 @@ __device__ __forceinline__ double2 trig64(const float *theta, int i) {
     return make_double2(c, s);
 }
 
-// One thread per bond of a NeighborList (query_point_indices address qp and trig).
-__global__ void k_pmft_list(BoxD bd, const float *__restrict__ p, const float *__restrict__ qp,
-                            const double2 *__restrict__ trig, const int32_t *__restrict__ qi,
-                            const int32_t *__restrict__ pj, int64_t m, PmftBins B,
-                            unsigned long long *__restrict__ hist) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = __ldg(qi + e), j = __ldg(pj + e);
-        const double3 d = exact_disp(bd, qp + 3 * (int64_t)i, p + 3 * (int64_t)j);
-        const int b = pmft_bin64(B, __ldg(trig + i), d);
-        if (b >= 0) atomicAdd(hist + b, 1ull);
+struct PmftListArgs {
+    BoxD bd;
+    const float *p, *qp, *theta;
+    const float2 *cs;          // FP32 (cos, sin) by query index
+    const int32_t *qi, *pj;
+    int64_t m;
+    PmftBins B;
+    float inv_dx, inv_dy, off_x, off_y;
+    float kx, ky, cx, cy;      // margin in bins: k * max(|d_x|, |d_y|) + c
+    float wx, wy, wz;          // 0.499 of the box lengths: plain differences below them
+    unsigned long long *hist;
+};
+
+// One thread per bond of a NeighborList (query_point_indices address qp and cs).  The
+// displacement is the defining FP64 one; rotation and binning run in FP32 and a bond
+// within the margin of an edge is binned again by the FP64 sequence.  SHARED: the block
+// counts into a shared histogram (bins <= kPmftListMaxBins) over its own contiguous
+// range of at most 2^30 bonds, so no 32-bit count can overflow.
+constexpr int kPmftListMaxBins = 16384;
+
+template <bool SHARED>
+__global__ void __launch_bounds__(256) k_pmft_list(const __grid_constant__ PmftListArgs a, int64_t per_block) {
+    extern __shared__ uint32_t lh[];
+    const int bins = a.B.bx * a.B.by;
+    if (SHARED) {
+        for (int b = threadIdx.x; b < bins; b += blockDim.x) lh[b] = 0;
+        __syncthreads();
+    }
+    const int64_t e0 = (int64_t)blockIdx.x * per_block, e1 = min(a.m, e0 + per_block);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int i = __ldg(a.qi + e), j = __ldg(a.pj + e);
+        const float *xi = a.qp + 3 * (int64_t)i, *xj = a.p + 3 * (int64_t)j;
+        // Below 0.499 of a box length on every axis, the defining sequence shifts by no
+        // box vector and its displacement is the plain difference, which the FP32
+        // difference matches within half an ulp.  Other bonds take the FP64 sequence.
+        float dx = __ldg(xj) - __ldg(xi), dy = __ldg(xj + 1) - __ldg(xi + 1);
+        const float dz = __ldg(xj + 2) - __ldg(xi + 2);
+        double3 d;
+        const bool plain = fabsf(dx) < a.wx && fabsf(dy) < a.wy && fabsf(dz) < a.wz;
+        if (!plain) {
+            d = exact_disp(a.bd, xi, xj);
+            dx = (float)d.x;
+            dy = (float)d.y;
+        }
+        const float dm = fmaxf(fabsf(dx), fabsf(dy));
+        const float2 cs = __ldg(a.cs + i);
+        const float xq = fmaf(cs.x, dx, cs.y * dy), yq = fmaf(cs.x, dy, -(cs.y * dx));
+        int b = pmft_decide(fmaf(xq, a.inv_dx, a.off_x), fmaf(yq, a.inv_dy, a.off_y), fmaf(a.kx, dm, a.cx),
+                            fmaf(a.ky, dm, a.cy), a.B.bx, a.B.by);
+        if (b == -2) {
+            if (plain) d = exact_disp(a.bd, xi, xj);
+            b = pmft_bin64(a.B, trig64(a.theta, i), d);
+        }
+        if (b >= 0) {
+            if (SHARED)
+                atomicAdd(lh + b, 1u);
+            else
+                atomicAdd(a.hist + b, 1ull);
+        }
+    }
+    if (SHARED) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+            const uint32_t v = lh[b];
+            if (v) atomicAdd(a.hist + b, (unsigned long long)v);
+        }
     }
 }
 
@@ -136,17 +206,9 @@ __device__ __noinline__ void pmft_tile_slow(const PmftTileArgs *ap, int i, int j
     }
 }
 
-// Bin of a bond at (tx, ty) in bin units (t = (x' + x_max) / dx in FP32): >= 0 decided
-// inside, -1 decided outside, -2 open.  An axis is decided when the fraction of t keeps
-// the margin from both edges; a decided axis outside the range settles the bond.
+// Bin of a bond at (tx, ty) in bin units with the kernel's margins.
 __device__ __forceinline__ int pmft_fast_bin(const PmftTileArgs &a, float tx, float ty) {
-    const float fx = floorf(tx), fy = floorf(ty);
-    const float rx = tx - fx, ry = ty - fy;
-    const bool okx = rx > a.mx && rx < 1.f - a.mx, oky = ry > a.my && ry < 1.f - a.my;
-    const bool inx = fx >= 0.f && fx < (float)a.B.bx, iny = fy >= 0.f && fy < (float)a.B.by;
-    if ((okx && !inx) || (oky && !iny)) return -1;
-    if (okx && oky) return (int)fx * a.B.by + (int)fy;
-    return -2;
+    return pmft_decide(tx, ty, a.mx, a.my, a.B.bx, a.B.by);
 }
 
 // Rotates and bins one queued pair (both directions).  The pair tests of the rounds
@@ -382,7 +444,6 @@ extern "C" int fgb_pmftxy_create(double x_max, double y_max, int32_t bins_x, int
 extern "C" void fgb_pmftxy_destroy(fgb_pmft *P) {
     if (!P) return;
     dfree(P->hist, P->stream);
-    dfree(P->trig, P->stream);
     dfree(P->trig32, P->stream);
     dfree(P->esc, P->stream);
     dfree(P->ctl, P->stream);
@@ -456,14 +517,7 @@ static int pmft_launch_tile(fgb_pmft *P, fgb_nq *nq, const StencilPlan &plan, do
 }
 
 static int pmft_ensure(fgb_pmft *P, int64_t n, bool sorted, cudaStream_t s) {
-    if (!sorted && P->trig_cap < n) {
-        dfree(P->trig, P->stream);
-        P->trig = nullptr;
-        P->trig_cap = 0;
-        FGB_TRY(dalloc_n(&P->trig, n, s));
-        P->trig_cap = n;
-    }
-    if (sorted && P->trig32_cap < n) {
+    if (P->trig32_cap < n) {
         dfree(P->trig32, P->stream);
         P->trig32 = nullptr;
         P->trig32_cap = 0;
@@ -545,7 +599,7 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
             FGB_TRY(pmft_ensure(P, n_query, false, s));
             {
                 FGB_KSCOPE("k_pmft_trig", s);
-                k_pmft_trig<<<(unsigned)((n_query + 255) / 256), 256, 0, s>>>(query_orientations, n_query, P->trig);
+                k_pmft_trig<<<(unsigned)((n_query + 255) / 256), 256, 0, s>>>(query_orientations, n_query, P->trig32);
             }
             FGB_LAUNCH_CHECK();
             fgb_nlist *own = nullptr;
@@ -559,13 +613,60 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
             }
             int st = FGB_OK;
             if (nlist->n_pairs > 0) {
-                const unsigned grid =
-                    (unsigned)std::min<int64_t>((nlist->n_pairs + 255) / 256, (int64_t)num_sms() * 16);
-                FGB_KSCOPE("k_pmft_list", s);
-                k_pmft_list<<<grid, 256, 0, s>>>(nq->box.d, nq->points, query_points ? query_points : nq->points,
-                                                 P->trig, nlist->qi, nlist->pj, nlist->n_pairs, B, P->hist);
-                cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "pmft launch failed: %s", cudaGetErrorString(e));
+                PmftListArgs a;
+                memset(&a, 0, sizeof(a));
+                a.bd = nq->box.d;
+                a.p = nq->points;
+                a.qp = query_points ? query_points : nq->points;
+                a.theta = query_orientations;
+                a.cs = P->trig32;
+                a.qi = nlist->qi;
+                a.pj = nlist->pj;
+                a.m = nlist->n_pairs;
+                a.B = B;
+                a.inv_dx = (float)(1.0 / B.dx);
+                a.inv_dy = (float)(1.0 / B.dy);
+                a.off_x = 0.5f * (float)B.bx;
+                a.off_y = 0.5f * (float)B.by;
+                // Error of x' in FP32 against the FP64 definition, dm = max(|d_x|, |d_y|):
+                // sincosf (4u each) 8u dm, the displacement (the FP64 one rounded to FP32, or
+                // the FP32 difference of the coordinates, within u |d| either way) sqrt(2) u dm,
+                // the product and the fused add (1 + sqrt 2) u dm: at most 12.5 u dm.  The
+                // index t = x' / dx + bins / 2 adds u bins (1.42 dm / x_max + 1).  Doubled,
+                // plus the FP64 sequence's own rounding.
+                const double u = std::ldexp(1.0, -24);
+                a.kx = (float)(25.0 * u / B.dx + 2.84 * u * B.bx / B.x_max + 1e-12 / B.dx);
+                a.ky = (float)(25.0 * u / B.dy + 2.84 * u * B.by / B.y_max + 1e-12 / B.dy);
+                a.cx = (float)(2.0 * u * B.bx + 1e-12 / B.dx + 1e-7);
+                a.cy = (float)(2.0 * u * B.by + 1e-12 / B.dy + 1e-7);
+                a.wx = (float)(0.499 * nq->box.p[0]);
+                a.wy = (float)(0.499 * nq->box.p[1]);
+                a.wz = (float)(0.499 * nq->box.p[2]);
+                a.hist = P->hist;
+                const int bins = B.bx * B.by;
+                const bool shared = bins <= kPmftListMaxBins;
+                const size_t smem = shared ? (size_t)bins * sizeof(uint32_t) : 0;
+                int per_sm = 8;
+                if (shared) {
+                    if (cudaFuncSetAttribute(k_pmft_list<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                            cudaSuccess ||
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pmft_list<true>, 256, smem) != cudaSuccess)
+                        st = fail(FGB_ERR_CUDA, "pmft list kernel setup failed");
+                }
+                // enough blocks to fill the GPU, each over at most 2^30 bonds
+                const int64_t m = nlist->n_pairs;
+                int64_t grid = std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * std::max(per_sm, 1));
+                grid = std::max<int64_t>(grid, (m + ((int64_t)1 << 30) - 1) >> 30);
+                const int64_t per_block = (m + grid - 1) / grid;
+                if (st == FGB_OK) {
+                    FGB_KSCOPE("k_pmft_list", s);
+                    if (shared)
+                        k_pmft_list<true><<<(unsigned)grid, 256, smem, s>>>(a, per_block);
+                    else
+                        k_pmft_list<false><<<(unsigned)grid, 256, 0, s>>>(a, per_block);
+                    cudaError_t e = cudaGetLastError();
+                    if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "pmft launch failed: %s", cudaGetErrorString(e));
+                }
             }
             if (own) fgb_nlist_destroy(own);
             if (st != FGB_OK) return st;

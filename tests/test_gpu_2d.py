@@ -218,10 +218,18 @@ def test_pmft_fused_edges_escalate(fgb):
     p.compute((b, dev(x)), dev(th))
     assert p.escalations() > 0
     assert np.array_equal(p.bin_counts, oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64))
+    # the list route on the same bonds (FP32 binning, FP64 for bonds near an edge)
+    nq = fgb.NeighborQuery(b, dev(x), r_cell=2.2)
+    nl = nq.query(None, dict(r_max=2.2, exclude_ii=True)).toNeighborList()
+    p.compute(nq, dev(th), neighbors=nl)
+    assert np.array_equal(p.bin_counts, oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64))
     # the same lattice turned by 90 degrees per particle: cos is -4.4e-8, not 0
     th = np.full(len(x), np.pi / 2, np.float32)
     p.compute((b, dev(x)), dev(th))
-    assert np.array_equal(p.bin_counts, oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64))
+    want = oracle.pmftxy(b, x, th, 1.5, 1.5, 6, 6).astype(np.uint64)
+    assert np.array_equal(p.bin_counts, want)
+    p.compute(nq, dev(th), neighbors=nl)
+    assert np.array_equal(p.bin_counts, want)
 
 
 @pytest.mark.parametrize("bins", [(7, 3), (128, 128), (200, 100)])
