@@ -558,6 +558,9 @@ def extras(fgb, torch, dev, stream, flush):
         rdf2.compute(fgb.NeighborQuery(w2.box, x2, r_cell=2.5), reset=True)
 
     comp["c2_rdf_ms"] = timed(c2_rdf, stream, flush)
+    rdf_l = fgb.RDF(130, 1.3)
+    comp["c2_rdf_from_list_ms"] = timed(lambda: rdf_l.compute(holder["nq"], neighbors=holder["nl"], reset=True),
+                                        stream, flush)
     comp["c2_nl_pairs"] = holder["nl"].n_pairs
     comp.update(pmft_components(fgb, torch, dev, stream, flush))
     holder.clear()

@@ -362,14 +362,79 @@ __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_co
     }
 }
 
-// Histogram of the pairs of a NeighborList: every pair decided with the FP64 sequence.
-__global__ void k_rdf_nlist(BoxD bd, const int32_t *__restrict__ qi, const int32_t *__restrict__ pj, int64_t m,
-                            const float *q_orig, const float *p_orig, const double *T, int bins,
-                            unsigned long long *hist) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int b = exact_bin(T, bins, exact_r2_idx(bd, q_orig, qi[e], p_orig, pj[e]));
-        if (b >= 0) atomicAdd(hist + b, 1ull);
+// Histogram of the pairs of a NeighborList.  Below 0.499 of a box length on every axis
+// the defining sequence shifts by no box vector and its displacement is the plain
+// difference, which the FP32 difference matches within u |d_k|: such pairs take the
+// FP32 bin test with bands for that error.  Other pairs, and pairs inside a band, are
+// decided with the FP64 sequence.
+struct RdfListArgs {
+    BoxD bd;
+    const int32_t *qi, *pj;
+    int64_t m;
+    const float *q_orig, *p_orig;
+    const double *T;
+    int bins;
+    BinParams P;
+    float wx, wy, wz;
+    unsigned long long *hist;
+};
+
+// COPIES shared histograms per block (one per warp for few bins, else one), over the
+// block's contiguous range of at most 2^30 pairs so no 32-bit count can overflow;
+// COPIES = 0 adds to the global counts directly (bins beyond the shared limit).
+constexpr int kRdfListWarps = 8;
+constexpr int kRdfListMaxBins = 16384;
+
+template <int COPIES>
+__global__ void __launch_bounds__(kRdfListWarps * 32) k_rdf_nlist(const __grid_constant__ RdfListArgs a,
+                                                                  int64_t per_block) {
+    extern __shared__ uint32_t lh[];
+    if (COPIES > 0) {
+        for (int b = threadIdx.x; b < COPIES * a.bins; b += blockDim.x) lh[b] = 0;
+        __syncthreads();
     }
+    uint32_t *h = lh + (COPIES > 1 ? (threadIdx.x >> 5) % COPIES : 0) * a.bins;
+    const int64_t e0 = (int64_t)blockIdx.x * per_block, e1 = min(a.m, e0 + per_block);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int i = __ldg(a.qi + e), j = __ldg(a.pj + e);
+        const float *xi = a.q_orig + 3 * (int64_t)i, *xj = a.p_orig + 3 * (int64_t)j;
+        const float dx = __ldg(xj) - __ldg(xi), dy = __ldg(xj + 1) - __ldg(xi + 1), dz = __ldg(xj + 2) - __ldg(xi + 2);
+        int b = -2;
+        if (fabsf(dx) < a.wx && fabsf(dy) < a.wy && fabsf(dz) < a.wz) b = rdf_bin(a.P, r2_f32(dx, dy, dz));
+        if (b == -2) b = exact_bin(a.T, a.bins, exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j));
+        if (b >= 0) {
+            if (COPIES > 0)
+                atomicAdd(h + b, 1u);
+            else
+                atomicAdd(a.hist + b, 1ull);
+        }
+    }
+    if (COPIES > 0) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+            unsigned long long v = 0;
+            for (int c = 0; c < COPIES; ++c) v += lh[c * a.bins + b];
+            if (v) atomicAdd(a.hist + b, v);
+        }
+    }
+}
+
+template <int COPIES>
+static int launch_rdf_nlist(const RdfListArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)COPIES * a.bins * sizeof(uint32_t);
+    int per_sm = 8;
+    if (COPIES > 0) {
+        FGB_CUDA(cudaFuncSetAttribute(k_rdf_nlist<COPIES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_nlist<COPIES>, kRdfListWarps * 32, smem));
+    }
+    // enough blocks to fill the GPU, each over at most 2^30 pairs
+    int64_t grid = std::min<int64_t>((a.m + 255) / 256, (int64_t)num_sms() * std::max(per_sm, 1));
+    grid = std::max<int64_t>(grid, (a.m + ((int64_t)1 << 30) - 1) >> 30);
+    const int64_t per_block = (a.m + grid - 1) / grid;
+    FGB_KSCOPE("k_rdf_nlist", s);
+    k_rdf_nlist<COPIES><<<(unsigned)grid, kRdfListWarps * 32, smem, s>>>(a, per_block);
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
 }
 
 template <int NS>
@@ -485,13 +550,48 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
     if (st == FGB_OK) cudaMemsetAsync(r->esc_count, 0, 2 * sizeof(int), s);  // [0] band pairs, [1] work
     if (st == FGB_OK && nlist) {
         const float *q_orig = query_points ? query_points : nq->points;
-        if (nlist->n_pairs > 0)
-            {
-                FGB_KSCOPE("k_rdf_nlist", s);
-                k_rdf_nlist<<<num_sms() * 8, 256, 0, s>>>(nq->box.d, nlist->qi, nlist->pj, nlist->n_pairs, q_orig,
-                                                          nq->points, r->T, r->bins, r->hist);
+        if (nlist->n_pairs > 0) {
+            // plain FP32 differences: each component within u |d_k| <= u R of the exact
+            // one for pairs that matter (with slack for the FP64 reference's rounding)
+            const BoxHost &b = nq->box;
+            const double Lsum = std::sqrt(b.M[0][0] * b.M[0][0]) +
+                                std::sqrt(b.M[0][1] * b.M[0][1] + b.M[1][1] * b.M[1][1]) +
+                                std::sqrt(b.M[0][2] * b.M[0][2] + b.M[1][2] * b.M[1][2] + b.M[2][2] * b.M[2][2]);
+            const double delta = r2_error_bound_eps(std::ldexp(1.0, -24) * R * 1.01, Lsum, R);
+            if (!r->band) st = dalloc_n(&r->band, r->bins + 1, s);
+            if (st == FGB_OK && delta != r->band_delta) {
+                {
+                    FGB_KSCOPE("k_band", s);
+                    k_band<<<(r->bins + 256) / 256, 256, 0, s>>>(r->T, r->bins + 1, delta, r->band);
+                }
+                r->band_delta = delta;
             }
-        st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "rdf nlist launch failed");
+            if (st == FGB_OK) {
+                RdfListArgs a;
+                memset(&a, 0, sizeof(a));
+                a.bd = b.d;
+                a.qi = nlist->qi;
+                a.pj = nlist->pj;
+                a.m = nlist->n_pairs;
+                a.q_orig = q_orig;
+                a.p_orig = nq->points;
+                a.T = r->T;
+                a.bins = r->bins;
+                a.P = bin_params(r->bins, r->r_min, r->r_max, delta, r->band, r->T_host);
+                a.wx = (float)(0.499 * b.p[0]);
+                a.wy = (float)(0.499 * b.p[1]);
+                a.wz = (float)(0.499 * b.p[2]);
+                a.hist = r->hist;
+                if (r->bins <= 1024)
+                    st = launch_rdf_nlist<kRdfListWarps>(a, s);
+                else if (r->bins <= kRdfListMaxBins)
+                    st = launch_rdf_nlist<1>(a, s);
+                else
+                    st = launch_rdf_nlist<0>(a, s);
+            }
+        }
+        if (st == FGB_OK)
+            st = cudaGetLastError() == cudaSuccess ? FGB_OK : fail(FGB_ERR_CUDA, "rdf nlist launch failed");
     } else if (st == FGB_OK && nqq > 0) {
         StencilPlan plan;
         st = plan_stencil(nq, R, 0, s, &plan);
