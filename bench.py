@@ -113,7 +113,7 @@ class ClockSampler:
 MEASURED_TRAFFIC = {
     "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "49c024a3625fcf66", 559.168256e6 + 1537.259e6, 2097152),
     "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "49c024a3625fcf66", 34.414336e6 + 0.018e6, 2097152),
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "54d9b313d5161218", 34.20928e6 + 0.079e6, 2097152),
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "1c4f2babc9bbf151", 34.247936e6 + 0.01152e6, 2097152),
 }
 
 
