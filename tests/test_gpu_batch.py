@@ -79,3 +79,24 @@ def test_batch_rejects_small_boxes(fgb):
     with pytest.raises(fgb.FGBError) as e:
         fgb.Batch([10], [box], r_max=1.5, rdf_r_max=3.0)
     assert e.value.code == fgb.ERR_BOX_TOO_SMALL
+
+
+def test_batch_mixes_2d_and_3d_frames(fgb):
+    # 2D frames (Lz = 0) next to 3D ones in one persistent launch
+    P = W.C5_PARAMS
+    fr = W.c5(seed=12, n_frames=3, n_lo=800, n_hi=3000)
+    flat = [(f.box, f.points) for f in fr]
+    for k, n in enumerate((1500, 4000, 700)):
+        g = W.p6(seed=40 + k, n=n, n_frames=1, neighbors=6.0, xy=0.1 * k)[0]
+        flat.insert(2 * k, (g.box, g.points))
+    refs = []
+    for box, x in flat:
+        counts = oracle.rdf_counts(box, x, P["rdf_bins"], P["rdf_r_max"])
+        _, off, pj, _ = oracle.ball_query(box, x, P["r_max"])
+        refs.append((counts, oracle.steinhardt(box, x, off, pj, P["l"]), np.diff(off)))
+    pts = torch.from_numpy(np.concatenate([x for _, x in flat])).cuda()
+    b = fgb.Batch([len(x) for _, x in flat], [box for box, _ in flat], r_max=P["r_max"], l=P["l"],
+                  rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"])
+    b.run(pts)
+    torch.cuda.synchronize()
+    check(b, None, refs)
