@@ -325,9 +325,18 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32, 3) k_pmft_tile(const __gr
     // a candidate farther than this from the queries' bounding box reaches none of them
     const float reach2 = a.reach2 * (1.0f + 1e-5f);
     // this warp's additions since its last flush bound every shared count's share from
-    // it; flushing at 2^28 keeps the sum over the block's warps below 2^32
+    // it; flushing at 2^28 keeps the sum over the block's warps below 2^32.  A chunk of
+    // 32 candidates against nq <= 32 queries adds at most 64 nq; after a flush the at
+    // most 31 queued pairs (62 additions) are still to come.
     uint32_t adds = 0;
     const uint32_t kFlushAt = 1u << 28;
+    auto charge = [&](int nq) {
+        if (adds > kFlushAt - 64u * kPmftTileQ) {
+            pmft_tile_flush(shist, a.bins, a.hist);
+            adds = 64u;
+        }
+        adds += 64u * (uint32_t)nq;
+    };
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(a.ctl + 1, 1u);
@@ -355,18 +364,12 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32, 3) k_pmft_tile(const __gr
                 const float4 q = qs[lane < nq ? lane : 0];
                 warp_box(q.x, q.y, q.z, lane < nq, blo, bhi);
             }
-            // at most two additions per pair test of this pass
-            const uint32_t pass_adds = 64u * (uint32_t)nq * (uint32_t)((nA + 31) / 32 + (total + 31) / 32 + 1);
-            if (adds > kFlushAt - pass_adds) {
-                pmft_tile_flush(shist, a.bins, a.hist);
-                adds = 0;
-            }
-            adds += pass_adds;
             // A's own points first (they pair only with earlier queries)
             for (int base = 0; base < nA; base += 32) {
                 const int k = base + lane;
                 const TileCand c = tile_load(a.t, ts, n, nA, k);
                 const float2 ccs = k < nA ? __ldg(a.cs32 + c.p) : make_float2(0.f, 0.f);
+                charge(nq);
                 pmft_tile_rounds<true>(a, qs, qcs, nq, c.x, c.y, c.j, ccs, k < nA ? k - qb : 0, Q, shist);
             }
             // the other cells: candidates out of reach of the whole pass are dropped, the
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32, 3) k_pmft_tile(const __gr
                     __syncwarp();
                     const float4 e = buf[lane];
                     const float2 ecs = __ldg(a.cs32 + __float_as_int(e.z));
+                    charge(nq);
                     pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, Q, shist);
                     const float4 rest = buf[32 + lane];
                     __syncwarp();
@@ -396,6 +400,7 @@ __global__ void __launch_bounds__(kPmftTileWarps * 32, 3) k_pmft_tile(const __gr
                 const bool v = lane < cnt;
                 const float4 e = v ? buf[lane] : make_float4(kFar, kFar, 0.f, __int_as_float(-1));
                 const float2 ecs = v ? __ldg(a.cs32 + __float_as_int(e.z)) : make_float2(0.f, 0.f);
+                charge(nq);
                 pmft_tile_rounds<false>(a, qs, qcs, nq, e.x, e.y, __float_as_int(e.w), ecs, 0, Q, shist);
             }
             // the queue refers to this pass's staged queries: empty it before they change

@@ -243,6 +243,26 @@ def test_pmft_bin_counts_across_routes(fgb, bins):
     assert np.array_equal(p.bin_counts, want.astype(np.uint64))
 
 
+def test_pmft_dense_cluster(fgb):
+    # thousands of points in a few cells next to a uniform background: long candidate
+    # streams per cell, heavy contention on the shared counts, and (angles 0) many bonds
+    # exactly on bin edges from the duplicated float32 coordinates
+    b = W.Box.square(60.0)
+    rng = np.random.default_rng(535)
+    bg = W.uniform_points(rng, b, 12000)
+    cl = np.zeros((4000, 3), np.float32)
+    cl[:, :2] = (rng.random((4000, 2)) * 1.6 - 0.8).astype(np.float32)
+    x = np.concatenate([bg, cl]).astype(np.float32)
+    th = np.zeros(len(x), np.float32)
+    p = fgb.PMFTXY(1.0, 1.0, 40)
+    p.compute((b, dev(x)), dev(th))
+    want = oracle.pmftxy(b, x, th, 1.0, 1.0, 40, 40).astype(np.uint64)
+    assert np.array_equal(p.bin_counts, want)
+    nq = fgb.NeighborQuery(b, dev(x), r_cell=1.5)
+    p.compute(nq, dev(th), neighbors=nq.query(None, dict(r_max=1.5, exclude_ii=True)).toNeighborList())
+    assert np.array_equal(p.bin_counts, want)
+
+
 def test_pmft_errors_and_empty(fgb):
     b3 = W.Box.cube(12.0)
     x3 = dev(W.small_random(530, 100, b3))
