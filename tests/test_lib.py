@@ -51,6 +51,24 @@ def test_host_side_argument_checks(lib):
     assert lib.fgb_nq_create(None, None, 0, 1.0, None, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
     b = fgb.fgb_box(10.0, -1.0, 10.0, 0, 0, 0)
     assert lib.fgb_nq_create(ctypes.byref(b), None, 0, 1.0, None, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    # a 2D box (Lz = 0) must have xz = yz = 0
+    b = fgb.fgb_box(10.0, 10.0, 0.0, 0.1, 0.2, 0.0)
+    assert lib.fgb_nq_create(ctypes.byref(b), None, 0, 1.0, None, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    assert b"2D" in lib.fgb_last_error()
+    # PMFT(x, y): extents and bin counts are checked on the host; a fresh accumulator
+    # reports zero counts, pcf 0 and an infinite PMFT without touching the device
+    assert lib.fgb_pmftxy_create(0.0, 1.0, 10, 10, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    assert lib.fgb_pmftxy_create(1.0, float("inf"), 10, 10, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    assert lib.fgb_pmftxy_create(1.0, 1.0, 0, 10, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    assert lib.fgb_pmftxy_create(1.0, 1.0, 1 << 14, 1 << 13, ctypes.byref(h)) == fgb.ERR_INVALID_ARG
+    assert lib.fgb_pmftxy_create(1.5, 1.0, 3, 2, ctypes.byref(h)) == 0
+    import numpy as np
+    c = np.full(6, 7, np.uint64)
+    g = np.full(6, 7.0)
+    f = np.zeros(6)
+    assert lib.fgb_pmftxy_result(h, c.ctypes.data, g.ctypes.data, f.ctypes.data, None) == 0
+    assert not c.any() and not g.any() and np.all(np.isinf(f))
+    lib.fgb_pmftxy_destroy(h)
 
 
 def test_product_path_never_imports_the_oracle():
