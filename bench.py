@@ -482,6 +482,10 @@ def extras(fgb, torch, dev, stream, flush):
         return nq.query(None, dict(r_max=2.5, exclude_ii=True)).toNeighborList()
 
     comp["c3_tree_build_query_ms"] = timed(tree_query, stream, flush, reps=3, warm=1)
+    aq3 = fgb.AABBQuery(w.box, x)
+    comp["c3_tree_knn12_ms"] = timed(lambda: aq3.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList(),
+                                     stream, flush, reps=3, warm=1)
+    del aq3
     comp["c3_cell_build_query_ms"] = timed(cell_query, stream, flush, reps=3, warm=1)
     # Q6 forward + backward, N = 2^20, fixed neighbor list r = 1.3
     w4 = W.c4()

@@ -361,79 +361,80 @@ template <class B, class F>
 __device__ __forceinline__ void bvh_walk(const BvhArgs &a, float3 qw, float3 qf, B &&bound, F &&fn) {
     if (a.n == 0) return;
     int stack[kBvhStack];
-    for (int sz = -1; sz <= 1; ++sz)
-        for (int sy = -1; sy <= 1; ++sy)
-            for (int sx = -1; sx <= 1; ++sx) {
-                const float gx = qf.x + sx, gy = qf.y + sy, gz = qf.z + sz;
-                const float ex = fmaxf(fmaxf(-gx, gx - 1.f), 0.f) * a.w[0];
-                const float ey = fmaxf(fmaxf(-gy, gy - 1.f), 0.f) * a.w[1];
-                const float ez = fmaxf(fmaxf(-gz, gz - 1.f), 0.f) * a.w[2];
-                const float lb = fmaxf(ex, fmaxf(ey, ez)) * (1.f - 1e-5f);
-                if (lb * lb > bound()) continue;
-                const float qx = qw.x + (float)sx * a.bf.L[0] + (float)sy * a.bf.a2x + (float)sz * a.bf.a3x;
-                const float qy = qw.y + (float)sy * a.bf.L[1] + (float)sz * a.bf.a3y;
-                const float qz = qw.z + (float)sz * a.bf.L[2];
-                int sp = 0;
-                int node = a.n >= 2 ? 0 : ~0;
-                for (int64_t visits = 0;; ++visits) {
-                    if (visits > 2 * (int64_t)a.n) {
-                        atomicExch(a.err, 4);
-                        break;
-                    }
-                    if (node < 0) {
-                        const float4 c = __ldg(a.pts + ~node);
-                        fn(__float_as_int(c.w), r2_f32(c.x - qx, c.y - qy, c.z - qz));
+    // the query's own image first: its neighbors set a tight bound at once, so most of
+    // the other 26 images are skipped by their lower bound
+    for (int t = 0; t < 27; ++t) {
+        const int code = t == 0 ? 13 : (t <= 13 ? t - 1 : t);
+        const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+        const float gx = qf.x + sx, gy = qf.y + sy, gz = qf.z + sz;
+        const float ex = fmaxf(fmaxf(-gx, gx - 1.f), 0.f) * a.w[0];
+        const float ey = fmaxf(fmaxf(-gy, gy - 1.f), 0.f) * a.w[1];
+        const float ez = fmaxf(fmaxf(-gz, gz - 1.f), 0.f) * a.w[2];
+        const float lb = fmaxf(ex, fmaxf(ey, ez)) * (1.f - 1e-5f);
+        if (lb * lb > bound()) continue;
+        const float qx = qw.x + (float)sx * a.bf.L[0] + (float)sy * a.bf.a2x + (float)sz * a.bf.a3x;
+        const float qy = qw.y + (float)sy * a.bf.L[1] + (float)sz * a.bf.a3y;
+        const float qz = qw.z + (float)sz * a.bf.L[2];
+        int sp = 0;
+        int node = a.n >= 2 ? 0 : ~0;
+        for (int64_t visits = 0;; ++visits) {
+            if (visits > 2 * (int64_t)a.n) {
+                atomicExch(a.err, 4);
+                break;
+            }
+            if (node < 0) {
+                const float4 c = __ldg(a.pts + ~node);
+                fn(__float_as_int(c.w), r2_f32(c.x - qx, c.y - qy, c.z - qz));
+            } else {
+                const BvhNode *nd = a.nodes + node;
+                const int c0 = __ldg(&nd->left), c1 = __ldg(&nd->right);
+                float d0, d1;
+                {
+                    float dx, dy, dz;
+                    if (c0 < 0) {
+                        const float4 p = __ldg(a.pts + ~c0);
+                        dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
                     } else {
-                        const BvhNode *nd = a.nodes + node;
-                        const int c0 = __ldg(&nd->left), c1 = __ldg(&nd->right);
-                        float d0, d1;
-                        {
-                            float dx, dy, dz;
-                            if (c0 < 0) {
-                                const float4 p = __ldg(a.pts + ~c0);
-                                dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
-                            } else {
-                                const BvhNode *cn = a.nodes + c0;
-                                dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
-                                dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
-                                dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
-                            }
-                            d0 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
-                            if (c1 < 0) {
-                                const float4 p = __ldg(a.pts + ~c1);
-                                dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
-                            } else {
-                                const BvhNode *cn = a.nodes + c1;
-                                dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
-                                dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
-                                dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
-                            }
-                            d1 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
-                        }
-                        const float lim = bound();
-                        const bool t0 = d0 <= lim, t1 = d1 <= lim;
-                        if (t0 && t1) {
-                            const bool first0 = d0 <= d1;
-                            if (sp < kBvhStack)
-                                stack[sp++] = first0 ? c1 : c0;
-                            else
-                                atomicExch(a.err, 3);
-                            node = first0 ? c0 : c1;
-                            continue;
-                        }
-                        if (t0 || t1) {
-                            node = t0 ? c0 : c1;
-                            continue;
-                        }
+                        const BvhNode *cn = a.nodes + c0;
+                        dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
+                        dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
+                        dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
                     }
-                    // pop, skipping entries the shrinking bound has ruled out is left to the
-                    // child test of the next node (its box is re-tested when expanded)
-                    if (sp == 0) break;
-                    node = stack[--sp];
+                    d0 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
+                    if (c1 < 0) {
+                        const float4 p = __ldg(a.pts + ~c1);
+                        dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
+                    } else {
+                        const BvhNode *cn = a.nodes + c1;
+                        dx = fmaxf(fmaxf(__ldg(cn->lo) - qx, qx - __ldg(cn->hi)), 0.f);
+                        dy = fmaxf(fmaxf(__ldg(cn->lo + 1) - qy, qy - __ldg(cn->hi + 1)), 0.f);
+                        dz = fmaxf(fmaxf(__ldg(cn->lo + 2) - qz, qz - __ldg(cn->hi + 2)), 0.f);
+                    }
+                    d1 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (1.f - 1e-5f);
+                }
+                const float lim = bound();
+                const bool t0 = d0 <= lim, t1 = d1 <= lim;
+                if (t0 && t1) {
+                    const bool first0 = d0 <= d1;
+                    if (sp < kBvhStack)
+                        stack[sp++] = first0 ? c1 : c0;
+                    else
+                        atomicExch(a.err, 3);
+                    node = first0 ? c0 : c1;
+                    continue;
+                }
+                if (t0 || t1) {
+                    node = t0 ? c0 : c1;
+                    continue;
                 }
             }
+            // pop, skipping entries the shrinking bound has ruled out is left to the
+            // child test of the next node (its box is re-tested when expanded)
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
 }
-
 template <int KT>
 __global__ void __launch_bounds__(128) k_bvh_knn(BvhKnn a) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
