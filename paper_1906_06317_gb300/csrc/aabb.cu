@@ -455,11 +455,16 @@ __global__ void __launch_bounds__(128) k_bvh_knn(BvhKnn a) {
         br[q] = INFINITY;
         bj[q] = 0x7fffffff;
     }
-    // bound: the (m+1)-th best so far (ties kept by the 1e-5 shrink of the box distances)
-    auto bound = [&]() { return pick<KT>(br, min(m, KT - 1)) * (1.f + 1e-5f); };
+    // bound: the (m+1)-th best so far (ties kept by the 1e-5 shrink of the box distances),
+    // refreshed when a candidate enters the list
+    float bnd = INFINITY;
+    auto bound = [&]() { return bnd; };
     bvh_walk(a.b, qw, qf, bound, [&](int j, float r2) {
         if (j == excl) return;
-        if (r2 < br[KT - 1] || (r2 == br[KT - 1] && j < bj[KT - 1])) topk_insert<KT>(br, bj, r2, j);
+        if (r2 < br[KT - 1] || (r2 == br[KT - 1] && j < bj[KT - 1])) {
+            topk_insert<KT>(br, bj, r2, j);
+            bnd = pick<KT>(br, min(m, KT - 1)) * (1.f + 1e-5f);
+        }
     });
     if (m == 0) return;
     const bool moved = fl != 0 || a.b.pts_moved;
