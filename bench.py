@@ -487,6 +487,24 @@ def extras(fgb, torch, dev, stream, flush):
                                      stream, flush, reps=3, warm=1)
     del aq3
     comp["c3_cell_build_query_ms"] = timed(cell_query, stream, flush, reps=3, warm=1)
+    # clustered points (2,000 Gaussian blobs of 1,000, sigma 0.5, overall density 0.1):
+    # the same r = 1 list from the tree and from the cell list, checked equal
+    wb = W.blobs()
+    xb = torch.from_numpy(wb.points).to(dev)
+    lists = {}
+
+    def blob_tree():
+        lists["tree"] = fgb.AABBQuery(wb.box, xb).query(None, dict(r_max=1.0, exclude_ii=True)).toNeighborList()
+
+    def blob_cells():
+        lists["cells"] = fgb.NeighborQuery(wb.box, xb, r_cell=1.0).query(None, dict(r_max=1.0, exclude_ii=True)
+                                                                         ).toNeighborList()
+
+    comp["blobs_tree_build_query_ms"] = timed(blob_tree, stream, flush, reps=3, warm=1)
+    comp["blobs_cell_build_query_ms"] = timed(blob_cells, stream, flush, reps=3, warm=1)
+    assert torch.equal(lists["tree"].point_indices, lists["cells"].point_indices)
+    comp["blobs_pairs"] = lists["cells"].n_pairs
+    del lists
     # Q6 forward + backward, N = 2^20, fixed neighbor list r = 1.3
     w4 = W.c4()
     x4 = torch.from_numpy(w4.points).to(dev)

@@ -707,7 +707,7 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
             k_bvh_write<<<grid1d(nqq, 128), 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
         }
         const int cap = (int)((hs.maxcount + 3) & ~3u);
-        st = sort_segments(nl->segments, nqq, cap, nq->n < ((int64_t)1 << 25) ? 1 : 0, nl->qi, nl->pj, nl->dist, s);
+        st = sort_segments(nl->segments, nqq, cap, nq->n, nl->qi, nl->pj, nl->dist, s);
     }
     if (st == FGB_OK) {
         cudaMemcpyAsync(&hs, dst, sizeof(Status), cudaMemcpyDeviceToHost, s);

@@ -250,8 +250,13 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->dist, hs.total, s);
     if (st == FGB_OK && nqq > 0 && hs.total > 0) {
         const int cap = (int)((hs.maxcount + 3) & ~3u);
-        if (tile && tile_write_smem(cap) <= 160 * 1024) {
+        if (tile && cap <= 128 && tile_write_smem(cap) <= 160 * 1024) {
             st = tile_write(nq, plan, R, a.exclude, a.err, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist, s);
+        } else if (tile && cap <= 16384) {
+            // long rows: appended to the list by the cell tiles, then sorted per row
+            st = tile_write_global(nq, plan, R, a.exclude, a.err, nl->segments, counts, nl->qi, nl->pj, nl->dist, s);
+            st = st ? st
+                    : sort_segments(nl->segments, nqq, cap, nq->n, nl->qi, nl->pj, nl->dist, s);
         } else {
         int block = 128;
         while (block > 32 && (size_t)cap * (block + 1) * sizeof(uint32_t) > 100 * 1024) block >>= 1;

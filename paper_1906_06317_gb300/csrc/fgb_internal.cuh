@@ -214,8 +214,12 @@ int aabb_knn_query(fgb_nq *nq, const float *query_points, int64_t n_query, const
                    cudaStream_t s, fgb_nlist *nl);
 // Sorts every segment of a list by point index in place (warp per segment, rows of at
 // most cap entries staged in shared memory); tile.cu.
-int sort_segments(const int64_t *seg, int64_t nq, int cap, int packable, int32_t *qi, int32_t *pj, float *dist,
+int sort_segments(const int64_t *seg, int64_t nq, int cap, int64_t npoints, int32_t *qi, int32_t *pj, float *dist,
                   cudaStream_t s);
+// Ball-query write for rows too long for the write kernel's shared rows: hits appended to
+// each query's segment in the list, unsorted (tile.cu; follow with sort_segments).
+int tile_write_global(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+                      const uint32_t *counts, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
 
 // Cell-tile kernels (tile.cu): one warp per query cell, self queries on the shift route.
 bool tile_ok(const StencilPlan &p);

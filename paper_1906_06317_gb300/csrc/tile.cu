@@ -512,37 +512,222 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_
                           counts, cap, packable != 0, qi_out, pj_out, d_out);
 }
 
+// ---- dense cells: rows appended straight to the list, sorted afterwards ----
+//
+// When the longest row would not fit the write kernel's shared rows, hits go straight
+// to the query's segment of the list: slots come from the row's shared counter (the row
+// length is the count pass's, so every slot lies inside the segment), and
+// sort_segments orders the rows by point index afterwards.
+
+template <int G>
+__device__ __forceinline__ void write_chunk_global(const float4 *sp, float4 Q, int i, int excl, float lo, float hi,
+                                                   int *rowcnt, int64_t off, uint32_t want, int32_t *__restrict__ qi_out,
+                                                   int32_t *__restrict__ pj_out, float *__restrict__ d_out,
+                                                   bool &band) {
+#pragma unroll 4
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        band |= (r2 >= lo) & (r2 < hi);
+        if (r2 < lo) {
+            const int j = __float_as_int(c.w);
+            if (j != excl) {
+                const uint32_t pos = (uint32_t)atomicAdd(rowcnt, 1);
+                if (pos < want) {
+                    qi_out[off + pos] = i;
+                    pj_out[off + pos] = j;
+                    d_out[off + pos] = r2 > 0.f ? r2 * rsqrt_ftz(r2) : 0.f;
+                }
+            }
+        }
+    }
+}
+
+// The band pairs of one chunk, decided by the FP64 sequence and appended.
+__device__ __noinline__ void write_chunk_global_exact(const TileArgs &a, const float4 *sp, int G, float4 Q, int excl,
+                                                      float lo, float hi, int *rowcnt, int64_t off, uint32_t want,
+                                                      int32_t *qi_out, int32_t *pj_out, float *d_out) {
+    const int i = __float_as_int(Q.w);
+    for (int r = 0; r < 32 / G; ++r) {
+        const float4 c = sp[r * G];
+        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+        const int j = __float_as_int(c.w);
+        if (r2 >= lo && r2 < hi && j != excl && j >= 0 && i >= 0) {
+            const double e = exact_r2_idx(a.bd, a.p_orig, i, a.p_orig, j);
+            if (e < a.T) {
+                const uint32_t pos = (uint32_t)atomicAdd(rowcnt, 1);
+                if (pos < want) {
+                    qi_out[off + pos] = i;
+                    pj_out[off + pos] = j;
+                    d_out[off + pos] = (float)sqrt(e);
+                }
+            }
+        }
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global(const __grid_constant__ TileArgs a,
+                                                                       const int64_t *__restrict__ seg,
+                                                                       const uint32_t *__restrict__ counts,
+                                                                       int32_t *__restrict__ qi_out,
+                                                                       int32_t *__restrict__ pj_out,
+                                                                       float *__restrict__ d_out) {
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    TileStencilT<NS> &ts = sts[warp];
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    const float lo = a.band.lo, hi = a.band.hi;
+    float4 *stage = sstage[warp];
+    int *rowlen = srow[warp];
+    for (int qb = 0; qb < nA; qb += kTileQueries) {
+        const int nq = min(kTileQueries, nA - qb);
+        const QLayout L = qlayout(nq);
+        const bool qact = L.myq < nq;
+        const float4 Q = qact ? __ldg(a.pts + begA + qb + L.myq) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
+        const int i = __float_as_int(Q.w);
+        const int excl = a.exclude ? i : -1;
+        const int64_t off = qact ? seg[i] : 0;
+        const uint32_t want = qact ? counts[i] : 0;
+        if (lane < kTileQueries) rowlen[lane] = 0;
+        __syncwarp();
+        int *myrc = rowlen + L.myq;
+        const float4 *sp = stage + L.g;
+        for (int base = 0; base < total; base += 32) {
+            tile_stage(a, ts, n, total, base, stage);
+            bool band = false;
+#define FGB_WG(GV) write_chunk_global<GV>(sp, Q, i, excl, lo, hi, myrc, off, want, qi_out, pj_out, d_out, band)
+            FGB_TILE_DISPATCH_G(L.G, FGB_WG)
+#undef FGB_WG
+            if (__any_sync(0xffffffffu, band))
+                write_chunk_global_exact(a, sp, L.G, Q, excl, lo, hi, myrc, off, want, qi_out, pj_out, d_out);
+            __syncwarp();
+        }
+        if (L.g == 0 && qact && (uint32_t)*myrc != want) atomicExch(a.err, *myrc > (int)want ? 1 : 2);
+        __syncwarp();
+    }
+}
+
+// Rows of up to 32 * KPL entries sorted on packed keys (index << SB | slot), for indices
+// below 2^(32 - SB) and rows of at most 2^SB slots, then stored.
+template <int KPL, int SB>
+__device__ __forceinline__ void store_sorted_packed_sb(const uint2 *row, uint32_t nL, int iL, int64_t oL,
+                                                       int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                       float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        v[r] = k < nL ? (row[k].x << SB) | k : 0xffffffffu;
+    }
+    bitonic_keys<KPL>(v);
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t k = KPL * lane + r;
+        if (k < nL) {
+            const uint2 e = row[v[r] & ((1u << SB) - 1u)];
+            __stcs(qi_out + oL + k, iL);
+            __stcs(pj_out + oL + k, (int32_t)e.x);
+            __stcs(d_out + oL + k, __uint_as_float(e.y));
+        }
+    }
+}
+
 // Sorts each segment [seg[q], seg[q+1]) of (qi, pj, dist) by point index in place: one
 // warp per segment, staged as (index, distance) in shared memory, then the same network
-// (or ranking) and stores as the write kernels.
-__global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int cap, int packable,
+// (or ranking) and stores as the write kernels.  WIDE (rows longer than 128): rows of up
+// to 512 or 1,024 entries take a register network on packed keys when the point indices
+// fit 23 or 22 bits; longer rows are sorted in shared memory by a bitonic network over
+// the row padded to a power of two (width entries per warp), then stored coalesced.
+// packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
+template <bool WIDE>
+__global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int cap, int width, int packable,
                                 int32_t *__restrict__ qi, int32_t *__restrict__ pj, float *__restrict__ dist) {
-    extern __shared__ uint2 srows[];  // (blockDim / 32) * cap
+    extern __shared__ uint2 srows[];  // (blockDim / 32) * (WIDE ? width : cap)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (q >= nq) return;
     const int64_t b = seg[q];
     const uint32_t n = (uint32_t)(seg[q + 1] - b);
     if (n <= 1 || n > (uint32_t)cap) return;
-    uint2 *row = srows + (size_t)warp * cap;
+    uint2 *row = srows + (size_t)warp * (WIDE ? width : cap);
     for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
     const int iq = qi[b];
+    if (!WIDE || n <= 128) {
+        __syncwarp();
+        sort_store_row(row, n, iq, b, (packable & 1) != 0, qi, pj, dist);
+        return;
+    }
+    if (n <= 512 && (packable & 2)) {
+        __syncwarp();
+        store_sorted_packed_sb<16, 9>(row, n, iq, b, qi, pj, dist);
+        return;
+    }
+    if (n <= 1024 && (packable & 4)) {
+        __syncwarp();
+        store_sorted_packed_sb<32, 10>(row, n, iq, b, qi, pj, dist);
+        return;
+    }
+
+    uint32_t N = 256;
+    while (N < n) N <<= 1;  // N <= width
+    for (uint32_t k = n + lane; k < N; k += 32) row[k] = make_uint2(0xffffffffu, 0u);
     __syncwarp();
-    sort_store_row(row, n, iq, b, packable != 0, qi, pj, dist);
+    for (uint32_t k = 2; k <= N; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = lane; t < N / 2; t += 32) {
+                // the t-th compare-exchange pair of this step: e has bit j clear, l = e | j
+                const uint32_t e = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = e | j;
+                const uint2 x = row[e], y = row[l];
+                const bool asc = (e & k) == 0;
+                if ((x.x > y.x) == asc) {
+                    row[e] = y;
+                    row[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+    for (uint32_t k = lane; k < n; k += 32) {
+        const uint2 e = row[k];
+        __stcs(qi + b + k, iq);
+        __stcs(pj + b + k, (int32_t)e.x);
+        __stcs(dist + b + k, __uint_as_float(e.y));
+    }
 }
 
-int sort_segments(const int64_t *seg, int64_t nq, int cap, int packable, int32_t *qi, int32_t *pj, float *dist,
+int sort_segments(const int64_t *seg, int64_t nq, int cap, int64_t npoints, int32_t *qi, int32_t *pj, float *dist,
                   cudaStream_t s) {
     if (nq == 0 || cap <= 1) return FGB_OK;
+    const int packable = (npoints < ((int64_t)1 << 25) ? 1 : 0) | (npoints < ((int64_t)1 << 23) ? 2 : 0) |
+                         (npoints < ((int64_t)1 << 22) ? 4 : 0);
+    int width = 256;
+    while (width < cap) width <<= 1;
+    const bool wide = cap > 128 && (size_t)width * sizeof(uint2) <= 128 * 1024;
+    const int stride = wide ? width : cap;
     int warps = 4;
-    while (warps > 1 && (size_t)warps * cap * sizeof(uint2) > 96 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * cap * sizeof(uint2);
-    if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tree query: more than %d neighbors of one point", 25600);
-    FGB_CUDA(cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
+    while (warps > 1 && (size_t)warps * stride * sizeof(uint2) > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * stride * sizeof(uint2);
+    if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "more than %d neighbors of one point", 25600);
+    const unsigned grid = (unsigned)((nq + warps - 1) / warps);
+    if (wide) {
+        FGB_CUDA(cudaFuncSetAttribute(k_sort_segments<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         FGB_KSCOPE("k_sort_segments", s);
-        k_sort_segments<<<(unsigned)((nq + warps - 1) / warps), 32 * warps, smem, s>>>(seg, nq, cap, packable, qi, pj,
-                                                                                        dist);
+        k_sort_segments<true><<<grid, 32 * warps, smem, s>>>(seg, nq, cap, width, packable, qi, pj, dist);
+    } else {
+        FGB_CUDA(cudaFuncSetAttribute(k_sort_segments<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FGB_KSCOPE("k_sort_segments", s);
+        k_sort_segments<false><<<grid, 32 * warps, smem, s>>>(seg, nq, cap, width, packable, qi, pj, dist);
     }
     FGB_LAUNCH_CHECK();
     return FGB_OK;
@@ -794,5 +979,21 @@ int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, 
 }
 
 size_t tile_write_smem(int cap) { return (size_t)kTileWarps * write_warp_bytes(cap); }
+
+int tile_write_global(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+                      const uint32_t *counts, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, R, exclude);
+    t.err = err;
+    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
+        FGB_KSCOPE("k_tile_write_global", s);
+        k_tile_write_global<32><<<grid, kTileWarps * 32, 0, s>>>(t, seg, counts, qi, pj, dist);
+    } else {
+        FGB_KSCOPE("k_tile_write_global", s);
+        k_tile_write_global<kTileMaxStencil><<<grid, kTileWarps * 32, 0, s>>>(t, seg, counts, qi, pj, dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
 
 }  // namespace fgb

@@ -462,3 +462,21 @@ def test_kernel_family_switches(switch):
     r = subprocess.run([sys.executable, "-c", KERNEL_SWITCH_CHECKS], env=env, cwd=root, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]
+
+
+def test_ball_dense_rows_global_path(fgb):
+    # blobs whose rows run from a few hundred to about 2,000 neighbors: the cell tiles
+    # append them to the list and a shared-memory network sorts each row; the tree
+    # query's row sort takes the same network
+    b = W.Box.cube(40.0)
+    rng = np.random.default_rng(77)
+    bg = W.uniform_points(rng, b, 10000)
+    centres = rng.uniform(-15, 15, size=(4, 3))
+    blobs = (np.repeat(centres, 2500, axis=0) + rng.normal(0.0, 0.45, size=(10000, 3))).astype(np.float32)
+    x = np.concatenate([bg, blobs]).astype(np.float32)
+    ref = oracle.ball_query(b, x, 1.0)
+    assert np.diff(ref[1]).max() > 1024 and np.diff(ref[1]).max() <= 16384
+    nl = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(r_max=1.0, exclude_ii=True)).toNeighborList()
+    assert_ball_equal(nl, ref, 1.0)
+    tl = fgb.AABBQuery(b, dev(x)).query(None, dict(r_max=1.0, exclude_ii=True)).toNeighborList()
+    assert_ball_equal(tl, ref, 1.0)

@@ -224,6 +224,19 @@ def p6(seed: int = 6, n: int = 20_000, n_frames: int = 10, neighbors: float = 12
 P6_PARAMS = dict(x_max=1.0, y_max=1.0, bins_x=100, bins_y=100, rdf_bins=100, rdf_r_max=math.sqrt(2.0))
 
 
+def blobs(seed: int = 7, n_blobs: int = 2000, per_blob: int = 1000, sigma: float = 0.5,
+          density: float = 0.1) -> Workload:
+    """Clustered points: Gaussian blobs (standard deviation sigma) at uniform centres in
+    a cubic box sized for the given overall density; a workload of very uneven cell
+    occupancy for comparing the tree query with the cell list."""
+    rng = np.random.default_rng(seed)
+    n = n_blobs * per_blob
+    box = Box.cube((n / density) ** (1.0 / 3.0))
+    centres = frac_to_cart(box, rng.random((n_blobs, 3)))
+    x = np.repeat(centres, per_blob, axis=0) + rng.normal(0.0, sigma, size=(n, 3))
+    return Workload(f"blobs{n_blobs}x{per_blob}", box, _to_f32(x), dict(r_max=1.0))
+
+
 def small_random(seed: int, n: int, box: Box) -> np.ndarray:
     return uniform_points(np.random.default_rng(seed), box, n)
 
