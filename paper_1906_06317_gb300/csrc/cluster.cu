@@ -6,7 +6,12 @@
 // larger of its two current roots under the smaller with an atomic compare-and-swap
 // (parents only ever decrease, so the forest stays acyclic and a component's root is its
 // smallest index); a failed swap means another bond moved that root, and the bond simply
-// looks its roots up again.  Clusters are then numbered by decreasing size, ties by
+// looks its roots up again.  A sampling pass first joins every point with the other ends
+// of its first two bonds, which in a neighbor graph already links most points into their
+// final components; the full pass then skips every bond whose ends had the same root
+// after sampling (such a bond joins nothing new), so crystals and dense clusters cost
+// two loads per bond (sampling after Sutton, Ben-Nun and Barak, "Optimizing Parallel
+// Graph Connectivity Computation via Subgraph Sampling", IPDPS 2018).  Clusters are then numbered by decreasing size, ties by
 // their smallest member, through one stable radix sort of (n - size) over the roots.
 //
 // Properties: each member is unwrapped to the image nearest the cluster's smallest
@@ -40,12 +45,8 @@ __global__ void k_cc_init(int *parent, int64_t n) {
     if (i < n) parent[i] = (int)i;
 }
 
-// One thread per bond (i, j); mask[e] == 0 skips the bond.
-__global__ void k_cc_union(const int32_t *__restrict__ qi, const int32_t *__restrict__ pj,
-                           const uint8_t *__restrict__ mask, int64_t m, int *parent, int *err) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m || (mask && !mask[e])) return;
-    int a = qi[e], b = pj[e];
+// Joins the components of a and b.
+__device__ __forceinline__ void cc_link(int *parent, int a, int b, int *err) {
     for (int it = 0; it < kUnionRetries; ++it) {
         a = cc_find(parent, a);
         b = cc_find(parent, b);
@@ -59,6 +60,46 @@ __global__ void k_cc_union(const int32_t *__restrict__ qi, const int32_t *__rest
         if (atomicCAS(parent + a, a, b) == a) return;
     }
     atomicExch(err, 1);
+}
+
+// Sampling pass: point i joins the other ends of the first two unmasked bonds of its
+// segment [seg[i], seg[i+1]) of the query-ordered list.
+__global__ void k_cc_sample(const int64_t *__restrict__ seg, int64_t nq, const int32_t *__restrict__ pj,
+                            const uint8_t *__restrict__ mask, int *parent, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    int taken = 0;
+    for (int64_t e = seg[i]; e < seg[i + 1] && taken < 2; ++e) {
+        if (mask && !mask[e]) continue;
+        cc_link(parent, (int)i, pj[e], err);
+        ++taken;
+    }
+}
+
+// Every point's root after sampling (also written as its parent, one of its ancestors).
+__global__ void k_cc_snapshot(int *parent, int64_t n, int *comp, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = cc_find(parent, (int)i);
+    if (r < 0) {
+        atomicExch(err, 1);
+        comp[i] = -1 - (int)i;  // matches no other point: its bonds take the full pass
+        return;
+    }
+    comp[i] = r;
+    parent[i] = r;
+}
+
+// One thread per bond (i, j); mask[e] == 0 skips the bond, and so does a bond whose ends
+// had the same root after sampling (comp).
+__global__ void k_cc_union(const int32_t *__restrict__ qi, const int32_t *__restrict__ pj,
+                           const uint8_t *__restrict__ mask, int64_t m, const int *__restrict__ comp, int *parent,
+                           int *err) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m || (mask && !mask[e])) return;
+    const int a = qi[e], b = pj[e];
+    if (__ldg(comp + a) == __ldg(comp + b)) return;
+    cc_link(parent, a, b, err);
 }
 
 // Final roots and component sizes.
@@ -216,9 +257,18 @@ extern "C" int fgb_cluster_compute(int64_t n, const fgb_nlist *nlist, const uint
             k_cc_init<<<grid1d(n, 256), 256, 0, s>>>(parent, n);
         }
         if (nlist->n_pairs > 0) {
+            {
+                FGB_KSCOPE("k_cc_sample", s);
+                k_cc_sample<<<grid1d(nlist->n_query, 256), 256, 0, s>>>(nlist->segments, nlist->n_query, nlist->pj,
+                                                                         bond_mask, parent, err);
+            }
+            {
+                FGB_KSCOPE("k_cc_snapshot", s);
+                k_cc_snapshot<<<grid1d(n, 256), 256, 0, s>>>(parent, n, root, err);
+            }
             FGB_KSCOPE("k_cc_union", s);
             k_cc_union<<<grid1d(nlist->n_pairs, 256), 256, 0, s>>>(nlist->qi, nlist->pj, bond_mask, nlist->n_pairs,
-                                                                    parent, err);
+                                                                    root, parent, err);
         }
         {
             FGB_KSCOPE("k_cc_roots", s);
