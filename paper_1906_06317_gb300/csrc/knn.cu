@@ -4,7 +4,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "fgb_device.cuh"
+#include "fgb_tile.cuh"
 
 namespace fgb {
 
@@ -158,6 +158,154 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a) {
         }
 }
 
+// Listed queries (those the cell-tile kernel left: too many candidates for its rows,
+// too few within its radius, or a near tie), a warp each: the same stencil walk,
+// widening and ranking rule as k_knn, with each cell's candidates split across the
+// lanes.  The best candidates so far are 64-bit keys (r2 bits << 32 | index: the (r2,
+// index) order, r2 >= 0) in a per-warp shared buffer; a candidate enters when its key is
+// below the KT-th best, and the buffer is sorted and cut back to KT entries whenever it
+// holds 64 or more, so dense cells cost about one compare per candidate.
+constexpr int kKnnWarps = 4;
+constexpr int kKnnBuf = 128;
+
+// Sorts buf[0, nb) (nb <= kKnnBuf, padded with ~0) and keeps the KT best; returns their
+// number and sets thr to the KT-th key (all ones while fewer are kept).
+template <int KT>
+__device__ __forceinline__ int knn_trim(unsigned long long *buf, int nb, unsigned long long &thr) {
+    const int lane = threadIdx.x & 31;
+    for (int k = nb + lane; k < kKnnBuf; k += 32) buf[k] = ~0ull;
+    __syncwarp();
+    for (unsigned k = 2; k <= (unsigned)kKnnBuf; k <<= 1)
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned t = lane; t < kKnnBuf / 2; t += 32) {
+                const unsigned e = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = e | j;
+                const unsigned long long x = buf[e], y = buf[l];
+                if ((x > y) == ((e & k) == 0)) {
+                    buf[e] = y;
+                    buf[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+    const int kept = min(nb, KT);
+    thr = kept == KT ? buf[KT - 1] : ~0ull;
+    return kept;
+}
+
+__device__ __forceinline__ float key_r2(unsigned long long key) { return __uint_as_float((uint32_t)(key >> 32)); }
+
+template <int KT>
+__global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(KnnArgs a) {
+    __shared__ unsigned long long sbuf[kKnnWarps][kKnnBuf];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long *buf = sbuf[warp];
+    const unsigned lt = lanemask_lt();
+    const int nlist = *a.list_count;
+    for (int64_t w = (int64_t)blockIdx.x * kKnnWarps + warp; w < nlist; w += (int64_t)gridDim.x * kKnnWarps) {
+        const int64_t t = a.list[w];
+        const float4 q = a.qs[t];
+        const int i = __float_as_int(q.w);
+        int cx, cy, cz;
+        cell_coords(a.qcell[t], a.nc, cx, cy, cz);
+        const int excl = a.exclude ? i : -1;
+        const int avail = (int)min((int64_t)0x7fffffff, a.npts - ((a.exclude && i < a.npts) ? 1 : 0));
+        const int m = min(a.k, avail);
+        int nb = 0, found = 0, s = 1, mode = 0;
+        unsigned long long thr = ~0ull;
+        float delta = 0.f;
+        for (;; ++s) {
+            bool all_full;
+            const Stencil S = knn_stencil(a, s, all_full);
+            mode = S.mode;
+            nb = 0;
+            found = 0;
+            thr = ~0ull;
+            // the query's own cell first (its points set a tight threshold at once), then
+            // the rest of the stencil
+            const int own = (cz * a.nc[1] + cy) * a.nc[0] + cx;
+            for (int pass = 0; pass < 2; ++pass)
+            for_stencil(S, cx, cy, cz, make_float3(q.x, q.y, q.z), false,
+                        [&](int cell, float qx, float qy, float qz, bool) {
+                            if ((cell == own) != (pass == 0)) return;
+                            const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
+                            for (uint32_t p0 = beg; p0 < end; p0 += 32) {
+                                const uint32_t p = p0 + lane;
+                                bool valid = false, take = false;
+                                unsigned long long key = ~0ull;
+                                if (p < end) {
+                                    const float4 c = __ldg(a.pts + p);
+                                    const int j = __float_as_int(c.w);
+                                    if (j != excl) {
+                                        const float3 d = cand_disp(S, a.bf, c, qx, qy, qz);
+                                        const float r2 = r2_f32(d.x, d.y, d.z);
+                                        key = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)j;
+                                        valid = true;
+                                        take = key < thr;
+                                    }
+                                }
+                                found += __popc(__ballot_sync(0xffffffffu, valid));
+                                const unsigned mk = __ballot_sync(0xffffffffu, take);
+                                if (take) buf[nb + __popc(mk & lt)] = key;  // nb <= 63 here
+                                nb += __popc(mk);
+                                if (nb >= 64) {
+                                    __syncwarp();
+                                    nb = knn_trim<KT>(buf, nb, thr);
+                                }
+                            }
+                        });
+            __syncwarp();
+            nb = knn_trim<KT>(buf, nb, thr);
+            if (all_full) {
+                delta = knn_delta(a, mode, s, m > 0 ? sqrtf(key_r2(buf[min(m, KT) - 1])) : 0.f);
+                break;
+            }
+            float rcov = INFINITY;
+            for (int k2 = 0; k2 < 3; ++k2)
+                if (!S.full[k2]) rcov = fminf(rcov, s * a.wc[k2]);
+            rcov *= 0.99999f;
+            if (found >= m && m > 0) {
+                const float rk2 = key_r2(buf[m - 1]);
+                delta = knn_delta(a, mode, s, sqrtf(rk2) + 1e-3f);
+                if (rk2 + delta < rcov * rcov) break;
+            } else if (m == 0) {
+                break;
+            }
+        }
+        if (lane == 0) a.counts[i] = m;
+        const float rm2 = m > 0 ? key_r2(buf[m - 1]) : 0.f;
+        if (m > 0 && rm2 + delta >= a.half_wmin2) {
+            if (lane == 0) atomicOr(a.err, 1);
+            __syncwarp();
+            continue;
+        }
+        // a ranking is certain when every neighbouring gap among the first m+1 exceeds 2 delta
+        const int last = min(found, KT) - 1;
+        const bool gap_small =
+            lane < m && lane + 1 <= last && key_r2(buf[lane + 1]) - key_r2(buf[lane]) <= 2.f * delta;
+        if (__any_sync(0xffffffffu, gap_small)) {
+            if (lane == 0) {
+                const int slot = atomicAdd(a.flag_count, 1);
+                if (slot < a.flag_cap) {
+                    const float thr2 = rm2 + 2.f * delta;
+                    a.flags[slot] = make_int4((int)t, s, __float_as_int(thr2 * 1.0000005f), 0);
+                } else {
+                    atomicOr(a.err, 2);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        const int64_t row = (int64_t)i * a.stride;
+        if (lane < m) {
+            const unsigned long long key = buf[lane];
+            a.qi_out[row + lane] = i;
+            a.pj_out[row + lane] = (int)(uint32_t)key;
+            a.d_out[row + lane] = sqrtf(key_r2(key));
+        }
+        __syncwarp();
+    }
+}
+
 // Exact ranking for flagged queries: candidates whose FP32 r2 is within the threshold
 // get their FP64 r2 and are ranked by (r2, j) in double precision.
 template <int KT>
@@ -240,7 +388,12 @@ __global__ void k_knn_segments(int64_t nq, int m, int64_t *seg) {
 
 template <int KT>
 static void launch_knn(const KnnArgs &a, cudaStream_t s) {
-    {
+    if (a.list) {
+        // the queries the cell-tile kernel left, a warp each (the list length is on the
+        // device: a grid of warps walks it)
+        FGB_KSCOPE("k_knn_warp", s);
+        k_knn_warp<KT><<<(unsigned)num_sms() * 8, kKnnWarps * 32, 0, s>>>(a);
+    } else {
         FGB_KSCOPE("k_knn", s);
         k_knn<KT><<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a);
     }

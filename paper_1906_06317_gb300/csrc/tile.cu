@@ -790,6 +790,12 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, Knn
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
     const int m = K.stride;
+    // about 4/27 of a 27-cell stencil lies within the covered radius: a stencil this
+    // dense overflows the 64-slot rows, so its queries go to the warp kernel at once
+    if (total > 1024) {
+        for (int q = lane; q < nA; q += 32) K.list[atomicAdd(K.list_count, 1)] = begA + q;
+        return;
+    }
     for (int qb = 0; qb < nA; qb += kTileQueries) {
         const int nq = min(kTileQueries, nA - qb);
         const QLayout L = qlayout(nq);
