@@ -111,8 +111,8 @@ class ClockSampler:
 # so it is scaled to the bench's N; once the source changes the figure is stale and is
 # reported as null.
 MEASURED_TRAFFIC = {
-    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "4fc0386f65dc27e9", 558.313216e6 + 1537.225e6, 2097152),
-    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "4fc0386f65dc27e9", 34.413568e6 + 0.013e6, 2097152),
+    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "6290c9852eb4eaa9", 559.067648e6 + 1537.455e6, 2097152),
+    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "6290c9852eb4eaa9", 34.415104e6 + 0.025e6, 2097152),
     "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "1c4f2babc9bbf151", 34.247936e6 + 0.01152e6, 2097152),
 }
 
