@@ -480,3 +480,20 @@ def test_ball_dense_rows_global_path(fgb):
     assert_ball_equal(nl, ref, 1.0)
     tl = fgb.AABBQuery(b, dev(x)).query(None, dict(r_max=1.0, exclude_ii=True)).toNeighborList()
     assert_ball_equal(tl, ref, 1.0)
+
+
+@pytest.mark.parametrize("k", [6, 12])
+def test_knn_dense_clusters(fgb, k):
+    # blob cells hold hundreds of points: the cell-tile kNN lists their queries and a warp
+    # per query keeps the best candidates in a shared buffer trimmed to k + 1
+    b = W.Box.cube(40.0)
+    rng = np.random.default_rng(78)
+    bg = W.uniform_points(rng, b, 10000)
+    centres = rng.uniform(-15, 15, size=(4, 3))
+    blobs = (np.repeat(centres, 2500, axis=0) + rng.normal(0.0, 0.45, size=(10000, 3))).astype(np.float32)
+    x = np.concatenate([bg, blobs]).astype(np.float32)
+    nl = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=k, exclude_ii=True)).toNeighborList()
+    assert_knn_equal(nl, oracle.knn(b, x, k), k)
+    if k == 12:
+        tl = fgb.AABBQuery(b, dev(x)).query(None, dict(num_neighbors=k, exclude_ii=True)).toNeighborList()
+        assert_knn_equal(tl, oracle.knn(b, x, k), k)
