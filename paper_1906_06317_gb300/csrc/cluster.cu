@@ -62,16 +62,17 @@ __device__ __forceinline__ void cc_link(int *parent, int a, int b, int *err) {
     atomicExch(err, 1);
 }
 
-// Sampling pass: point i joins the other ends of the first two unmasked bonds of its
-// segment [seg[i], seg[i+1]) of the query-ordered list.
-__global__ void k_cc_sample(const int64_t *__restrict__ seg, int64_t nq, const int32_t *__restrict__ pj,
-                            const uint8_t *__restrict__ mask, int *parent, int *err) {
+// Sampling pass: the first two unmasked bonds of every segment [seg[i], seg[i+1]) join
+// their two ends (for a query-ordered list, point i and two of its neighbors; each link
+// is a bond of the list whatever its order, so the result never depends on it).
+__global__ void k_cc_sample(const int64_t *__restrict__ seg, int64_t nq, const int32_t *__restrict__ qi,
+                            const int32_t *__restrict__ pj, const uint8_t *__restrict__ mask, int *parent, int *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nq) return;
     int taken = 0;
     for (int64_t e = seg[i]; e < seg[i + 1] && taken < 2; ++e) {
         if (mask && !mask[e]) continue;
-        cc_link(parent, (int)i, pj[e], err);
+        cc_link(parent, qi[e], pj[e], err);
         ++taken;
     }
 }
@@ -259,8 +260,8 @@ extern "C" int fgb_cluster_compute(int64_t n, const fgb_nlist *nlist, const uint
         if (nlist->n_pairs > 0) {
             {
                 FGB_KSCOPE("k_cc_sample", s);
-                k_cc_sample<<<grid1d(nlist->n_query, 256), 256, 0, s>>>(nlist->segments, nlist->n_query, nlist->pj,
-                                                                         bond_mask, parent, err);
+                k_cc_sample<<<grid1d(nlist->n_query, 256), 256, 0, s>>>(nlist->segments, nlist->n_query, nlist->qi,
+                                                                         nlist->pj, bond_mask, parent, err);
             }
             {
                 FGB_KSCOPE("k_cc_snapshot", s);
