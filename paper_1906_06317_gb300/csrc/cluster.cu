@@ -103,18 +103,25 @@ __global__ void k_cc_union(const int32_t *__restrict__ qi, const int32_t *__rest
     cc_link(parent, a, b, err);
 }
 
-// Final roots and component sizes.
+// Final roots and component sizes; the lanes of a warp with the same root add to its
+// size once (one atomic per distinct root: a spanning cluster would otherwise put every
+// point's addition on one address).
 __global__ void k_cc_roots(int *parent, int64_t n, int *root, uint32_t *size, int *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int r = cc_find(parent, (int)i);
-    if (r < 0) {
-        atomicExch(err, 1);
-        root[i] = (int)i;
-        return;
+    int r = -1;
+    if (i < n) {
+        r = cc_find(parent, (int)i);
+        if (r < 0) {
+            atomicExch(err, 1);
+            r = (int)i;
+        }
+        root[i] = r;
     }
-    root[i] = r;
-    atomicAdd(size + r, 1u);
+    const unsigned live = __ballot_sync(0xffffffffu, i < n);
+    if (i >= n) return;
+    const unsigned same = __match_any_sync(live, r);
+    const int lane = threadIdx.x & 31;
+    if (lane == __ffs(same) - 1) atomicAdd(size + r, (uint32_t)__popc(same));
 }
 
 __global__ void k_cc_is_root(const int *__restrict__ root, int64_t n, uint32_t *flag) {
@@ -153,33 +160,53 @@ __global__ void k_cc_label(const int *__restrict__ root, const int *__restrict__
 
 // ------------------------------------------------------------------ properties
 
+// Adds v to *dst for every lane of the warp (live: the lanes holding a point; cluster c).
+// A warp whose points all belong to one cluster (the usual case for large clusters, whose
+// points sit together in index order more often than not) adds its sum once; otherwise
+// every lane adds its own value.
+__device__ __forceinline__ void warp_add(double *dst, double v, bool uniform) {
+    if (uniform) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(dst, v);
+    } else {
+        atomicAdd(dst, v);
+    }
+}
+
 __global__ void k_cl_offsets(BoxF b, const float *__restrict__ x, int64_t n, const int32_t *__restrict__ cid,
                              const int32_t *__restrict__ roots, double *sums) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cid[i];
-    const float3 d = bond_f32(b, x, roots[c], i);
-    atomicAdd(sums + 3 * c + 0, (double)d.x);
-    atomicAdd(sums + 3 * c + 1, (double)d.y);
-    atomicAdd(sums + 3 * c + 2, (double)d.z);
+    const bool live = i < n;
+    const int c = live ? cid[i] : -1;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    const bool uniform = __all_sync(0xffffffffu, live && c == c0);
+    if (!uniform && !live) return;
+    const float3 d = live ? bond_f32(b, x, roots[c], i) : make_float3(0.f, 0.f, 0.f);
+    warp_add(sums + 3 * c + 0, (double)d.x, uniform);
+    warp_add(sums + 3 * c + 1, (double)d.y, uniform);
+    warp_add(sums + 3 * c + 2, (double)d.z, uniform);
 }
 
 __global__ void k_cl_gyration(BoxF b, const float *__restrict__ x, int64_t n, const int32_t *__restrict__ cid,
                               const int32_t *__restrict__ roots, const int32_t *__restrict__ sizes,
                               const double *__restrict__ sums, double *g) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cid[i];
+    const bool live = i < n;
+    const int c = live ? cid[i] : -1;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    const bool uniform = __all_sync(0xffffffffu, live && c == c0);
+    if (!uniform && !live) return;
     const float3 d = bond_f32(b, x, roots[c], i);
     const double inv = 1.0 / sizes[c];
     const double ex = d.x - sums[3 * c] * inv, ey = d.y - sums[3 * c + 1] * inv, ez = d.z - sums[3 * c + 2] * inv;
     double *gc = g + 6 * c;
-    atomicAdd(gc + 0, ex * ex);
-    atomicAdd(gc + 1, ex * ey);
-    atomicAdd(gc + 2, ex * ez);
-    atomicAdd(gc + 3, ey * ey);
-    atomicAdd(gc + 4, ey * ez);
-    atomicAdd(gc + 5, ez * ez);
+    warp_add(gc + 0, ex * ex, uniform);
+    warp_add(gc + 1, ex * ey, uniform);
+    warp_add(gc + 2, ex * ez, uniform);
+    warp_add(gc + 3, ey * ey, uniform);
+    warp_add(gc + 4, ey * ez, uniform);
+    warp_add(gc + 5, ez * ez, uniform);
 }
 
 // centre = x_root + mean offset, wrapped into the box; gyration = mean outer product
