@@ -215,7 +215,11 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     const bool checkj = !Q.self && a.exclude;
     const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && !force_thread_kernels();
     if (st == FGB_OK && nqq > 0 && tile) {
-        st = tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
+        // 2D: the tile kernels walk only the points' layer; a point off the plane keeps a
+        // count of zero instead of an unwritten one
+        if (nq->box.is2d && cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nqq, s) != cudaSuccess)
+            st = fail(FGB_ERR_CUDA, "memset failed");
+        st = st ? st : tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
         st = st ? st : scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK && nqq > 0) {
         const unsigned grid = (unsigned)((nqq + 127) / 128);

@@ -18,7 +18,8 @@ struct TileArgs {
     const float4 *off;        // offset table of half-width ts
     const float4 *pts;        // sorted records
     const uint32_t *cell_start;
-    int64_t ncell;
+    int64_t ncell;            // query cells walked: [cell_lo, ncell)
+    int64_t cell_lo;          // (2D grids: the layer that holds the points)
     const float *p_orig;
     BoxF bf;
     BoxD bd;

@@ -479,7 +479,10 @@ int knn_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *args, cuda
         const bool tile = Q.self && plan.mode == 0 && plan.s[0] == 1 && plan.s[1] == 1 && plan.s[2] == 1 &&
                           m_uniform >= 1 && m_uniform <= 62 && tile_worth(nq) && !force_thread_kernels();
         if (tile && nqq > 0) {
-            st = tile_knn(nq, plan, k, m_uniform, a.exclude, tqi, tpj, td, nl->counts, ctl + 4, ctl + 2, s);
+            // 2D: only the points' layer is walked; a point off the plane keeps a zero count
+            if (nq->box.is2d && cudaMemsetAsync(nl->counts, 0, sizeof(int32_t) * nqq, s) != cudaSuccess)
+                st = fail(FGB_ERR_CUDA, "memset failed");
+            st = st ? st : tile_knn(nq, plan, k, m_uniform, a.exclude, tqi, tpj, td, nl->counts, ctl + 4, ctl + 2, s);
             a.list = ctl + 4;
             a.list_count = ctl + 2;
         }

@@ -282,15 +282,16 @@ __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_co
     const float reach2 = a.P.rmax_hi * (1.0f + 1e-5f);
     uint64_t tests = 0;  // pair tests since the last flush bound every private count
     for (;;) {
-        unsigned A = 0;
-        if (lane == 0) A = atomicAdd(a.work, 1u);
-        A = __shfl_sync(0xffffffffu, A, 0);
-        if ((int64_t)A >= a.t.ncell) break;
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(a.work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const int64_t A = a.t.cell_lo + (int64_t)w;
+        if (A >= a.t.ncell) break;
         const int begA = (int)__ldg(a.t.cell_start + A);
         const int nA = (int)__ldg(a.t.cell_start + A + 1) - begA;
         if (nA == 0) continue;
         int cx, cy, cz;
-        cell_coords(A, a.t.nc, cx, cy, cz);
+        cell_coords((uint32_t)A, a.t.nc, cx, cy, cz);
         __syncwarp();
         const int n = tile_stencil(a.t, cx, cy, cz, true, ts);
         const int total = ts.pre[n];
@@ -442,7 +443,7 @@ static int launch_rdf_tile_ns(const RdfTileArgs &ta, cudaStream_t s) {
     const size_t smem = (size_t)kRdfTileWarps * ta.bins * sizeof(uint32_t);
     int per_sm = 0;
     FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_tile<NS>, kRdfTileWarps * 32, smem));
-    const int64_t cells = ta.t.ncell;
+    const int64_t cells = ta.t.ncell - ta.t.cell_lo;
     const int64_t want = (cells + kRdfTileWarps - 1) / kRdfTileWarps;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * std::max(per_sm, 1)));
     FGB_KSCOPE("k_rdf_tile", s);

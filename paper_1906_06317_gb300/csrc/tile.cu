@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_count(TileArgs a, u
     __shared__ TileStencilT<NS> sts[kTileWarps];
     __shared__ float4 sstage[kTileWarps][64];  // kept candidates, packed
     const int warp = threadIdx.x >> 5;
-    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_
     __shared__ float4 sstage[kTileWarps][32];
     __shared__ int srow[kTileWarps][kTileQueries];
     const int warp = threadIdx.x >> 5;
-    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global(const __g
     __shared__ float4 sstage[kTileWarps][32];
     __shared__ int srow[kTileWarps][kTileQueries];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, Knn
     __shared__ uint2 srowbuf[kTileWarps][kTileQueries][64];
     __shared__ int srow[kTileWarps][kTileQueries];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t A = (int64_t)blockIdx.x * kTileWarps + warp;
+    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
@@ -906,6 +906,14 @@ TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude
     t.pts = nq->sorted;
     t.cell_start = nq->cell_start;
     t.ncell = nq->grid.ncell;
+    t.cell_lo = 0;
+    if (nq->box.is2d) {
+        // every point of a 2D box lies in the middle of the three z layers: its query cells
+        // are that layer's (points elsewhere break the z = 0 rule and are not queried)
+        const int64_t layer = (int64_t)nq->grid.nc[0] * nq->grid.nc[1];
+        t.cell_lo = layer;
+        t.ncell = 2 * layer;
+    }
     t.p_orig = nq->points;
     t.bf = nq->box.f;
     t.bd = nq->box.d;
@@ -920,7 +928,7 @@ int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, un
     TileArgs t = tile_args(nq, p, R, exclude);
     t.esc = esc;
     t.err = err;
-    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    const unsigned grid = (unsigned)((t.ncell - t.cell_lo + kTileWarps - 1) / kTileWarps);
     if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
         FGB_KSCOPE("k_tile_count", s);
         k_tile_count<32><<<grid, kTileWarps * 32, 0, s>>>(t, counts);
@@ -940,7 +948,7 @@ int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, in
     t.err = err;
     const size_t smem = tile_write_smem(cap);
     if (smem > 160 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tile write: neighbor count too large");
-    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    const unsigned grid = (unsigned)((t.ncell - t.cell_lo + kTileWarps - 1) / kTileWarps);
     const int packable = cap <= 128 && nq->n < ((int64_t)1 << 25);
     // the kernel also holds static shared memory: always raise the dynamic limit
     if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
@@ -975,7 +983,7 @@ int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, 
     K.counts = counts;
     K.list = list;
     K.list_count = list_count;
-    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    const unsigned grid = (unsigned)((t.ncell - t.cell_lo + kTileWarps - 1) / kTileWarps);
     {
         FGB_KSCOPE("k_tile_knn", s);
         k_tile_knn<32><<<grid, kTileWarps * 32, 0, s>>>(t, K);
@@ -990,7 +998,7 @@ int tile_write_global(const fgb_nq *nq, const StencilPlan &p, double R, int excl
                       const uint32_t *counts, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
     TileArgs t = tile_args(nq, p, R, exclude);
     t.err = err;
-    const unsigned grid = (unsigned)((nq->grid.ncell + kTileWarps - 1) / kTileWarps);
+    const unsigned grid = (unsigned)((t.ncell - t.cell_lo + kTileWarps - 1) / kTileWarps);
     if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
         FGB_KSCOPE("k_tile_write_global", s);
         k_tile_write_global<32><<<grid, kTileWarps * 32, 0, s>>>(t, seg, counts, qi, pj, dist);
