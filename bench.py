@@ -111,9 +111,9 @@ class ClockSampler:
 # so it is scaled to the bench's N; once the source changes the figure is stale and is
 # reported as null.
 MEASURED_TRAFFIC = {
-    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "6290c9852eb4eaa9", 559.067648e6 + 1537.455e6, 2097152),
-    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "6290c9852eb4eaa9", 34.415104e6 + 0.025e6, 2097152),
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "1c4f2babc9bbf151", 34.247936e6 + 0.01152e6, 2097152),
+    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "06f1005e6e3ebc0d", 558.15552e6 + 1537.322e6, 2097152),
+    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "06f1005e6e3ebc0d", 34.582528e6 + 0.12e6, 2097152),
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "321bbcb2ac39fe62", 34.208e6 + 0.022e6, 2097152),
 }
 
 
