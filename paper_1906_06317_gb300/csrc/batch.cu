@@ -164,10 +164,12 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs a) {
 #pragma unroll
                 for (int m = 0; m <= L; ++m) sr[m] = si[m] = 0.f;
                 int n = 0;
+                BondBuffer<L> bb;
                 ball_visit(fr.ball, p, lc, i, [&](int, float3 d, float, double) {
                     ++n;
-                    accumulate_bond<L>(d, sr, si);
+                    bb.add(d, sr, si);
                 });
+                bb.flush(sr, si);
                 finish<L>(i, n, sr, si, a.q, a.Q, a.nn);
             }
         }

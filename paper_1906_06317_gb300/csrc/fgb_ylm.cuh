@@ -115,6 +115,26 @@ __device__ __forceinline__ void accumulate_bond(float3 d, float (&sr)[L + 1], fl
     }
 }
 
+// Bonds met during a neighbor walk, accumulated after it (or whenever the buffer fills):
+// inside the walk only the hit branch would evaluate the harmonics, with the warp's lanes
+// that found no neighbor idle, while a separate loop keeps them in step.  Bonds are
+// accumulated in the order met, so the sums equal accumulating them in the walk.
+constexpr int kBondBuf = 32;
+
+template <int L>
+struct BondBuffer {
+    float3 d[kBondBuf];
+    int nb = 0;
+    __device__ __forceinline__ void add(float3 v, float (&sr)[L + 1], float (&si)[L + 1]) {
+        d[nb++] = v;
+        if (nb == kBondBuf) flush(sr, si);
+    }
+    __device__ __forceinline__ void flush(float (&sr)[L + 1], float (&si)[L + 1]) {
+        for (int k = 0; k < nb; ++k) accumulate_bond<L>(d[k], sr, si);
+        nb = 0;
+    }
+};
+
 // Raw gradient of Re sum_m f_m conj(Q_m) Y~_m at u (before projection), f_0 = 1, f_m = 2.
 template <int L>
 __device__ __forceinline__ float3 contract_grad(const float (&A)[L + 2], const float (&wr)[L + 1],

@@ -50,10 +50,12 @@ __global__ void __launch_bounds__(128) k_st_fused(BallArgs a, float *__restrict_
 #pragma unroll
     for (int m = 0; m <= L; ++m) sr[m] = si[m] = 0.f;
     int n = 0;
+    BondBuffer<L> bb;
     const int nesc = ball_visit(a, p, a.qcell[t], i, [&](int, float3 d, float, double) {
         ++n;
-        accumulate_bond<L>(d, sr, si);
+        bb.add(d, sr, si);
     });
+    bb.flush(sr, si);
     if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
     finish<L>(i, n, sr, si, q, Q, nn);
 }
