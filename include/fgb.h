@@ -428,9 +428,10 @@ typedef struct fgb_batch_params {
     double rdf_r_max;
     double rdf_r_min;
     int32_t cell_div;    /* cells per r_max along each axis: 1 or 2; 0 = autotune */
-    int32_t block;       /* threads per block of the persistent kernel: 64..512; 0 = autotune */
-    int32_t hist_copies; /* shared histogram copies per block: 1, 2 or 4; 0 = autotune */
-    int32_t reserved;
+    int32_t block;       /* threads per block of the per-point kernel: 64..512; 0 = autotune */
+    int32_t hist_copies; /* its shared histogram copies per block: 1, 2 or 4; 0 = autotune */
+    int32_t tile_cells;  /* largest work item of the cell-tile kernels, in cells: 1..4096;
+                            0 = autotune; -1 = every frame on the per-point kernel */
 } fgb_batch_params;
 
 /*
@@ -445,22 +446,30 @@ int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, const fgb_b
                      const fgb_batch_params *params, void *stream, fgb_batch **out);
 void fgb_batch_destroy(fgb_batch *b);
 
-/* One pass over all frames: per-frame binning, one sort over all frames, and one
- * persistent kernel that computes every frame's RDF counts and q_l. */
+/* One pass over all frames: per-frame binning and one sort over all frames, then every
+ * frame's RDF counts and q_l.  A frame whose RDF half stencil and ball stencil are both
+ * on the fixed-offset route with at most 128 cells (and rdf_bins <= 1024) takes the
+ * persistent cell-tile kernels (a warp per query cell, work items of up to tile_cells
+ * cells); the others take the persistent per-point kernel (a thread per point).  The RDF
+ * counts are the same either way; q_l may differ in the last bits (summation order). */
 int fgb_batch_run(fgb_batch *b, const float *points, void *stream);
 
 /* Same work replayed from a CUDA graph captured on the first call for this `points`
  * pointer (recaptured when it changes). */
 int fgb_batch_run_graph(fgb_batch *b, const float *points, void *stream);
 
-/* Times the candidate (cell_div, block, hist_copies) settings on `points` and keeps the
- * fastest (the parameters set to 0 at create).  Synchronises `stream`. */
+/* Times the candidate (cell_div, tile_cells, block, hist_copies) settings on `points` and
+ * keeps the fastest (the parameters set to 0 at create).  Synchronises `stream`. */
 int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, fgb_batch_params *chosen);
 
 /* Device outputs: RDF counts uint64 (n_frames, bins), q_l float32 (total points, in
  * input order), neighbor counts int32 (total). */
 int fgb_batch_outputs(const fgb_batch *b, const uint64_t **rdf_counts, const float **q,
                       const int32_t **n_neighbors);
+
+/* Number of frames on the cell-tile kernels and on the per-point kernel in the current
+ * configuration (host values; either pointer may be NULL). */
+int fgb_batch_routes(const fgb_batch *b, int32_t *tile_frames, int32_t *point_frames);
 
 #ifdef __cplusplus
 }

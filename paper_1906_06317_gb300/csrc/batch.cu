@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "fgb_ball.cuh"
+#include "fgb_batch.cuh"
 #include "fgb_ylm.cuh"
 
 namespace fgb {
@@ -226,8 +227,8 @@ struct fgb_batch {
     std::vector<fgb_box> boxes;
     fgb_batch_params prm;
     int64_t total;
-    int cell_div, block, copies;
-    bool tune_div, tune_block, tune_copies;
+    int cell_div, block, copies, tile_cells;
+    bool tune_div, tune_block, tune_copies, tune_tile;
     // configuration-dependent device state
     FrameDev *frames_d;
     float2 *origin_d;
@@ -235,6 +236,11 @@ struct fgb_batch {
     float2 *band_d;
     int4 *items_d;
     int nitems;
+    FrameTile *ft_d;      // frames on the cell-tile route
+    int4 *titems_d;       // their work items
+    int ntitems;
+    int ntile_frames;
+    bool small_r, small_q;  // every tile frame's RDF half stencil <= 64 cells, ball stencil <= 32
     uint32_t *cell_start;
     int64_t ncell_total;
     // fixed device state
@@ -254,6 +260,7 @@ struct fgb_batch {
     unsigned long long *qesc;
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
+    BatchTileLaunch tl;
     const float *graph_pts;
     cudaStream_t stream;
     cudaStream_t cap_stream;  // capture needs a stream other than the legacy default
@@ -265,7 +272,11 @@ static void free_config(fgb_batch *b, cudaStream_t s) {
     dfree(b->offset_d, s);
     dfree(b->band_d, s);
     dfree(b->items_d, s);
+    dfree(b->ft_d, s);
+    dfree(b->titems_d, s);
     dfree(b->cell_start, s);
+    b->ft_d = nullptr;
+    b->titems_d = nullptr;
     b->frames_d = nullptr;
     b->origin_d = nullptr;
     b->offset_d = nullptr;
@@ -282,8 +293,15 @@ static void drop_graph(fgb_batch *b) {
     b->graph_pts = nullptr;
 }
 
-// Builds every per-frame table for a cell division and a block size (synchronises).
-static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
+// A frame takes the cell-tile kernels when both of its stencils are on the shift route
+// with at most kTileMaxStencil cells (the RDF's half stencil) and its histogram fits a
+// warp's private copy; the others take the per-point kernel.
+constexpr int kBatchTileMaxBins = 1024;
+
+// Builds every per-frame table for a cell division, a block size of the per-point kernel
+// and the largest work item of the tile kernels (tile_cells < 0: no tile route);
+// synchronises.
+static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cudaStream_t s) {
     drop_graph(b);
     free_config(b, s);
     const int F = b->nframes;
@@ -297,6 +315,9 @@ static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
         size_t org, offq, offr, band;
     };
     std::vector<Fix> fix(F);
+    std::vector<FrameTile> tiles;
+    std::vector<int64_t> tile_lo, tile_hi;  // query cells of each tile frame
+    bool small_r = true, small_q = true;
     int64_t cell_base = 0;
     for (int f = 0; f < F; ++f) {
         BoxHost box;
@@ -353,12 +374,68 @@ static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
         d.n = (int)nf;
         d.cell_base = (uint32_t)cell_base;
         cell_base += g.ncell;
-        for (int64_t s0 = 0; s0 < nf; s0 += block)
-            items.push_back(make_int4(f, (int)(b->off[f] + s0), (int)std::min<int64_t>(block, nf - s0), 0));
+        auto cells = [](const StencilPlan &p) { return (2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1); };
+        const bool tile = tile_cells > 0 && pq.mode == 0 && pr.mode == 0 && cells(pq) <= kTileMaxStencil &&
+                          (cells(pr) + 1) / 2 <= kTileMaxStencil && b->prm.rdf_bins <= kBatchTileMaxBins;
+        if (tile) {
+            FrameTile ft;
+            memset(&ft, 0, sizeof(ft));
+            auto fill = [&](TileArgs &t, const StencilPlan &p) {
+                for (int k = 0; k < 3; ++k) {
+                    t.nc[k] = g.nc[k];
+                    t.s[k] = p.s[k];
+                    t.ts[k] = p.ts[k];
+                }
+                t.pts = b->sorted;
+                t.ncell = g.ncell;
+                t.bf = box.f;
+                t.bd = box.d;
+                t.exclude = 1;
+            };
+            fill(ft.r, pr);
+            ft.r.half = 1;
+            fill(ft.b, pq);
+            ft.b.T = ba.T;
+            ft.b.band = ba.band;
+            ft.P = d.P;
+            ft.f = f;
+            tiles.push_back(ft);
+            small_r = small_r && (cells(pr) + 1) / 2 <= 64;
+            small_q = small_q && cells(pq) <= 32;
+            // a 2D frame's points all lie in the middle one of its three z layers
+            const int64_t layer = (int64_t)g.nc[0] * g.nc[1];
+            tile_lo.push_back(box.is2d ? layer : 0);
+            tile_hi.push_back(box.is2d ? 2 * layer : g.ncell);
+        } else {
+            for (int64_t s0 = 0; s0 < nf; s0 += block)
+                items.push_back(make_int4(f, (int)(b->off[f] + s0), (int)std::min<int64_t>(block, nf - s0), 0));
+        }
+    }
+    // Tile work items: frames in order, each cut into ranges of at most tile_cells cells,
+    // shrinking toward the end of the list (about twice as many items left as resident
+    // warps) so the last items finish together.
+    std::vector<int4> titems;
+    {
+        int64_t left = 0;
+        for (size_t k = 0; k < tiles.size(); ++k) left += tile_hi[k] - tile_lo[k];
+        const int64_t w2 = 2 * (int64_t)std::max(b->tl.warps, 1);
+        for (size_t k = 0; k < tiles.size(); ++k) {
+            for (int64_t c = tile_lo[k]; c < tile_hi[k];) {
+                int64_t chunk = std::min<int64_t>((left + w2 - 1) / w2, tile_cells);
+                chunk = std::max<int64_t>(1, std::min(chunk, tile_hi[k] - c));
+                titems.push_back(make_int4((int)k, (int)c, (int)(c + chunk), 0));
+                c += chunk;
+                left -= chunk;
+            }
+        }
     }
     if (cell_base >= ((int64_t)1 << 32) - 1) return fail(FGB_ERR_CAPACITY, "too many cells over all frames");
     b->ncell_total = cell_base;
     b->nitems = (int)items.size();
+    b->ntitems = (int)titems.size();
+    b->ntile_frames = (int)tiles.size();
+    b->small_r = small_r;
+    b->small_q = small_q;
     int st = FGB_OK;
     st = st ? st : dalloc_n(&b->frames_d, F, s);
     st = st ? st : dalloc_n(&b->origin_d, std::max<size_t>(org.size(), 1), s);
@@ -366,6 +443,8 @@ static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
     st = st ? st : dalloc_n(&b->band_d, bands.size(), s);
     st = st ? st : dalloc_n(&b->items_d, std::max<size_t>(items.size(), 1), s);
     st = st ? st : dalloc_n(&b->cell_start, cell_base + 1, s);
+    st = st ? st : dalloc_n(&b->ft_d, std::max<size_t>(tiles.size(), 1), s);
+    st = st ? st : dalloc_n(&b->titems_d, std::max<size_t>(titems.size(), 1), s);
     FGB_TRY(st);
     for (int f = 0; f < F; ++f) {
         FrameDev &d = fh[f];
@@ -389,6 +468,13 @@ static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
         d.ball.esc = b->qesc;
         d.ball.err = reinterpret_cast<int *>(b->qesc + 1);
     }
+    for (FrameTile &ft : tiles) {
+        const FrameDev &d = fh[ft.f];
+        ft.r.off = b->offset_d + fix[ft.f].offr;
+        ft.b.off = b->offset_d + fix[ft.f].offq;
+        ft.r.cell_start = ft.b.cell_start = b->cell_start + d.cell_base;
+        ft.P.band = d.P.band;
+    }
     // the walks index original coordinates through the packed points, set per run
     FGB_CUDA(cudaMemcpyAsync(b->frames_d, fh.data(), sizeof(FrameDev) * F, cudaMemcpyHostToDevice, s));
     if (!org.empty())
@@ -398,9 +484,14 @@ static int configure(fgb_batch *b, int cell_div, int block, cudaStream_t s) {
     FGB_CUDA(cudaMemcpyAsync(b->band_d, bands.data(), sizeof(float2) * bands.size(), cudaMemcpyHostToDevice, s));
     if (!items.empty())
         FGB_CUDA(cudaMemcpyAsync(b->items_d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+    if (!tiles.empty())
+        FGB_CUDA(cudaMemcpyAsync(b->ft_d, tiles.data(), sizeof(FrameTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    if (!titems.empty())
+        FGB_CUDA(cudaMemcpyAsync(b->titems_d, titems.data(), sizeof(int4) * titems.size(), cudaMemcpyHostToDevice, s));
     FGB_CUDA(cudaStreamSynchronize(s));
     b->cell_div = cell_div;
     b->block = block;
+    b->tile_cells = tile_cells;
     return FGB_OK;
 }
 
@@ -487,6 +578,25 @@ static int enqueue(fgb_batch *b, const float *pts, cudaStream_t s) {
     dispatch_batch_l<MaxBlocks>(b->prm.l, b->block, smem, &per_sm);
     const int grid = std::max(1, std::min(b->nitems, num_sms() * std::max(per_sm, 1)));
     if (b->nitems > 0) dispatch_batch_l<RunBatch>(b->prm.l, a, grid, b->block, smem, s);
+    if (b->ntitems > 0) {
+        BatchTileArgs t;
+        memset(&t, 0, sizeof(t));
+        t.ft = b->ft_d;
+        t.items = b->titems_d;
+        t.nitems = b->ntitems;
+        t.ctl = b->ctl;
+        t.pts = pts;
+        t.bins = b->prm.rdf_bins;
+        t.T = b->T_d;
+        t.counts = b->counts;
+        t.esc = b->esc;
+        t.esc_cap = b->esc_cap;
+        t.q = b->q;
+        t.Q = b->Q;
+        t.nn = b->nn;
+        t.qesc = b->qesc;
+        FGB_TRY(batch_tile_run(t, b->prm.l, b->tl, b->small_r, b->small_q, s));
+    }
     {
         FGB_KSCOPE("k_batch_escalated", s);
         k_batch_escalated<<<num_sms() * 2, 256, 0, s>>>(a);
@@ -506,7 +616,7 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
         p.rdf_r_min < 0.0)
         return fail(FGB_ERR_INVALID_ARG, "invalid batch parameters");
     if (p.cell_div < 0 || p.cell_div > 2 || p.block < 0 || p.block > 512 || (p.block && p.block % 32) ||
-        p.hist_copies < 0 || p.hist_copies > 4)
+        p.hist_copies < 0 || p.hist_copies > 4 || p.tile_cells < -1 || p.tile_cells > 4096)
         return fail(FGB_ERR_INVALID_ARG, "invalid tuning parameters");
     if (frame_offsets[0] != 0) return fail(FGB_ERR_INVALID_ARG, "frame_offsets[0] must be 0");
     for (int f = 0; f < n_frames; ++f)
@@ -522,6 +632,7 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
     b->tune_div = p.cell_div == 0;
     b->tune_block = p.block == 0;
     b->tune_copies = p.hist_copies == 0;
+    b->tune_tile = p.tile_cells == 0;
     b->copies = p.hist_copies ? p.hist_copies : 2;
     b->stream = s;
     const int bins = p.rdf_bins;
@@ -548,11 +659,12 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
     st = st ? st : dalloc_n(&b->esc, b->esc_cap, s);
     st = st ? st : dalloc_n(&b->qesc, 2, s);
     if (st == FGB_OK && p.l >= 0) st = ensure_consts();
+    if (st == FGB_OK) st = batch_tile_init(std::min(bins, kBatchTileMaxBins), p.l, &b->tl);
     if (st == FGB_OK) {
         cudaMemcpyAsync(b->off_d, frame_offsets, sizeof(int64_t) * (n_frames + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(b->T_d, b->T_h.data(), sizeof(double) * (bins + 1), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(b->qesc, 0, 2 * sizeof(unsigned long long), s);
-        st = configure(b, p.cell_div ? p.cell_div : 1, p.block ? p.block : 128, s);
+        st = configure(b, p.cell_div ? p.cell_div : 1, p.block ? p.block : 128, p.tile_cells ? p.tile_cells : 64, s);
     }
     if (st != FGB_OK) {
         fgb_batch_destroy(b);
@@ -621,39 +733,48 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
     if (!b || (b->total > 0 && !points)) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = as_stream(stream);
     std::vector<int> divs = b->tune_div ? std::vector<int>{1, 2} : std::vector<int>{b->cell_div};
+    std::vector<int> tiles = b->tune_tile ? std::vector<int>{16, 64} : std::vector<int>{b->tile_cells};
     std::vector<int> blocks = b->tune_block ? std::vector<int>{64, 128, 256} : std::vector<int>{b->block};
     std::vector<int> copies = b->tune_copies ? std::vector<int>{1, 2, 4} : std::vector<int>{b->copies};
     cudaEvent_t e0, e1;
     FGB_CUDA(cudaEventCreate(&e0));
     FGB_CUDA(cudaEventCreate(&e1));
     float best = INFINITY;
-    int bd = b->cell_div, bb = b->block, bc = b->copies;
+    int bd = b->cell_div, bt = b->tile_cells, bb = b->block, bc = b->copies;
     int st = FGB_OK;
     for (int dv : divs) {
-        for (int bl : blocks) {
-            st = configure(b, dv, bl, s);
-            if (st) break;
-            for (int cp : copies) {
-                if (cp * 32 > bl) continue;
-                b->copies = cp;
-                st = enqueue(b, points, s);  // warm-up
+        for (int tc : tiles) {
+            for (int bl : blocks) {
+                st = configure(b, dv, bl, tc, s);
                 if (st) break;
-                float tot = 0.f;
-                for (int r = 0; r < 3 && st == FGB_OK; ++r) {
-                    cudaEventRecord(e0, s);
-                    st = enqueue(b, points, s);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    tot += ms;
+                // settings of a kernel with no work in this division are timed once
+                if (b->ntitems == 0 && tc != tiles[0]) break;
+                if (b->nitems == 0 && bl != blocks[0]) break;
+                for (int cp : copies) {
+                    if (cp * 32 > bl) continue;
+                    if (b->nitems == 0 && cp != copies[0]) break;
+                    b->copies = cp;
+                    st = enqueue(b, points, s);  // warm-up
+                    if (st) break;
+                    float tot = 0.f;
+                    for (int r = 0; r < 3 && st == FGB_OK; ++r) {
+                        cudaEventRecord(e0, s);
+                        st = enqueue(b, points, s);
+                        cudaEventRecord(e1, s);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tot += ms;
+                    }
+                    if (st == FGB_OK && tot < best) {
+                        best = tot;
+                        bd = dv;
+                        bt = tc;
+                        bb = bl;
+                        bc = cp;
+                    }
                 }
-                if (st == FGB_OK && tot < best) {
-                    best = tot;
-                    bd = dv;
-                    bb = bl;
-                    bc = cp;
-                }
+                if (st) break;
             }
             if (st) break;
         }
@@ -663,12 +784,13 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
     cudaEventDestroy(e1);
     FGB_TRY(st);
     b->copies = bc;
-    FGB_TRY(configure(b, bd, bb, s));
+    FGB_TRY(configure(b, bd, bb, bt, s));
     if (chosen) {
         *chosen = b->prm;
         chosen->cell_div = bd;
         chosen->block = bb;
         chosen->hist_copies = bc;
+        chosen->tile_cells = bt;
     }
     return FGB_OK;
 }
@@ -679,5 +801,12 @@ extern "C" int fgb_batch_outputs(const fgb_batch *b, const uint64_t **rdf_counts
     if (rdf_counts) *rdf_counts = reinterpret_cast<const uint64_t *>(b->counts);
     if (q) *q = b->q;
     if (n_neighbors) *n_neighbors = b->nn;
+    return FGB_OK;
+}
+
+extern "C" int fgb_batch_routes(const fgb_batch *b, int32_t *tile_frames, int32_t *point_frames) {
+    if (!b) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    if (tile_frames) *tile_frames = b->ntile_frames;
+    if (point_frames) *point_frames = b->nframes - b->ntile_frames;
     return FGB_OK;
 }

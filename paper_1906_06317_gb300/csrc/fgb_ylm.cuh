@@ -115,6 +115,27 @@ __device__ __forceinline__ void accumulate_bond(float3 d, float (&sr)[L + 1], fl
     }
 }
 
+// Y~_Lm(u) for m = 0..L of one bond (real and imaginary parts); all zero for a zero
+// displacement, which has no bond direction.
+template <int L>
+__device__ __forceinline__ void bond_harmonics(float3 d, float (&yr)[L + 1], float (&yi)[L + 1]) {
+    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    if (!(r2 > 0.f)) {
+#pragma unroll
+        for (int m = 0; m <= L; ++m) yr[m] = yi[m] = 0.f;
+        return;
+    }
+    const float inv = rsqrtf(r2);
+    float A[L + 2], wr[L + 1], wi[L + 1];
+    legendre_row<L>(d.z * inv, A);
+    powers<L>(d.x * inv, d.y * inv, wr, wi);
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        yr[m] = A[m] * wr[m];
+        yi[m] = A[m] * wi[m];
+    }
+}
+
 // Bonds met during a neighbor walk, accumulated after it (or whenever the buffer fills):
 // inside the walk only the hit branch would evaluate the harmonics, with the warp's lanes
 // that found no neighbor idle, while a separate loop keeps them in step.  Bonds are

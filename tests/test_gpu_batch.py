@@ -1,5 +1,6 @@
-"""Batched frames (one persistent launch, CUDA-graph replay, autotuner) against the
-oracle frame by frame: RDF counts bit-exact, q_l within 1e-5 * max(q, 1e-2)."""
+"""Batched frames (persistent launches, CUDA-graph replay, autotuner) against the oracle
+frame by frame: RDF counts bit-exact, q_l within 1e-5 * max(q, 1e-2), on both routes
+(cell-tile kernels and the per-point kernel)."""
 import numpy as np
 import pytest
 
@@ -38,21 +39,65 @@ def check(b, fr, refs):
     for k, (c_ref, q_ref, nn_ref) in enumerate(refs):
         assert np.array_equal(counts[k].astype(np.uint64), c_ref), f"frame {k} RDF counts"
         qk = q[off[k]:off[k + 1]]
-        assert np.all(np.abs(qk - q_ref) <= 1e-5 * np.maximum(q_ref, 1e-2)), f"frame {k} q6"
+        assert np.all(np.abs(qk - q_ref) <= 1e-5 * np.maximum(q_ref, 1e-2)), f"frame {k} q_l"
         assert np.array_equal(nn[off[k]:off[k + 1]], nn_ref)
 
 
-@pytest.mark.parametrize("cell_div,block,copies", [(1, 128, 2), (2, 64, 1), (1, 256, 4)])
-def test_batch_matches_oracle(fgb, frames, cell_div, block, copies):
+# (cell_div, block, hist_copies, tile_cells, route): tile_cells -1 puts every frame on the
+# per-point kernel; cell_div 2 makes the RDF half stencil too wide for the tile kernels;
+# tile_cells 1 gives one-cell work items
+@pytest.mark.parametrize("cell_div,block,copies,tile,route", [
+    (1, 128, 2, -1, "per_point"), (2, 64, 1, 0, "per_point"), (1, 256, 4, 0, "tile"), (1, 128, 2, 1, "tile")])
+def test_batch_matches_oracle(fgb, frames, cell_div, block, copies, tile, route):
     fr, refs = frames
     P = W.C5_PARAMS
     pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
     b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
                   rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"], cell_div=cell_div, block=block,
-                  hist_copies=copies)
+                  hist_copies=copies, tile_cells=tile)
+    assert b.routes()[route] == len(fr)
     b.run(pts)
     torch.cuda.synchronize()
     check(b, fr, refs)
+
+
+def test_batch_routes_agree(fgb, frames):
+    # the same frames on both routes: identical RDF and neighbor counts, q_l to rounding
+    fr, _ = frames
+    P = W.C5_PARAMS
+    pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
+    out = []
+    for tile in (-1, 64):
+        b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
+                      rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"], cell_div=1, tile_cells=tile)
+        b.run(pts)
+        torch.cuda.synchronize()
+        out.append([t.cpu().numpy() for t in b.outputs()])
+    (c0, q0, n0), (c1, q1, n1) = out
+    assert np.array_equal(c0, c1) and np.array_equal(n0, n1)
+    assert np.all(np.abs(q0 - q1) <= 1e-5 * np.maximum(np.abs(q0), 1e-2))
+
+
+@pytest.mark.parametrize("l", [4, 12])
+def test_batch_crowded_cells(fgb, l):
+    # about 40 points per cell (several query passes per cell in the tile kernels), one
+    # cubic and one triclinic frame, l with two partial sums (4) and with one (12)
+    rng = np.random.default_rng(21 + l)
+    boxes = [W.Box.cube(8.0), W.Box(8.2, 8.0, 8.4, 0.1, -0.05, 0.08)]
+    xs = [W.uniform_points(rng, boxes[0], 5000), W.uniform_points(rng, boxes[1], 5400)]
+    P = W.C5_PARAMS
+    refs = []
+    for box, x in zip(boxes, xs):
+        counts = oracle.rdf_counts(box, x, P["rdf_bins"], P["rdf_r_max"])
+        _, off, pj, _ = oracle.ball_query(box, x, P["r_max"])
+        refs.append((counts, oracle.steinhardt(box, x, off, pj, l), np.diff(off)))
+    pts = torch.from_numpy(np.concatenate(xs)).cuda()
+    b = fgb.Batch([len(x) for x in xs], boxes, r_max=P["r_max"], l=l, rdf_bins=P["rdf_bins"],
+                  rdf_r_max=P["rdf_r_max"], cell_div=1)
+    assert b.routes()["tile"] == 2
+    b.run(pts)
+    torch.cuda.synchronize()
+    check(b, None, refs)
 
 
 def test_batch_graph_replay_and_tune(fgb, frames):
@@ -62,7 +107,7 @@ def test_batch_graph_replay_and_tune(fgb, frames):
     b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
                   rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"])
     chosen = b.tune(pts)
-    assert chosen["cell_div"] in (1, 2) and chosen["block"] in (64, 128, 256)
+    assert chosen["cell_div"] in (1, 2) and chosen["block"] in (64, 128, 256) and chosen["tile_cells"] in (16, 64)
     for _ in range(3):
         b.run(pts, graph=True)
     torch.cuda.synchronize()
