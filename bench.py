@@ -604,6 +604,12 @@ def batch_extras(fgb, torch, dev, stream, flush):
                   rdf_r_max=P["rdf_r_max"])
     tuned = b.tune(pts)
     t_graph = timed(lambda: b.run(pts, graph=True), stream, flush)
+    routes = b.routes()
+    # the same frames with every frame on the per-point kernel (its tuned settings)
+    bp = fgb.Batch(sizes, [f.box for f in frames], r_max=P["r_max"], l=P["l"], rdf_bins=P["rdf_bins"],
+                   rdf_r_max=P["rdf_r_max"], cell_div=1, block=256, hist_copies=1, tile_cells=-1)
+    t_point = timed(lambda: bp.run(pts, graph=True), stream, flush)
+    del bp
     xs = [torch.from_numpy(f.points).to(dev) for f in frames]
     rdf = fgb.RDF(P["rdf_bins"], P["rdf_r_max"])
     st = fgb.Steinhardt(P["l"])
@@ -617,7 +623,8 @@ def batch_extras(fgb, torch, dev, stream, flush):
     t_loop = timed(loop, stream, flush, reps=3, warm=1)
     return {"c5_frames": len(frames), "c5_points": int(sum(sizes)), "c5_batched_graph_ms": t_graph,
             "c5_frames_per_s_batched": len(frames) / (t_graph * 1e-3), "c5_per_frame_loop_ms": t_loop,
-            "c5_frames_per_s_per_frame_loop": len(frames) / (t_loop * 1e-3), "c5_tuned": tuned}
+            "c5_frames_per_s_per_frame_loop": len(frames) / (t_loop * 1e-3), "c5_tuned": tuned,
+            "c5_routes": routes, "c5_per_point_route_graph_ms": t_point}
 
 
 if __name__ == "__main__":
