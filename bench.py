@@ -200,9 +200,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=4_194_304,
                     help="points of the uniform workload (smaller cases are for profiling only)")
-    ap.add_argument("--only", choices=["pmft"], default=None,
+    ap.add_argument("--only", choices=["pmft", "batch"], default=None,
                     help="time one group of components alone and print them (profiling runs)")
     ap.add_argument("--pmft-points", type=int, default=4_194_304, help="points of the large 2D PMFT frame")
+    ap.add_argument("--batch-frames", type=int, default=256, help="--only batch: the first frames of the c5 set")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -216,6 +217,13 @@ def main():
         dev = torch.device("cuda", local)
         flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
         comp = pmft_components(fgb, torch, dev, torch.cuda.current_stream(), flush, n_big=args.pmft_points)
+        print(json.dumps({"components": comp}), flush=True)
+        return
+    if args.only == "batch":
+        dev = torch.device("cuda", local)
+        flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+        comp = batch_only(fgb, torch, dev, torch.cuda.current_stream(), flush, args.batch_frames, args.steps,
+                          args.warmup)
         print(json.dumps({"components": comp}), flush=True)
         return
     dist = None
@@ -383,6 +391,22 @@ def timed(fn, stream, flush, reps=5, warm=2):
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
     return statistics.median(out)
+
+
+def batch_only(fgb, torch, dev, stream, flush, n_frames, steps, warmup):
+    """The c5 frames [0, n_frames) in one batch at fixed settings (cell size r_max, tile
+    items of up to 64 cells), `warmup` then `steps` plain runs (no graph, no tuning): the
+    command behind the batch kernels' launch lists and captures."""
+    frames = W.c5()[:n_frames]
+    P = W.C5_PARAMS
+    sizes = [len(f.points) for f in frames]
+    pts = torch.from_numpy(np.concatenate([f.points for f in frames])).to(dev)
+    b = fgb.Batch(sizes, [f.box for f in frames], r_max=P["r_max"], l=P["l"], rdf_bins=P["rdf_bins"],
+                  rdf_r_max=P["rdf_r_max"], cell_div=1, block=128, hist_copies=2, tile_cells=64)
+    for _ in range(warmup):
+        b.run(pts)
+    ms = timed(lambda: b.run(pts), stream, flush, reps=max(steps, 1), warm=0)
+    return {"batch_frames": len(frames), "batch_points": int(sum(sizes)), "batch_ms": ms, "routes": b.routes()}
 
 
 def pmft_components(fgb, torch, dev, stream, flush, n_big=4_194_304):

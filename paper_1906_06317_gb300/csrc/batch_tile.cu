@@ -94,11 +94,10 @@ __device__ __noinline__ void bt_rdf_slow(const BatchTileArgs *ap, const FrameTil
     if (be >= 0) atomicAdd(a.counts + (int64_t)fr->f * a.bins + be, 2ull);
 }
 
-// One candidate per lane against the queries [0, nq) of the pass.  CENTER: the candidate
-// may be one of the cell's own points, valid only against queries before it (tl < lim).
-// The fast test is the single-frame one: bin floor(x) when x = (r - r_min)/Delta is
-// further than the error bound from both edges.
-template <bool CENTER>
+// One candidate per lane against the queries [0, nq) of the pass, valid only for
+// queries tl < lim (a point of the cell itself pairs only with earlier queries; other
+// candidates carry no limit).  The fast test is the single-frame one: bin floor(x) when
+// x = (r - r_min)/Delta is further than the error bound from both edges.
 __device__ __forceinline__ void bt_rdf_rounds(const BatchTileArgs &a, const FrameTile &fr, const float4 *qs, int nq,
                                               float cx, float cy, float cz, int cj, int lim, uint32_t *h) {
     const BinParams &P = fr.P;
@@ -108,9 +107,7 @@ __device__ __forceinline__ void bt_rdf_rounds(const BatchTileArgs &a, const Fram
     for (int tl = 0; tl < nq; ++tl) {
         const float4 q = qs[tl];
         const float r2 = r2_f32(cx - q.x, cy - q.y, cz - q.z);
-        bool in = r2 < rhi && r2 >= rlo;
-        if (CENTER) in = in && tl < lim;
-        if (in) {
+        if (r2 < rhi && r2 >= rlo && tl < lim) {
             const float inv = rsqrt_ftz(r2);
             const float x = fmaf(r2 * inv, invd, -rmid);
             const float fb = floorf(x);
@@ -133,9 +130,12 @@ __device__ __forceinline__ void bt_guard(const BatchTileArgs &a, const FrameTile
     tests += 32u * (unsigned)nq;
 }
 
+// The candidates of the cell's half stencil (its own points first) are packed into full
+// chunks of 32, dropping those out of reach of the pass's bounding box; the cell's own
+// points carry their limit (k - qb) in `lim`.
 template <int NS>
 __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameTile &fr, int A, TileStencilT<NS> &ts,
-                                            float4 *qs, float4 *buf, uint32_t *h, uint64_t &tests) {
+                                            float4 *qs, float4 *buf, int *lim, uint32_t *h, uint64_t &tests) {
     const TileArgs &t = fr.r;
     const int lane = threadIdx.x & 31;
     const int begA = (int)__ldg(t.cell_start + A);
@@ -159,30 +159,30 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
             const float4 q = qs[lane < nq ? lane : 0];
             warp_box(q.x, q.y, q.z, lane < nq, blo, bhi);
         }
-        // the cell's own points first (they pair only with earlier queries)
-        for (int base = 0; base < nA; base += 32) {
-            bt_guard(a, fr, h, tests, nq);
-            const int k = base + lane;
-            const TileCand c = tile_load(t, ts, n, nA, k);
-            bt_rdf_rounds<true>(a, fr, qs, nq, c.x, c.y, c.z, c.j, k < nA ? k - qb : 0, h);
-        }
-        // the other cells: candidates in reach of the pass, packed into full chunks
         int cnt = 0;
-        for (int base = nA; base < total; base += 32) {
+        for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
             const TileCand c = tile_load(t, ts, n, total, k);
-            const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+            const bool keep = k < total && (k < nA || box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2);
             const unsigned m = __ballot_sync(kFull, keep);
-            if (keep) buf[cnt + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+            if (keep) {
+                const int slot = cnt + __popc(m & lt);
+                buf[slot] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+                lim[slot] = k < nA ? k - qb : 0x7fffffff;
+            }
             cnt += __popc(m);
             if (cnt >= 32) {
                 __syncwarp();
                 bt_guard(a, fr, h, tests, nq);
                 const float4 e = buf[lane];
-                bt_rdf_rounds<false>(a, fr, qs, nq, e.x, e.y, e.z, __float_as_int(e.w), 0, h);
+                bt_rdf_rounds(a, fr, qs, nq, e.x, e.y, e.z, __float_as_int(e.w), lim[lane], h);
                 const float4 rest = buf[32 + lane];
+                const int rl = lim[32 + lane];
                 __syncwarp();
-                if (lane < cnt - 32) buf[lane] = rest;
+                if (lane < cnt - 32) {
+                    buf[lane] = rest;
+                    lim[lane] = rl;
+                }
                 __syncwarp();
                 cnt -= 32;
             }
@@ -191,7 +191,7 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
             __syncwarp();
             bt_guard(a, fr, h, tests, nq);
             const float4 e = lane < cnt ? buf[lane] : make_float4(kFar, kFar, kFar, __int_as_float(-1));
-            bt_rdf_rounds<false>(a, fr, qs, nq, e.x, e.y, e.z, __float_as_int(e.w), 0, h);
+            bt_rdf_rounds(a, fr, qs, nq, e.x, e.y, e.z, __float_as_int(e.w), lane < cnt ? lim[lane] : 0, h);
         }
     }
 }
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
     __shared__ TileStencilT<NS> sts[kBtW];
     __shared__ float4 sq[kBtW][32];
     __shared__ float4 sbuf[kBtW][64];  // kept candidates
+    __shared__ int slim[kBtW][64];     // their query limits
     extern __shared__ uint32_t shist[];  // kBtW * bins
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *h = shist + warp * a.bins;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
             bt_load_frame(a.ft + w.x, &fr);
             cur = w.x;
         }
-        for (int c = w.y; c < w.z; ++c) bt_rdf_cell<NS>(a, fr, c, sts[warp], sq[warp], sbuf[warp], h, tests);
+        for (int c = w.y; c < w.z; ++c) bt_rdf_cell<NS>(a, fr, c, sts[warp], sq[warp], sbuf[warp], slim[warp], h, tests);
     }
     if (cur >= 0) bt_flush(h, a.bins, a.counts + (int64_t)fr.f * a.bins);
 }
