@@ -2,14 +2,16 @@
 // trajectory listings): per-frame RDF counts and per-particle q_l.
 //
 // All frames are binned by one kernel into one global cell array (frame f owns cells
-// cell_base[f] .. cell_base[f+1]), sorted by one radix sort, and analysed by one
-// persistent kernel: blocks take work items (a frame and up to `block` consecutive
-// sorted points) from an atomic counter, stage that frame's description in shared
-// memory, and for every point walk (1) the RDF half stencil into a shared histogram that
-// is flushed when the block moves to another frame, and (2) the ball-query stencil into
-// the spherical-harmonic accumulators.  Every buffer is allocated at create time, so a
-// run is a fixed launch sequence with no host synchronisation; fgb_batch_run_graph
-// captures it once in a CUDA graph and replays it.
+// cell_base[f] .. cell_base[f+1]) and sorted by one radix sort.  Frames whose RDF half
+// stencil and ball stencil are on the fixed-offset route take the cell-tile kernels of
+// batch_tile.cu (a warp per query cell).  The others take the persistent per-point
+// kernel here: blocks take work items (a frame and up to `block` consecutive sorted
+// points) from an atomic counter, stage that frame's description in shared memory, and
+// for every point walk (1) the RDF half stencil into a shared histogram that is flushed
+// when the block moves to another frame, and (2) the ball-query stencil into the
+// spherical-harmonic accumulators.  Every buffer is allocated at create time, so a run
+// is a fixed launch sequence with no host synchronisation; fgb_batch_run_graph captures
+// it once in a CUDA graph and replays it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
