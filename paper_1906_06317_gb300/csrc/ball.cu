@@ -135,6 +135,36 @@ __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *_
     }
 }
 
+// Write pass for long rows (thread per query): each query appends its neighbors to its
+// segment in walk order (bounded by its count), and sort_segments then sorts every row
+// by point index with a warp per row.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_ball_write_rows(BallArgs a, const int64_t *__restrict__ seg,
+                                                         const uint32_t *__restrict__ counts,
+                                                         int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                         float *__restrict__ d_out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nq) return;
+    const float4 q = a.qs[t];
+    const int i = __float_as_int(q.w);
+    const int64_t off = seg[i];
+    const uint32_t want = counts[i];
+    const float xi0 = __ldg(a.q_orig + 3 * (int64_t)i), xi1 = __ldg(a.q_orig + 3 * (int64_t)i + 1),
+                xi2 = __ldg(a.q_orig + 3 * (int64_t)i + 2);
+    uint32_t n = 0;
+    ball_visit_m<MODE>(a, q, a.qcell[t], i, [&](int j, float3, float, double) {
+        if (n < want) {
+            const float3 d = bond_f32v(a.bf, xi0, xi1, xi2, __ldg(a.p_orig + 3 * (int64_t)j),
+                                       __ldg(a.p_orig + 3 * (int64_t)j + 1), __ldg(a.p_orig + 3 * (int64_t)j + 2));
+            qi_out[off + n] = i;
+            pj_out[off + n] = j;
+            d_out[off + n] = sqrtf(r2_f32(d.x, d.y, d.z));
+        }
+        ++n;
+    });
+    if (n != want) atomicExch(a.err, 2);
+}
+
 // Write pass for very large neighbor counts: insertion straight into the output arrays.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_ball_write_global(BallArgs a, const int64_t *__restrict__ seg,
@@ -261,6 +291,18 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
             st = tile_write_global(nq, plan, R, a.exclude, a.err, nl->segments, counts, nl->qi, nl->pj, nl->dist, s);
             st = st ? st
                     : sort_segments(nl->segments, nqq, cap, nq->n, nl->qi, nl->pj, nl->dist, s);
+        } else if (cap > 64 && cap <= 16384) {
+            // long rows: written in walk order, then sorted per row (a rank sort of each
+            // row by one warp costs O(row^2) and held c1's 268-entry rows to 128 warps)
+            const unsigned g2 = (unsigned)((nqq + 127) / 128);
+            {
+                FGB_KSCOPE("k_ball_write_rows", s);
+                if (a.S.mode == 0)
+                    k_ball_write_rows<0><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+                else
+                    k_ball_write_rows<1><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+            }
+            st = sort_segments(nl->segments, nqq, cap, nq->n, nl->qi, nl->pj, nl->dist, s);
         } else {
         int block = 128;
         while (block > 32 && (size_t)cap * (block + 1) * sizeof(uint32_t) > 100 * 1024) block >>= 1;
