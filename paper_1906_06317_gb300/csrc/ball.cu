@@ -135,6 +135,112 @@ __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *_
     }
 }
 
+// ------------------------------------------------------------------ split queries
+//
+// Few queries (a small grid): G consecutive lanes share one query, lane g taking the
+// candidates beg + g, beg + g + G, ... of every stencil cell (coalesced across the
+// group), so the GPU holds G times as many warps.  Pairs are decided exactly as in the
+// single-lane walks.
+
+constexpr int kSplitG = 8;
+
+template <int MODE, bool CHECKJ, class F>
+__device__ __forceinline__ void split_walk(const BallArgs &a, float4 q, uint32_t qc, int i, int g, F &&fn) {
+    int cx, cy, cz;
+    cell_coords(qc, a.S.nc, cx, cy, cz);
+    const int excl = a.exclude ? i : -1;
+    const float lo = a.band.lo, hi = a.band.hi;
+    for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), false,
+                [&](int cell, float qx, float qy, float qz, bool) {
+                    const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
+                    for (uint32_t p = beg + (uint32_t)g; p < end; p += kSplitG) {
+                        const float4 c = __ldg(a.pts + p);
+                        const float3 d = cand_disp_m<MODE>(a.bf, c, qx, qy, qz);
+                        const float r2 = r2_f32(d.x, d.y, d.z);
+                        if (r2 < hi) {
+                            const int j = __float_as_int(c.w);
+                            if (j == excl) continue;
+                            if (r2 < lo)
+                                fn(j, 0);
+                            else if (exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j) < a.T)
+                                fn(j, 1);
+                            else
+                                fn(-1, 1);
+                        }
+                    }
+                });
+}
+
+// Neighbor count of every query (kSplitG lanes per query).
+template <int MODE>
+__global__ void __launch_bounds__(128) k_ball_count_split(BallArgs a, uint32_t *__restrict__ counts) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t qx = t / kSplitG;
+    const int g = (int)(t % kSplitG);
+    const bool act = qx < a.nq;
+    uint32_t cnt = 0;
+    int nesc = 0, i = -1;
+    if (act) {
+        const float4 q = a.qs[qx];
+        i = __float_as_int(q.w);
+        split_walk<MODE, true>(a, q, a.qcell[qx], i, g, [&](int j, int esc) {
+            nesc += esc;
+            cnt += j >= 0 ? 1u : 0u;
+        });
+    }
+#pragma unroll
+    for (int o = kSplitG / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (act && g == 0) counts[i] = cnt;
+    if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
+}
+
+// Rows of every query (kSplitG lanes per query), unsorted: each lane counts its share,
+// takes its offset in the row from an exclusive scan over the group, and writes its
+// neighbors there (bounded by the row's count); sort_segments sorts the rows.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_ball_write_split(BallArgs a, const int64_t *__restrict__ seg,
+                                                          const uint32_t *__restrict__ counts,
+                                                          int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                          float *__restrict__ d_out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t qx = t / kSplitG;
+    const int g = (int)(t % kSplitG);
+    const bool act = qx < a.nq;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t qc = 0, mine = 0;
+    int i = -1;
+    if (act) {
+        q = a.qs[qx];
+        qc = a.qcell[qx];
+        i = __float_as_int(q.w);
+        split_walk<MODE, true>(a, q, qc, i, g, [&](int j, int) { mine += j >= 0 ? 1u : 0u; });
+    }
+    uint32_t inc = mine;
+#pragma unroll
+    for (int d = 1; d < kSplitG; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, d);
+        if (g >= d) inc += u;
+    }
+    if (!act) return;
+    const int64_t off = seg[i];
+    const uint32_t want = counts[i];
+    if (g == kSplitG - 1 && inc != want) atomicExch(a.err, 2);
+    const float xi0 = __ldg(a.q_orig + 3 * (int64_t)i), xi1 = __ldg(a.q_orig + 3 * (int64_t)i + 1),
+                xi2 = __ldg(a.q_orig + 3 * (int64_t)i + 2);
+    uint32_t n = inc - mine;
+    split_walk<MODE, true>(a, q, qc, i, g, [&](int j, int) {
+        if (j < 0) return;
+        if (n < want) {
+            const float3 d = bond_f32v(a.bf, xi0, xi1, xi2, __ldg(a.p_orig + 3 * (int64_t)j),
+                                       __ldg(a.p_orig + 3 * (int64_t)j + 1), __ldg(a.p_orig + 3 * (int64_t)j + 2));
+            qi_out[off + n] = i;
+            pj_out[off + n] = j;
+            d_out[off + n] = sqrtf(r2_f32(d.x, d.y, d.z));
+        }
+        ++n;
+    });
+}
+
 // Write pass for long rows (thread per query): each query appends its neighbors to its
 // segment in walk order (bounded by its count), and sort_segments then sorts every row
 // by point index with a warp per row.
@@ -244,6 +350,8 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
     const bool checkj = !Q.self && a.exclude;
     const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && !force_thread_kernels();
+    // few queries: several lanes per query (the single-lane kernels would leave most SMs idle)
+    const bool split = !tile && nqq < (int64_t)num_sms() * 128;
     if (st == FGB_OK && nqq > 0 && tile) {
         // 2D: the tile kernels walk only the points' layer; a point off the plane keeps a
         // count of zero instead of an unwritten one
@@ -251,6 +359,16 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
             st = fail(FGB_ERR_CUDA, "memset failed");
         st = st ? st : tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
         st = st ? st : scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
+    } else if (st == FGB_OK && nqq > 0 && split) {
+        {
+            FGB_KSCOPE("k_ball_count_split", s);
+            const unsigned g2 = (unsigned)((nqq * kSplitG + 127) / 128);
+            if (a.S.mode == 0)
+                k_ball_count_split<0><<<g2, 128, 0, s>>>(a, counts);
+            else
+                k_ball_count_split<1><<<g2, 128, 0, s>>>(a, counts);
+        }
+        st = scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK && nqq > 0) {
         const unsigned grid = (unsigned)((nqq + 127) / 128);
         {
@@ -291,12 +409,19 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
             st = tile_write_global(nq, plan, R, a.exclude, a.err, nl->segments, counts, nl->qi, nl->pj, nl->dist, s);
             st = st ? st
                     : sort_segments(nl->segments, nqq, cap, nq->n, nl->qi, nl->pj, nl->dist, s);
-        } else if (cap > 64 && cap <= 16384) {
-            // long rows: written in walk order, then sorted per row (a rank sort of each
+        } else if (cap <= 16384 && (split || cap > 64)) {
+            // rows written unsorted, then sorted per row by a warp (a rank sort of each
             // row by one warp costs O(row^2) and held c1's 268-entry rows to 128 warps)
-            const unsigned g2 = (unsigned)((nqq + 127) / 128);
-            {
+            if (split) {
+                FGB_KSCOPE("k_ball_write_split", s);
+                const unsigned g2 = (unsigned)((nqq * kSplitG + 127) / 128);
+                if (a.S.mode == 0)
+                    k_ball_write_split<0><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+                else
+                    k_ball_write_split<1><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+            } else {
                 FGB_KSCOPE("k_ball_write_rows", s);
+                const unsigned g2 = (unsigned)((nqq + 127) / 128);
                 if (a.S.mode == 0)
                     k_ball_write_rows<0><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
                 else
