@@ -69,6 +69,17 @@ def test_host_side_argument_checks(lib):
     assert lib.fgb_pmftxy_result(h, c.ctypes.data, g.ctypes.data, f.ctypes.data, None) == 0
     assert not c.any() and not g.any() and np.all(np.isinf(f))
     lib.fgb_pmftxy_destroy(h)
+    # batched frames: tuning parameters are checked before any device work
+    off = np.array([0, 10], np.int64)
+    boxes = (fgb.fgb_box * 1)(fgb.fgb_box(10.0, 10.0, 10.0, 0, 0, 0))
+    for bad in (dict(tile_cells=-2), dict(tile_cells=5000), dict(cell_div=3), dict(block=48),
+                dict(hist_copies=5)):
+        prm = fgb.fgb_batch_params(1.5, 6, 200, 3.0, 0.0, bad.get("cell_div", 0), bad.get("block", 0),
+                                   bad.get("hist_copies", 0), bad.get("tile_cells", 0))
+        assert lib.fgb_batch_create(1, off.ctypes.data, boxes, ctypes.byref(prm), None,
+                                    ctypes.byref(h)) == fgb.ERR_INVALID_ARG, bad
+        assert b"tuning" in lib.fgb_last_error()
+    assert lib.fgb_batch_routes(None, None, None) == fgb.ERR_INVALID_ARG
 
 
 def test_product_path_never_imports_the_oracle():
