@@ -145,3 +145,37 @@ def test_batch_mixes_2d_and_3d_frames(fgb):
     b.run(pts)
     torch.cuda.synchronize()
     check(b, None, refs)
+
+
+def test_full_c5_batch_sampled(fgb):
+    # the 256-frame workload in the bench's launch configuration (autotuned, graph
+    # replay); the smallest, median and largest frames and two more against the oracle,
+    # and for every frame the symmetry of a self query: an even total of ordered RDF
+    # pairs and of neighbor counts
+    fr = W.c5()
+    P = W.C5_PARAMS
+    sizes = np.array([len(f.points) for f in fr])
+    pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
+    b = fgb.Batch(sizes.tolist(), [f.box for f in fr], r_max=P["r_max"], l=P["l"], rdf_bins=P["rdf_bins"],
+                  rdf_r_max=P["rdf_r_max"])
+    b.tune(pts)
+    b.run(pts, graph=True)
+    b.run(pts, graph=True)
+    torch.cuda.synchronize()
+    counts, q, nn = (t.cpu().numpy() for t in b.outputs())
+    off = b.offsets
+    order = np.argsort(sizes, kind="stable")
+    rng = np.random.default_rng(55)
+    picks = sorted({int(order[0]), int(order[len(order) // 2]), int(order[-1]),
+                    *rng.choice(len(fr), 2, replace=False).tolist()})
+    for k in picks:
+        f = fr[k]
+        c_ref = oracle.rdf_counts(f.box, f.points, P["rdf_bins"], P["rdf_r_max"])
+        _, o, pj, _ = oracle.ball_query(f.box, f.points, P["r_max"])
+        q_ref = oracle.steinhardt(f.box, f.points, o, pj, P["l"])
+        assert np.array_equal(counts[k].astype(np.uint64), c_ref), f"frame {k} RDF counts"
+        qk = q[off[k]:off[k + 1]]
+        assert np.all(np.abs(qk - q_ref) <= 1e-5 * np.maximum(q_ref, 1e-2)), f"frame {k} q_l"
+        assert np.array_equal(nn[off[k]:off[k + 1]], np.diff(o)), f"frame {k} neighbor counts"
+    for k in range(len(fr)):
+        assert int(counts[k].sum()) % 2 == 0 and int(nn[off[k]:off[k + 1]].sum()) % 2 == 0, f"frame {k}"
