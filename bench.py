@@ -5,7 +5,10 @@ Workload (one step): N = 4,194,304 uniform points in a cubic box at density 0.85
 synthetic, shaped like the paper's random-point benchmarks); build the cell list; ball
 query r_max = 2.5 producing the full sorted NeighborList (~2.33e8 pairs); fused RDF of
 500 bins on [0, 5] (~1.87e9 ordered pairs, never stored).  value = neighbor pairs
-handled per second = (NeighborList pairs + RDF pairs) / step time, summed over ranks.
+handled per second = (NeighborList pairs + RDF pairs) / step time.  Under torchrun the
+ranks split that one frame by ranges of query cells (each holds every point, writes the
+rows of its own queries and histograms its own pairs; the counts and the histogram are
+summed over NCCL), so the value is the frame's pairs over the slowest rank's time.
 
 Timing: W untimed warm-up steps; K timed steps, each bracketed by CUDA events on the
 launching stream; L2 is flushed (a 512 MB write) before every step outside the events;
@@ -43,8 +46,9 @@ def env_rank():
 
 
 def frame_seed(rank: int) -> int:
-    """Each rank analyses its own independent frame of the workload (weak scaling)."""
-    return 3 + rank
+    """The c3 frame's seed.  Under torchrun every rank holds the same frame and walks its
+    own range of the query cells (strong scaling over one frame)."""
+    return 3
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -58,8 +62,15 @@ def max_over_ranks(x: float, dist=None, device="cpu") -> float:
 
 
 def weak_value(units_per_rank: int, world: int, step_ms: float) -> float:
-    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    """Whole-job throughput when every rank processes its own units: all ranks' units over
+    the slowest rank's time."""
     return units_per_rank * world / (step_ms * 1e-3)
+
+
+def strong_value(units: int, step_ms: float) -> float:
+    """Whole-job throughput when the ranks split one frame: its units over the slowest
+    rank's time."""
+    return units / (step_ms * 1e-3)
 
 
 class ClockSampler:
@@ -130,6 +141,29 @@ def measured_traffic(kernel: str, n: int):
     return nbytes * n / n0 if cur.startswith(sha) else None
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), architecture and cores."""
+    import platform
+    fields = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            fields.setdefault(k.strip(), v.strip())
+    except (OSError, subprocess.SubprocessError):
+        pass
+    name = fields.get("Model name") or fields.get("Vendor ID") or ""
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()}, {os.cpu_count()} logical cores)"
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -178,7 +212,7 @@ def run_reference(args, rank, world):
     sample = f"queries [0, {ORACLE_SAMPLE}) of {len(w.points)} (ball r=2.5 + RDF 500 bins [0,5]); cell builds charged pro rata"
     line = {"impl": "reference", "metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": v,
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "c3: cubic rho=0.85, N=4194304 uniform, ball r=2.5 NL + RDF 500 bins [0,5]",
                        "oracle_sample": sample},
@@ -240,8 +274,17 @@ def main():
     rdf = fgb.RDF(p["rdf_bins"], p["rdf_r_max"])
     stream = torch.cuda.current_stream()
 
+    if world > 1:
+        from paper_1906_06317_gb300 import shard
+
     def step(x):
         nq = fgb.NeighborQuery(w.box, x, r_cell=p["r_max"])
+        if world > 1:
+            # one frame split across the ranks by ranges of query cells; the counts and
+            # the histogram are summed over NCCL
+            nl = shard.sharded_ball_query(nq, p["r_max"], rank, world, all_reduce=dist.all_reduce)
+            shard.sharded_rdf(rdf, nq, rank, world, all_reduce=dist.all_reduce)
+            return nl
         nl = nq.query(None, dict(r_max=p["r_max"], exclude_ii=True)).toNeighborList()
         rdf.compute(nq, reset=True)
         return nl
@@ -249,8 +292,10 @@ def main():
     for _ in range(max(3, args.warmup)):
         nl = step(pts)
     torch.cuda.synchronize()
-    nl_pairs = nl.n_pairs
+    nl_pairs = int(nl.global_segments[-1]) if world > 1 else nl.n_pairs
+    nl_esc = 0 if world > 1 else nl.escalations
     rdf_pairs = int(rdf.bin_counts.sum())
+    rdf_esc = rdf.escalations()
     units = nl_pairs + rdf_pairs
     del nl
 
@@ -282,14 +327,19 @@ def main():
     fgb.timing_enable(False)
     kern = {}
     for name in ("k_bin", "k_radix_hist", "k_radix_scatter", "k_cell_start", "k_ball_count", "k_ball_write",
-                 "k_ball_write_global", "k_tile_count", "k_tile_write", "k_rdf_tile", "k_reduce", "k_top", "k_down",
-                 "k_rdf", "k_rdf_escalated", "k_offset_table", "k_origin_tables", "k_band"):
+                 "k_ball_write_global", "k_tile_count", "k_tile_write", "k_nl_count", "k_nl_count_scatter",
+                 "k_nl_write", "k_nl_fill_qi", "k_tile_write_listed", "k_tile_write_global_listed",
+                 "k_sort_segments", "k_rdf_tile", "k_reduce", "k_top", "k_down", "k_rdf", "k_rdf_escalated",
+                 "k_offset_table", "k_origin_tables", "k_band"):
         t, n = fgb.timing_read(name)
         if n:
             kern[name] = {"ms_per_step": t / args.steps, "launches_per_step": n / args.steps}
     step_ms = sum(ms) / len(ms)
+    # FP64 decisions inside the FP32 bands, per pair (one step's list and histogram)
+    esc = {"nl_fp64_decisions": int(nl_esc), "nl_fraction_of_pairs": nl_esc / max(nl_pairs, 1),
+           "rdf_fp64_decisions": int(rdf_esc), "rdf_fraction_of_unordered_pairs": rdf_esc / max(rdf_pairs / 2, 1)}
     step_ms_max = max_over_ranks(step_ms, dist, dev)
-    value = weak_value(units, world, step_ms_max)
+    value = strong_value(units, step_ms_max)
 
     # ---------------- end to end through the public API, host buffers
     e2e_ms = []
@@ -301,7 +351,7 @@ def main():
         x = host.to(dev, non_blocking=True)
         nl = step(x)
         counts = rdf.bin_counts           # D2H of the step's result (synchronises)
-        got = int(counts.sum()) + nl.n_pairs
+        got = int(counts.sum()) + (int(nl.global_segments[-1]) if world > 1 else nl.n_pairs)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
@@ -316,16 +366,22 @@ def main():
     n = len(w.points)
     dominant = max(kern, key=lambda k: kern[k]["ms_per_step"])
     sm_clock = (clk or {}).get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12   # FP32 lane-instructions per second, T/s
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sms * 128 * sm_clock * 1e6 / 1e12   # FP32 lane-instructions per second, T/s
     rdf_unordered = rdf_pairs / 2
     nl_bytes = (12.0 * nl_pairs + 28.0 * n) / 1e9    # 12 B per stored pair; record, count, offset per query
     cnt_bytes = 20.0 * n / 1e9                        # sorted record read + count write per query
+    nlw_bytes = (8.0 * nl_pairs + 28.0 * n) / 1e9    # point index + distance per pair; record, count, offset per query
+    qi_bytes = (4.0 * nl_pairs + 8.0 * n) / 1e9      # query index per pair; offset per query
     rdf_ops = 10.0 * rdf_unordered / 1e12             # ~10 FP32 operations per unordered pair inside r_max
     roofs = {
         "k_ball_write": ("hbm", nl_bytes, "GB/s", hbm),
         "k_tile_write": ("hbm", nl_bytes, "GB/s", hbm),
         "k_ball_count": ("hbm", cnt_bytes, "GB/s", hbm),
         "k_tile_count": ("hbm", cnt_bytes, "GB/s", hbm),
+        "k_nl_write": ("hbm", nlw_bytes, "GB/s", hbm),
+        "k_nl_fill_qi": ("hbm", qi_bytes, "GB/s", hbm),
+        "k_nl_count": ("hbm", cnt_bytes, "GB/s", hbm),
         "k_rdf": ("alu", rdf_ops, "TOP/s", alu_peak),
         "k_rdf_tile": ("alu", rdf_ops, "TOP/s", alu_peak),
     }
@@ -336,7 +392,7 @@ def main():
                 "unit": unit, "frac": achieved / peak, "traffic": measured_traffic(dominant, n),
                 "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 2,097,152 points)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if bound == "hbm"
-                else f"derived: 152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
+                else f"derived: {n_sms} SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
     others = {}
     for k, (b, wk, u, pk) in roofs.items():
         if k in kern:
@@ -354,22 +410,27 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads)
-        cpu = {"value": r, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        r1, pairs1, t1 = oracle_rate(w, ORACLE_SAMPLE // 16, 1)
+        cpu = {"value": r, "unit": "pairs/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"queries [0, {ORACLE_SAMPLE}) of {n}: {pairs} pairs in {t:.1f} s "
-                         "(cell builds charged pro rata)"}
+                         "(cell builds charged pro rata)",
+               "single_thread": {"value": r1, "unit": "pairs/s", "cores": 1,
+                                 "sample": f"queries [0, {ORACLE_SAMPLE // 16}) of {n}: {pairs1} pairs in {t1:.1f} s"}}
 
     if rank == 0:
         line = {"metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": value, "unit": "pairs/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": "c3: cubic rho=0.85, N=4194304 uniform, cell list r=2.5, ball r=2.5 full "
                                        "sorted NeighborList + fused RDF 500 bins [0,5]",
                            "nl_pairs": nl_pairs, "rdf_pairs": rdf_pairs, "points_per_rank": n,
-                           "l2": "flushed (512 MB write) before every step", "parallelism": f"{world} independent frames"},
-                "e2e": {"value": weak_value(units, world, e2e_step), "unit": "pairs/s",
+                           "l2": "flushed (512 MB write) before every step", "parallelism": "one frame" if world == 1 else
+                           f"one frame over {world} ranks: query-cell slabs, counts and histogram summed (NCCL)"},
+                "e2e": {"value": strong_value(units, e2e_step), "unit": "pairs/s",
                         "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": p["rdf_bins"] * 8},
                 "gpu_launches": int(launches), "roofline": roofline, "kernels": kern, "kernel_rooflines": others,
+                "escalations": esc,
                 "components": components, "clocks": clk, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
@@ -457,14 +518,15 @@ def pmft_components(fgb, torch, dev, stream, flush, n_big=4_194_304):
         per[k] = t / max(c, 1)
     peaks = measured_peaks()
     sm_clock = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sms * 128 * sm_clock * 1e6 / 1e12
     # 32 FP32 operations per unordered pair within reach: displacement 2, r^2 2, and per
     # direction rotation 4, bin index 2, floor 2, fraction 2, margin tests 4
     ops = 32.0 * (bonds / 2) / 1e12
     tile_s = per["k_pmft_tile"] * 1e-3
     roof = {"kernel": "k_pmft_tile", "bound": "alu", "achieved": ops / tile_s, "peak": alu_peak, "unit": "TOP/s",
             "frac": ops / tile_s / alu_peak, "ms": per["k_pmft_tile"],
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
+            "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x {sm_clock:.0f} MHz"}
     t_bigr = timed(lambda: rdf.compute(nqb, reset=True), stream, flush)
     nl_holder = {}
 

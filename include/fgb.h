@@ -90,11 +90,17 @@ int32_t fgb_version(void);
  * function name, e.g. "k_ball_write"); fgb_timing_reset clears the totals. */
 int64_t fgb_kernel_launches(void);
 
-/* Device blocks of 1 MB or more freed by the library (neighbor lists, sort buffers) are
- * kept, up to 48 GB, and handed to later allocations of a similar size on any stream
- * (ordered by an event recorded when they were freed).  fgb_trim_memory waits for
- * their last use and returns them to the device. */
+/* Device memory of the library comes from a memory pool of its own on each device (the
+ * device's default pool, shared with torch and other libraries, is left as it is).
+ * Device blocks of 1 MB or more freed by the library (neighbor lists, sort buffers) are
+ * kept, up to the cache limit, and handed to later allocations of a similar size on
+ * any stream (ordered by an event recorded when they were freed); the pool also keeps
+ * up to the cache limit of freed memory mapped.  fgb_trim_memory waits for the kept
+ * blocks' last use and returns them and the pool's unused memory to the device.
+ * fgb_set_memory_cache sets the cache limit in bytes (default 4 GB, or the environment
+ * variable FGB_MEMORY_CACHE_MB read at load) and releases kept blocks beyond it. */
 int fgb_trim_memory(void);
+int fgb_set_memory_cache(uint64_t bytes);
 int fgb_timing_enable(int32_t on);
 int fgb_timing_read(const char *name, double *total_ms, int64_t *count);
 int fgb_timing_reset(void);
@@ -113,6 +119,15 @@ int fgb_timing_reset(void);
 int fgb_nq_create(const fgb_box *box, const float *points, int64_t n, double r_cell, void *stream,
                   fgb_nq **out);
 void fgb_nq_destroy(fgb_nq *nq);
+
+/*
+ * A NeighborQuery of the box and the points only, with no search structure: for the
+ * computes that take a NeighborList (Steinhardt forward and backward, W_l, averages,
+ * descriptors, RDF / PMFT from a list, clusters, solid-liquid), e.g. a Q_l evaluated
+ * every step of a biased-sampling loop over a fixed list.  No device work, no
+ * allocation; fgb_nq_query on it is UNSUPPORTED.  points must outlive the handle.
+ */
+int fgb_nq_create_points(const fgb_box *box, const float *points, int64_t n, fgb_nq **out);
 
 /* ----------------------------------------------------- NeighborQuery (AABB tree) */
 
@@ -220,19 +235,23 @@ int fgb_rdf_compute(fgb_rdf *rdf, fgb_nq *nq, const float *query_points, int64_t
  */
 int fgb_rdf_result(fgb_rdf *rdf, uint64_t *counts, double *rdf_values, double *bin_centers, void *stream);
 
-/* Device pointer of the uint64 accumulator (bins entries), for graph-captured use. */
+/* Device pointer of the uint64 accumulator (bins entries), for graph-captured use and
+ * for summing the partial histograms of sharded frames across ranks. */
 int fgb_rdf_counts_device(const fgb_rdf *rdf, const uint64_t **counts);
+
+/* The RDF's bins and range (any pointer may be NULL). */
+int fgb_rdf_params(const fgb_rdf *rdf, int32_t *bins, double *r_max, double *r_min);
 
 /* Number of pairs re-decided in FP64 by the last compute (synchronises `stream`). */
 int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
 
 /*
  * Allocation-free RDF of one frame (self query, exclude_ii), for callers that cannot
- * allocate device memory while they run: work recorded into a CUDA graph by a framework
- * that forbids allocation nodes, a simulation engine analysing inside its time step
- * with a fixed memory budget, a runtime whose memory pool owns the device.  The paper
- * has no counterpart; it is the same computation as fgb_rdf_compute with reset != 0
- * and no NeighborList.
+ * allocate device memory while they run: a simulation engine analysing inside its time
+ * step with a fixed memory budget, a runtime whose memory pool owns the device and
+ * treats an outside cudaMalloc (which may synchronise the device) as an error.  The
+ * paper has no counterpart; it is the same computation as fgb_rdf_compute with
+ * reset != 0 and no NeighborList.
  *   points: device float32 (n, 3); counts: device uint64 (bins), overwritten with the
  *   ordered-pair counts of bins [r_min + b (r_max - r_min)/bins, ...).
  * Limits: n <= 262144 points, bins <= 8192 (FGB_ERR_CAPACITY beyond), and the
@@ -240,7 +259,9 @@ int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
  * All working memory (cell list, sort buffers, thresholds, band-pair list; about 24 MB)
  * is one static device array of the library, held by every GPU that loads it until the
  * process exits.  The first call on a device looks up that array's device address, so
- * make the first call on each device before any stream capture.  Every call shares the
+ * make the first call on each device before any stream capture; that address lives as
+ * long as the device's context, so use after a cudaDeviceReset of a device already used
+ * here is not supported.  Every call shares the
  * array and leaves its contents behind (each call clears what must start at zero):
  * calls whose work overlaps on the GPU (different streams, other threads) race and must
  * be serialised by the caller.  No cudaMalloc, cudaFree or allocating library routine is
@@ -248,6 +269,61 @@ int fgb_rdf_escalations(fgb_rdf *rdf, int64_t *n, void *stream);
  */
 int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t n, int32_t bins, double r_max, double r_min,
                     uint64_t *counts, void *stream);
+
+/* ----------------------------------------------- one frame split across ranks */
+
+/*
+ * One frame sharded by contiguous ranges of query cells (Section "Implementation": the
+ * parallel wrappers split per-particle work across workers; here a worker is one GPU
+ * holding every point of the frame, so no halo is exchanged).  Cells are numbered
+ * (z * ny + y) * nx + x on the grid of fgb_nq_dims, so a range is a stack of z slabs.
+ * The ranges of all ranks must partition [0, nx*ny*nz).  Between the calls the caller
+ * sums the ranks' partial counts and histograms (an all-reduce); the library does no
+ * communication.  These calls take the cell-tile route (self query, exclude_ii as
+ * given, every axis at least 2s+1 cells and at most 128 stencil cells; UNSUPPORTED
+ * otherwise) and synchronise `stream` where noted.
+ *
+ * fgb_nq_count_cells: overwrites counts[n] (uint32, device, caller's point order) with
+ * this range's partial neighbor counts of the ball query r_max: each unordered pair whose
+ * half-stencil cell lies in the range adds one to both of its points (plus one for the
+ * self pair of the range's own points when exclude_ii == 0).  The sum over the ranges is
+ * every point's neighbor count.  Asynchronous.
+ */
+int fgb_nq_count_cells(fgb_nq *nq, double r_max, int32_t exclude_ii, int64_t cell_lo, int64_t cell_hi,
+                       uint32_t *counts, void *stream);
+
+/*
+ * From the summed counts (device, n): local_segments (device int64, n + 1) = exclusive
+ * scan of the counts of the points in cells [cell_lo, cell_hi) (other points get empty
+ * rows), global_segments (device int64, n + 1, may be NULL) = exclusive scan of all
+ * counts (the row starts of the whole frame's NeighborList), and on the host the
+ * range's number of pairs and its largest count (either pointer may be NULL).
+ * Synchronises `stream`.
+ */
+int fgb_nq_shard_segments(const fgb_nq *nq, int64_t cell_lo, int64_t cell_hi, const uint32_t *counts,
+                          int64_t *local_segments, int64_t *global_segments, int64_t *n_local_pairs,
+                          uint32_t *max_count, void *stream);
+
+/*
+ * Writes the rows of the range's query points, each sorted by point index as in
+ * fgb_nq_query, at segments[i] (device int64, n + 1; e.g. the local segments above) into
+ * caller-allocated device arrays qi, pj (int32) and dist (float32) of the range's pair
+ * count.  counts: the summed counts; max_count: their largest value over the range.
+ * Synchronises `stream`; CUDA if a row disagrees with its count.
+ */
+int fgb_nq_write_cells(fgb_nq *nq, double r_max, int32_t exclude_ii, int64_t cell_lo, int64_t cell_hi,
+                       const int64_t *segments, const uint32_t *counts, uint32_t max_count, int32_t *qi,
+                       int32_t *pj, float *dist, void *stream);
+
+/*
+ * fgb_rdf_compute of the NeighborQuery's own points restricted to the pairs whose
+ * half-stencil cell lies in [cell_lo, cell_hi) (each unordered pair counted twice, as
+ * there); the ranges' accumulators sum to the frame's histogram.  The normalisation
+ * counts the whole frame, so g(r) of the summed counts is the frame's.  At most 1024
+ * bins.  Asynchronous.
+ */
+int fgb_rdf_compute_cells(fgb_rdf *rdf, fgb_nq *nq, int64_t cell_lo, int64_t cell_hi, int32_t reset,
+                          void *stream);
 
 /* ------------------------------------------------------------------------ PMFT */
 

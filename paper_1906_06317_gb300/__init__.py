@@ -62,12 +62,14 @@ _SIGS = {
     "fgb_version": (_I32, []),
     "fgb_kernel_launches": (_I64, []),
     "fgb_trim_memory": (_I32, []),
+    "fgb_set_memory_cache": (_I32, [ctypes.c_uint64]),
     "fgb_timing_enable": (_I32, [_I32]),
     "fgb_timing_read": (_I32, [ctypes.c_char_p, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "fgb_timing_reset": (_I32, []),
     "fgb_nq_create": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _D, _P, _PP]),
     "fgb_nq_destroy": (None, [_P]),
     "fgb_aabb_create": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _P, _PP]),
+    "fgb_nq_create_points": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _PP]),
     "fgb_nq_dims": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "fgb_nq_cells": (_I32, [_P, _PP, _PP, _PP]),
     "fgb_nq_query": (_I32, [_P, _P, _I64, ctypes.POINTER(fgb_query_args), _P, _PP]),
@@ -83,6 +85,12 @@ _SIGS = {
     "fgb_rdf_counts_device": (_I32, [_P, _PP]),
     "fgb_rdf_escalations": (_I32, [_P, ctypes.POINTER(_I64), _P]),
     "fgb_rdf_noalloc": (_I32, [ctypes.POINTER(fgb_box), _P, _I64, _I32, _D, _D, _P, _P]),
+    "fgb_rdf_params": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "fgb_nq_count_cells": (_I32, [_P, _D, _I32, _I64, _I64, _P, _P]),
+    "fgb_nq_shard_segments": (_I32, [_P, _I64, _I64, _P, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_uint32),
+                                     _P]),
+    "fgb_nq_write_cells": (_I32, [_P, _D, _I32, _I64, _I64, _P, _P, ctypes.c_uint32, _P, _P, _P, _P]),
+    "fgb_rdf_compute_cells": (_I32, [_P, _P, _I64, _I64, _I32, _P]),
     "fgb_pmftxy_create": (_I32, [_D, _D, _I32, _I32, _PP]),
     "fgb_pmftxy_destroy": (None, [_P]),
     "fgb_pmftxy_compute": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P]),
@@ -140,6 +148,11 @@ def kernel_launches() -> int:
 def trim_memory():
     """Return the device blocks the library keeps for reuse."""
     _check(lib().fgb_trim_memory())
+
+
+def set_memory_cache(nbytes: int):
+    """Largest total of freed device memory the library keeps for reuse (default 4 GB)."""
+    _check(lib().fgb_set_memory_cache(int(nbytes)))
 
 
 def timing_enable(on: bool = True):
@@ -393,6 +406,27 @@ class AABBQuery(NeighborQuery):
     def cells(self):
         raise FGBError(ERR_UNSUPPORTED, "a tree NeighborQuery has no cell list")
 
+
+
+class PointsQuery(NeighborQuery):
+    """The box and the points only, for computes given a NeighborList (no search
+    structure is built; querying it raises)."""
+
+    def __init__(self, box, points: torch.Tensor):
+        self.box = Box.from_box(box)
+        self.points = _need_cuda(points, name="points")
+        if self.points.ndim != 2 or self.points.shape[1] != 3:
+            raise ValueError("points must have shape (N, 3)")
+        self.r_cell = None
+        h = ctypes.c_void_p()
+        b = self.box._c()
+        _check(lib().fgb_nq_create_points(ctypes.byref(b), self.points.data_ptr(), self.points.shape[0],
+                                          ctypes.byref(h)))
+        self._o = _Owned(h.value, "fgb_nq_destroy", (self.points,))
+        self._h = self._o.ptr
+
+    def cells(self):
+        raise FGBError(ERR_UNSUPPORTED, "a NeighborQuery of points only has no cell list")
 
 
 def _as_nq(system, r_cell=None) -> NeighborQuery:
@@ -693,7 +727,7 @@ class Q6Mean(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, points, box, nlist, l=6):
-        nq = NeighborQuery(box, points.detach(), r_cell=None)
+        nq = PointsQuery(box, points.detach())  # the list is fixed: no cell list needed
         st = Steinhardt(l)
         st.compute(nq, neighbors=nlist)
         ctx.st = st

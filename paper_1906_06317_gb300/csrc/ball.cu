@@ -18,6 +18,17 @@ bool force_thread_kernels() {
     return v == 1;
 }
 
+// FGB_SPLIT_KERNELS=0 keeps few-query grids on the one-thread-per-query kernels instead
+// of the 8-lanes-per-query ones (so that both stay covered by tests).
+static bool split_kernels_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_SPLIT_KERNELS");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 bool force_tile_kernels() {
     static int v = -1;
     if (v < 0) {
@@ -349,15 +360,18 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->segments, nqq + 1, s);
     uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
     const bool checkj = !Q.self && a.exclude;
-    const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && !force_thread_kernels();
+    const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && (nq->walk_set || !force_thread_kernels());
     // few queries: several lanes per query (the single-lane kernels would leave most SMs idle)
-    const bool split = !tile && nqq < (int64_t)num_sms() * 128;
+    const bool split = !tile && nqq < (int64_t)num_sms() * 128 && split_kernels_enabled();
     if (st == FGB_OK && nqq > 0 && tile) {
         // 2D: the tile kernels walk only the points' layer; a point off the plane keeps a
         // count of zero instead of an unwritten one
         if (nq->box.is2d && cudaMemsetAsync(counts, 0, sizeof(uint32_t) * nqq, s) != cudaSuccess)
             st = fail(FGB_ERR_CUDA, "memset failed");
-        st = st ? st : tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
+        if (nl_kernels_enabled())
+            st = st ? st : nl_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
+        else
+            st = st ? st : tile_count(nq, plan, R, a.exclude, a.esc, a.err, counts, s);
         st = st ? st : scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK && nqq > 0 && split) {
         {
@@ -402,7 +416,9 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     st = st ? st : dalloc_n(&nl->dist, hs.total, s);
     if (st == FGB_OK && nqq > 0 && hs.total > 0) {
         const int cap = (int)((hs.maxcount + 3) & ~3u);
-        if (tile && cap <= 128 && tile_write_smem(cap) <= 160 * 1024) {
+        if (tile && nl_kernels_enabled()) {
+            st = nl_write(nq, plan, R, a.exclude, a.err, nl->segments, counts, cap, nqq, nl->qi, nl->pj, nl->dist, s);
+        } else if (tile && cap <= 128 && tile_write_smem(cap) <= 160 * 1024) {
             st = tile_write(nq, plan, R, a.exclude, a.err, nl->segments, counts, cap, nl->qi, nl->pj, nl->dist, s);
         } else if (tile && cap <= 16384) {
             // long rows: appended to the list by the cell tiles, then sorted per row
@@ -495,7 +511,9 @@ extern "C" int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_que
     memset(nl, 0, sizeof(*nl));
     nl->stream = s;
     int st = FGB_OK;
-    if (nq->kind == 1) {
+    if (nq->kind == 2) {
+        st = fail(FGB_ERR_UNSUPPORTED, "a NeighborQuery of points only answers no query; pass a NeighborList");
+    } else if (nq->kind == 1) {
         st = ball ? aabb_ball_query(nq, query_points, n_query, args, s, nl)
                   : aabb_knn_query(nq, query_points, n_query, args, s, nl);
     } else {

@@ -1,6 +1,7 @@
 // Library state shared by all entry points: error messages, allocation, device info.
 #include <atomic>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -23,37 +24,60 @@ int fail(int code, const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
-// The device's default memory pool returns freed memory to the system at every
-// synchronisation unless told otherwise; then each neighbor list (gigabytes) is mapped
-// again on the next query.  Keep freed blocks cached in this process instead.
-static void keep_pool_cached() {
-    static bool done[64] = {false};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+// Device memory comes from a memory pool of the library's own on each device (the
+// device's default pool, which torch and other libraries share, keeps its settings).
+// The pool keeps up to the cache limit of freed memory mapped, so a neighbor list
+// (gigabytes) is not mapped again on every query.
+namespace {
+std::mutex g_amu;
+cudaMemPool_t g_pool[64];
+bool g_pool_failed[64];
+
+size_t cache_limit_default() {
+    const char *e = getenv("FGB_MEMORY_CACHE_MB");
+    if (e && *e) {
+        const long long mb = atoll(e);
+        if (mb >= 0) return (size_t)mb << 20;
     }
-    cudaGetLastError();
-    done[dev] = true;
+    return size_t(4) << 30;  // 4 GB
+}
+size_t g_cache_limit = cache_limit_default();
+
+// The library's pool on device dev (created on first use), or nullptr when the device
+// cannot create one (allocations then use the default pool, left as it is).  g_amu held.
+cudaMemPool_t lib_pool_locked(int dev) {
+    if (dev < 0 || dev >= 64 || g_pool_failed[dev]) return nullptr;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&g_pool[dev], &props) != cudaSuccess) {
+            cudaGetLastError();
+            g_pool[dev] = nullptr;
+            g_pool_failed[dev] = true;
+            return nullptr;
+        }
+        uint64_t keep = g_cache_limit;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return g_pool[dev];
 }
 
-// Large blocks (neighbor lists, sort buffers) are kept for reuse instead of being freed:
-// even from a cached memory pool, mapping a fresh gigabyte-sized block takes about a
-// millisecond per call.  A kept block carries an event recorded on the stream that freed
-// it; the stream that reuses it waits on that event first, so reuse is ordered on any
-// stream.  fgb_trim_memory() releases everything kept.
-namespace {
+// Large blocks (neighbor lists, sort buffers) are also kept for reuse instead of being
+// freed: even from a pool that keeps its memory, mapping a fresh gigabyte-sized block
+// takes about a millisecond per call.  A kept block carries an event recorded on the
+// stream that freed it; the stream that reuses it waits on that event first, so reuse
+// is ordered on any stream.  The kept blocks total at most the cache limit;
+// fgb_trim_memory() releases everything kept.
 constexpr size_t kKeepMin = size_t(1) << 20;
-constexpr size_t kKeepMax = size_t(48) << 30;
 struct Kept {
     void *p;
     size_t bytes;
     int dev;
     cudaEvent_t done;
 };
-std::mutex g_amu;
 std::vector<Kept> g_kept;
 size_t g_kept_bytes = 0;
 std::unordered_map<void *, size_t> g_sizes;
@@ -62,37 +86,52 @@ bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
 }
+
+// Releases kept blocks (oldest first) until they total at most `limit`.  g_amu held.
+void release_kept_locked(size_t limit) {
+    while (g_kept_bytes > limit && !g_kept.empty()) {
+        Kept b = g_kept.front();
+        g_kept.erase(g_kept.begin());
+        g_kept_bytes -= b.bytes;
+        cudaEventSynchronize(b.done);
+        cudaEventDestroy(b.done);
+        cudaFree(b.p);
+    }
+}
 }  // namespace
 
 int dalloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
-    keep_pool_cached();
     if (bytes == 0) bytes = 16;
-    if (bytes >= kKeepMin && !capturing(s)) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool = nullptr;
+    {
         std::lock_guard<std::mutex> lk(g_amu);
-        size_t best = SIZE_MAX;
-        int bi = -1;
-        for (size_t k = 0; k < g_kept.size(); ++k) {
-            const Kept &b = g_kept[k];
-            if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes && b.bytes < best) {
-                best = b.bytes;
-                bi = (int)k;
+        pool = lib_pool_locked(dev);
+        if (bytes >= kKeepMin && !capturing(s)) {
+            size_t best = SIZE_MAX;
+            int bi = -1;
+            for (size_t k = 0; k < g_kept.size(); ++k) {
+                const Kept &b = g_kept[k];
+                if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes && b.bytes < best) {
+                    best = b.bytes;
+                    bi = (int)k;
+                }
+            }
+            if (bi >= 0) {
+                Kept b = g_kept[bi];
+                g_kept.erase(g_kept.begin() + bi);
+                g_kept_bytes -= b.bytes;
+                cudaStreamWaitEvent(s, b.done, 0);
+                cudaEventDestroy(b.done);
+                *p = b.p;
+                g_sizes[b.p] = b.bytes;
+                return FGB_OK;
             }
         }
-        if (bi >= 0) {
-            Kept b = g_kept[bi];
-            g_kept.erase(g_kept.begin() + bi);
-            g_kept_bytes -= b.bytes;
-            cudaStreamWaitEvent(s, b.done, 0);
-            cudaEventDestroy(b.done);
-            *p = b.p;
-            g_sizes[b.p] = b.bytes;
-            return FGB_OK;
-        }
     }
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -115,7 +154,7 @@ void dfree(void *p, cudaStream_t s) {
             const size_t bytes = it->second;
             g_sizes.erase(it);
             cudaEvent_t ev;
-            if (g_kept_bytes + bytes <= kKeepMax && !capturing(s) &&
+            if (g_kept_bytes + bytes <= g_cache_limit && !capturing(s) &&
                 cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
                 if (cudaEventRecord(ev, s) == cudaSuccess) {
                     int dev = 0;
@@ -131,15 +170,21 @@ void dfree(void *p, cudaStream_t s) {
     cudaFreeAsync(p, s);
 }
 
+int set_memory_cache(size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_amu);
+    g_cache_limit = bytes;
+    release_kept_locked(bytes);
+    uint64_t keep = bytes;
+    for (int d = 0; d < 64; ++d)
+        if (g_pool[d]) cudaMemPoolSetAttribute(g_pool[d], cudaMemPoolAttrReleaseThreshold, &keep);
+    return FGB_OK;
+}
+
 int trim_memory() {
     std::lock_guard<std::mutex> lk(g_amu);
-    for (Kept &b : g_kept) {
-        cudaEventSynchronize(b.done);
-        cudaEventDestroy(b.done);
-        cudaFree(b.p);
-    }
-    g_kept.clear();
-    g_kept_bytes = 0;
+    release_kept_locked(0);
+    for (int d = 0; d < 64; ++d)
+        if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
     return FGB_OK;
 }
 
@@ -211,6 +256,8 @@ static void resolve_timings() {
 }  // namespace fgb
 
 extern "C" int fgb_trim_memory(void) { return fgb::trim_memory(); }
+
+extern "C" int fgb_set_memory_cache(uint64_t bytes) { return fgb::set_memory_cache((size_t)bytes); }
 
 extern "C" int64_t fgb_kernel_launches(void) { return fgb::g_launches.load(); }
 

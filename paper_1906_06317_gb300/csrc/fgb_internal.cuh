@@ -33,9 +33,11 @@ void clear_error();
             return fgb_s_;         \
     } while (0)
 
-// Stream-ordered device allocation (the device's default memory pool).
+// Stream-ordered device allocation (a memory pool of the library's own, capi.cu).
 int dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
+int trim_memory();
+int set_memory_cache(size_t bytes);
 template <class T>
 int dalloc_n(T **p, size_t n, cudaStream_t s) {
     return dalloc(reinterpret_cast<void **>(p), n * sizeof(T), s);
@@ -132,9 +134,14 @@ struct fgb_nq {
     float2 *origin_buf;    // all origin tables, packed
     fgb::OriginTables org;
     cudaStream_t stream;
-    int kind;              // 0: cell list, 1: bounding-volume hierarchy (sorted = points in Morton order)
+    int kind;              // 0: cell list, 1: bounding-volume hierarchy (sorted = points in Morton order),
+                           // 2: box and points only (consumers of a given NeighborList)
     void *bvh;             // kind 1: n-1 internal nodes (aabb.cu)
     int bvh_moved;         // kind 1: wrapping moved some point
+    // query cells the cell-tile kernels walk: all cells unless a sharded call (shard.cu)
+    // narrows them to [walk_lo, walk_hi) for its duration
+    int walk_set;
+    int64_t walk_lo, walk_hi;
 };
 
 // Steinhardt state (steinhardt.cu, order.cu): per-particle Q_lm, m = 0..l, and the
@@ -239,6 +246,16 @@ int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, 
              int32_t *counts, int *list, int *list_count, cudaStream_t s);
 int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
                const uint32_t *counts, int cap, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
+
+// NeighborList count and write of a self ball query on the cell tiles (nlist.cu): the
+// count tests each unordered pair once over half stencils; the write sorts each cell's
+// pruned stencil by point index once and stores every hit in place.  FGB_NL_KERNELS=0
+// keeps tile_count / tile_write instead.
+bool nl_kernels_enabled();
+int nl_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
+             uint32_t *counts, cudaStream_t s);
+int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+             const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
 
 // RDF bin parameters for an error bound G2 on r^2 (rdf.cu).
 struct BinParams;

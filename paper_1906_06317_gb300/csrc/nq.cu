@@ -455,6 +455,26 @@ extern "C" int fgb_nq_create(const fgb_box *box, const float *points, int64_t n,
     return FGB_OK;
 }
 
+extern "C" int fgb_nq_create_points(const fgb_box *box, const float *points, int64_t n, fgb_nq **out) {
+    clear_error();
+    if (!out) return fail(FGB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !points)) return fail(FGB_ERR_INVALID_ARG, "points/n invalid");
+    if (n >= (int64_t)1 << 31) return fail(FGB_ERR_CAPACITY, "at most 2^31-1 points");
+    fgb_nq *nq = new fgb_nq();
+    memset(nq, 0, sizeof(*nq));
+    nq->points = points;
+    nq->n = n;
+    nq->kind = 2;
+    const int st = make_box(box, &nq->box);
+    if (st != FGB_OK) {
+        delete nq;
+        return st;
+    }
+    *out = nq;
+    return FGB_OK;
+}
+
 extern "C" void fgb_nq_destroy(fgb_nq *nq) {
     if (!nq) return;
     dfree(nq->sorted, nq->stream);

@@ -633,7 +633,7 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                 const int nfull = (2 * plan.s[0] + 1) * (2 * plan.s[1] + 1) * (2 * plan.s[2] + 1);
                 const int nhalf = (nfull + 1) / 2;
                 const bool tile = a.half && nhalf <= kTileMaxStencil && r->bins <= kRdfTileMaxBins && tile_worth(nq) &&
-                                  !force_thread_kernels();
+                                  (nq->walk_set || !force_thread_kernels());
                 if (tile) {
                     st = launch_rdf_tile(nq, plan, R, r, a.P, nhalf, s);
                 } else {
@@ -688,6 +688,14 @@ extern "C" int fgb_rdf_result(fgb_rdf *r, uint64_t *counts, double *rdf_values, 
     return FGB_OK;
 }
 
+extern "C" int fgb_rdf_params(const fgb_rdf *r, int32_t *bins, double *r_max, double *r_min) {
+    if (!r) return fail(FGB_ERR_INVALID_ARG, "rdf is NULL");
+    if (bins) *bins = r->bins;
+    if (r_max) *r_max = r->r_max;
+    if (r_min) *r_min = r->r_min;
+    return FGB_OK;
+}
+
 extern "C" int fgb_rdf_counts_device(const fgb_rdf *r, const uint64_t **counts) {
     if (!r || !counts) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
     *counts = reinterpret_cast<const uint64_t *>(r->hist);
@@ -708,7 +716,6 @@ extern "C" int fgb_rdf_escalations(fgb_rdf *r, int64_t *n, void *stream) {
 // ------------------------------------------------------------------ allocation-free RDF
 //
 // fgb_rdf_noalloc serves callers that must not allocate device memory while they run:
-// code recorded into a CUDA graph by a host framework that forbids allocation nodes,
 // simulation engines that call analysis from inside their time step with a fixed
 // memory budget, or runtimes whose own pool owns the device and treats an outside
 // cudaMalloc (which may synchronise the device) as an error.  Its whole working set
@@ -751,7 +758,10 @@ static void *g_addr[64];
 static std::mutex g_mu;
 
 // Device address of g_scratch on the current device, looked up once per device (the
-// host-side symbol is only a stand-in and must never be handed to a kernel).
+// host-side symbol is only a stand-in and must never be handed to a kernel).  The
+// address stays valid for the life of the device's context: a cudaDeviceReset (which
+// unloads the module) would leave it stale, so calls after a reset of a device already
+// used here are not supported.
 static int scratch(void **out) {
     int dev = 0;
     FGB_CUDA(cudaGetDevice(&dev));

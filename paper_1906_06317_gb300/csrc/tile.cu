@@ -480,6 +480,31 @@ __device__ __forceinline__ void write_cell_passes(const TileArgs &a, const TS &t
     }
 }
 
+// The write of one query cell A (one warp).
+template <int NS>
+__device__ __forceinline__ void tile_write_cell(const TileArgs &a, int64_t A, const int64_t *__restrict__ seg,
+                                                const uint32_t *__restrict__ counts, int cap, int packable,
+                                                int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                float *__restrict__ d_out, unsigned char *tsm,
+                                                TileStencilT<NS> &ts, float4 *stage1, int *rowlen) {
+    const int warp = threadIdx.x >> 5;
+    const int begA = (int)__ldg(a.cell_start + A);
+    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
+    if (nA == 0) return;
+    int cx, cy, cz;
+    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
+    const int n = tile_stencil(a, cx, cy, cz, false, ts);
+    const int total = ts.pre[n];
+    unsigned char *region = tsm + (size_t)warp * write_warp_bytes(cap);
+    if (total <= kWriteStage)
+        write_cell_staged(a, ts, n, total, begA, nA, reinterpret_cast<float4 *>(region),
+                          reinterpret_cast<uint2 *>(region + kWriteStage * sizeof(float4)), seg, counts, cap,
+                          packable != 0, qi_out, pj_out, d_out);
+    else
+        write_cell_passes(a, ts, n, total, begA, nA, stage1, rowlen, reinterpret_cast<uint2 *>(region), seg, counts,
+                          cap, packable != 0, qi_out, pj_out, d_out);
+}
+
 template <int NS>
 __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_constant__ TileArgs a,
                                                                    const int64_t *__restrict__ seg,
@@ -494,22 +519,32 @@ __global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write(const __grid_
     const int warp = threadIdx.x >> 5;
     const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
-    const int begA = (int)__ldg(a.cell_start + A);
-    const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
-    if (nA == 0) return;
-    int cx, cy, cz;
-    cell_coords((uint32_t)A, a.nc, cx, cy, cz);
-    TileStencilT<NS> &ts = sts[warp];
-    const int n = tile_stencil(a, cx, cy, cz, false, ts);
-    const int total = ts.pre[n];
-    unsigned char *region = tsm + (size_t)warp * write_warp_bytes(cap);
-    if (total <= kWriteStage)
-        write_cell_staged(a, ts, n, total, begA, nA, reinterpret_cast<float4 *>(region),
-                          reinterpret_cast<uint2 *>(region + kWriteStage * sizeof(float4)), seg, counts, cap,
-                          packable != 0, qi_out, pj_out, d_out);
-    else
-        write_cell_passes(a, ts, n, total, begA, nA, sstage[warp], srow[warp], reinterpret_cast<uint2 *>(region), seg,
-                          counts, cap, packable != 0, qi_out, pj_out, d_out);
+    tile_write_cell<NS>(a, A, seg, counts, cap, packable, qi_out, pj_out, d_out, tsm, sts[warp], sstage[warp],
+                        srow[warp]);
+}
+
+// The same over a device list of cells (warps stride through it).
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32, 5) k_tile_write_listed(const __grid_constant__ TileArgs a,
+                                                                          const int *__restrict__ cells,
+                                                                          const int *__restrict__ ncells,
+                                                                          const int64_t *__restrict__ seg,
+                                                                          const uint32_t *__restrict__ counts,
+                                                                          int cap, int packable,
+                                                                          int32_t *__restrict__ qi_out,
+                                                                          int32_t *__restrict__ pj_out,
+                                                                          float *__restrict__ d_out) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5;
+    const int m = *ncells;
+    for (int k = blockIdx.x * kTileWarps + warp; k < m; k += gridDim.x * kTileWarps) {
+        tile_write_cell<NS>(a, cells[k], seg, counts, cap, packable, qi_out, pj_out, d_out, tsm, sts[warp],
+                            sstage[warp], srow[warp]);
+        __syncwarp();
+    }
 }
 
 // ---- dense cells: rows appended straight to the list, sorted afterwards ----
@@ -566,30 +601,22 @@ __device__ __noinline__ void write_chunk_global_exact(const TileArgs &a, const f
     }
 }
 
+// Hits of one query cell A appended to their segments (one warp).
 template <int NS>
-__global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global(const __grid_constant__ TileArgs a,
-                                                                       const int64_t *__restrict__ seg,
-                                                                       const uint32_t *__restrict__ counts,
-                                                                       int32_t *__restrict__ qi_out,
-                                                                       int32_t *__restrict__ pj_out,
-                                                                       float *__restrict__ d_out) {
-    __shared__ TileStencilT<NS> sts[kTileWarps];
-    __shared__ float4 sstage[kTileWarps][32];
-    __shared__ int srow[kTileWarps][kTileQueries];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
-    if (A >= a.ncell) return;
+__device__ __forceinline__ void tile_write_global_cell(const TileArgs &a, int64_t A, const int64_t *__restrict__ seg,
+                                                       const uint32_t *__restrict__ counts,
+                                                       int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                                       float *__restrict__ d_out, TileStencilT<NS> &ts, float4 *stage,
+                                                       int *rowlen) {
+    const int lane = threadIdx.x & 31;
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
     if (nA == 0) return;
     int cx, cy, cz;
     cell_coords((uint32_t)A, a.nc, cx, cy, cz);
-    TileStencilT<NS> &ts = sts[warp];
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
     const float lo = a.band.lo, hi = a.band.hi;
-    float4 *stage = sstage[warp];
-    int *rowlen = srow[warp];
     for (int qb = 0; qb < nA; qb += kTileQueries) {
         const int nq = min(kTileQueries, nA - qb);
         const QLayout L = qlayout(nq);
@@ -614,6 +641,40 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global(const __g
             __syncwarp();
         }
         if (L.g == 0 && qact && (uint32_t)*myrc != want) atomicExch(a.err, *myrc > (int)want ? 1 : 2);
+        __syncwarp();
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global(const __grid_constant__ TileArgs a,
+                                                                       const int64_t *__restrict__ seg,
+                                                                       const uint32_t *__restrict__ counts,
+                                                                       int32_t *__restrict__ qi_out,
+                                                                       int32_t *__restrict__ pj_out,
+                                                                       float *__restrict__ d_out) {
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5;
+    const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
+    if (A >= a.ncell) return;
+    tile_write_global_cell<NS>(a, A, seg, counts, qi_out, pj_out, d_out, sts[warp], sstage[warp], srow[warp]);
+}
+
+// The same over a device list of cells (warps stride through it).
+template <int NS>
+__global__ void __launch_bounds__(kTileWarps * 32) k_tile_write_global_listed(
+    const __grid_constant__ TileArgs a, const int *__restrict__ cells, const int *__restrict__ ncells,
+    const int64_t *__restrict__ seg, const uint32_t *__restrict__ counts, int32_t *__restrict__ qi_out,
+    int32_t *__restrict__ pj_out, float *__restrict__ d_out) {
+    __shared__ TileStencilT<NS> sts[kTileWarps];
+    __shared__ float4 sstage[kTileWarps][32];
+    __shared__ int srow[kTileWarps][kTileQueries];
+    const int warp = threadIdx.x >> 5;
+    const int m = *ncells;
+    for (int k = blockIdx.x * kTileWarps + warp; k < m; k += gridDim.x * kTileWarps) {
+        tile_write_global_cell<NS>(a, cells[k], seg, counts, qi_out, pj_out, d_out, sts[warp], sstage[warp],
+                                   srow[warp]);
         __syncwarp();
     }
 }
@@ -891,7 +952,8 @@ bool tile_ok(const StencilPlan &p) {
 
 bool tile_worth(const fgb_nq *nq) {
     const int64_t cells = nq->grid.ncell;
-    return force_tile_kernels() || (cells >= 4 * (int64_t)num_sms() && nq->n <= 64 * cells);
+    // a sharded call walks cells, which only the cell-tile kernels do
+    return nq->walk_set || force_tile_kernels() || (cells >= 4 * (int64_t)num_sms() && nq->n <= 64 * cells);
 }
 
 TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude) {
@@ -913,6 +975,12 @@ TileArgs tile_args(const fgb_nq *nq, const StencilPlan &p, double R, int exclude
         const int64_t layer = (int64_t)nq->grid.nc[0] * nq->grid.nc[1];
         t.cell_lo = layer;
         t.ncell = 2 * layer;
+    }
+    if (nq->walk_set) {
+        // a shard of the query cells (Section "Implementation": per-particle work split
+        // across workers): walk only [walk_lo, walk_hi)
+        t.cell_lo = std::max<int64_t>(t.cell_lo, nq->walk_lo);
+        t.ncell = std::max<int64_t>(t.cell_lo, std::min<int64_t>(t.ncell, nq->walk_hi));
     }
     t.p_orig = nq->points;
     t.bf = nq->box.f;
@@ -1005,6 +1073,51 @@ int tile_write_global(const fgb_nq *nq, const StencilPlan &p, double R, int excl
     } else {
         FGB_KSCOPE("k_tile_write_global", s);
         k_tile_write_global<kTileMaxStencil><<<grid, kTileWarps * 32, 0, s>>>(t, seg, counts, qi, pj, dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+// The write kernels over a device list of cells (the cells the staged-sort write
+// kernel of nlist.cu could not take); the grid strides through the list.
+int tile_write_listed(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
+                      const uint32_t *counts, int cap, const int *cells, const int *ncells, int32_t *qi, int32_t *pj,
+                      float *dist, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, R, exclude);
+    t.err = err;
+    const size_t smem = tile_write_smem(cap);
+    if (smem > 160 * 1024) return fail(FGB_ERR_UNSUPPORTED, "tile write: neighbor count too large");
+    const int packable = cap <= 128 && nq->n < ((int64_t)1 << 25);
+    const unsigned grid = (unsigned)num_sms() * 4;
+    if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
+        FGB_CUDA(cudaFuncSetAttribute(k_tile_write_listed<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FGB_KSCOPE("k_tile_write_listed", s);
+        k_tile_write_listed<32><<<grid, kTileWarps * 32, smem, s>>>(t, cells, ncells, seg, counts, cap, packable, qi,
+                                                                    pj, dist);
+    } else {
+        FGB_CUDA(cudaFuncSetAttribute(k_tile_write_listed<kTileMaxStencil>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FGB_KSCOPE("k_tile_write_listed", s);
+        k_tile_write_listed<kTileMaxStencil><<<grid, kTileWarps * 32, smem, s>>>(t, cells, ncells, seg, counts, cap,
+                                                                                 packable, qi, pj, dist);
+    }
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
+int tile_write_global_listed(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err,
+                             const int64_t *seg, const uint32_t *counts, const int *cells, const int *ncells,
+                             int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
+    TileArgs t = tile_args(nq, p, R, exclude);
+    t.err = err;
+    const unsigned grid = (unsigned)num_sms() * 4;
+    if ((2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1) <= 32) {
+        FGB_KSCOPE("k_tile_write_global_listed", s);
+        k_tile_write_global_listed<32><<<grid, kTileWarps * 32, 0, s>>>(t, cells, ncells, seg, counts, qi, pj, dist);
+    } else {
+        FGB_KSCOPE("k_tile_write_global_listed", s);
+        k_tile_write_global_listed<kTileMaxStencil><<<grid, kTileWarps * 32, 0, s>>>(t, cells, ncells, seg, counts,
+                                                                                     qi, pj, dist);
     }
     FGB_LAUNCH_CHECK();
     return FGB_OK;

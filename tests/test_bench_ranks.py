@@ -1,7 +1,7 @@
 """The multi-rank logic of bench.py on CPU: world size 2 over gloo (127.0.0.1).
 
-Each rank analyses its own frame (weak scaling); the step time is the slowest rank's and
-the value counts the units of every rank."""
+The ranks split one frame (strong scaling): every rank holds the same frame, the step
+time is the slowest rank's and the value counts the frame's units once."""
 import os
 import socket
 
@@ -27,7 +27,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     r, w, _ = bench.env_rank()
     t = bench.max_over_ranks(10.0 * (r + 1), dist, "cpu")
-    out[rank] = (r, w, t, bench.frame_seed(r), bench.weak_value(1000, w, t))
+    out[rank] = (r, w, t, bench.frame_seed(r), bench.strong_value(1000, t))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -43,10 +43,11 @@ def test_two_ranks_take_the_slowest_time_and_sum_units():
     for rank, (r, w, t, seed, value) in res.items():
         assert r == rank and w == world
         assert t == 20.0                       # max over ranks
-        assert value == pytest.approx(1000 * 2 / 0.020)
-    assert res[0][3] != res[1][3]              # independent frames per rank
+        assert value == pytest.approx(1000 / 0.020)
+    assert res[0][3] == res[1][3]              # one frame shared by the ranks
 
 
 def test_single_rank_defaults():
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.weak_value(10, 1, 1000.0) == pytest.approx(10.0)
+    assert bench.strong_value(10, 1000.0) == pytest.approx(10.0)

@@ -41,6 +41,8 @@ def assert_ball(nl, b, x, r):
     _, off, pj, dist = oracle.ball_query(b, x, r)
     assert np.array_equal(nl.segments.cpu().numpy(), off), "segments differ"
     assert np.array_equal(nl.point_indices.cpu().numpy(), pj), "point indices differ"
+    assert np.array_equal(nl.query_point_indices.cpu().numpy(), np.repeat(np.arange(len(off) - 1), np.diff(off))), \
+        "query indices differ"
     assert np.all(np.abs(nl.distances.cpu().numpy() - dist) <= 2e-6 * r + 1e-7), "distances differ"
 
 
@@ -294,6 +296,7 @@ for b in (W.Box.square(30.0), W.Box(28.0, 24.0, 0.0, 0.3)):
         _, off, pj, _ = oracle.ball_query(b, x, r)
         assert np.array_equal(nl.segments.cpu().numpy(), off)
         assert np.array_equal(nl.point_indices.cpu().numpy(), pj)
+        assert np.array_equal(nl.query_point_indices.cpu().numpy(), np.repeat(np.arange(len(off) - 1), np.diff(off)))
         h = fgb.RDF(120, r); h.compute(fgb.NeighborQuery(b, dev(x), r_cell=r))
         assert np.array_equal(h.bin_counts, oracle.rdf_counts(b, x, 120, r))
     k = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()

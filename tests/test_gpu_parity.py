@@ -344,6 +344,24 @@ def test_q6_backward_autograd_and_knn_scatter(fgb):
     assert abs(Q.item() - q_ref.mean()) <= 1e-6
 
 
+def test_points_only_query_serves_list_computes(fgb):
+    # Q6Mean's handle: the box and the points, no cell list; same q6 and gradient as a
+    # cell-list NeighborQuery given the same list, and no query of its own
+    w = W.c4(n_cells=6)
+    pts = dev(w.points)
+    nq = fgb.NeighborQuery(w.box, pts, r_cell=1.3)
+    nl = nq.query(None, dict(r_max=1.3, exclude_ii=True)).toNeighborList()
+    a, b = fgb.Steinhardt(6), fgb.Steinhardt(6)
+    a.compute(nq, neighbors=nl)
+    pq = fgb.PointsQuery(w.box, pts)
+    b.compute(pq, neighbors=nl)
+    assert torch.equal(a.particle_order, b.particle_order)
+    assert torch.equal(a.backward(1.0), b.backward(1.0))
+    with pytest.raises(fgb.FGBError) as e:
+        pq.query(None, dict(r_max=1.3, exclude_ii=True)).toNeighborList()
+    assert e.value.code == fgb.ERR_UNSUPPORTED
+
+
 # ---------------------------------------------- full-size workloads, sampled outputs
 
 
@@ -419,8 +437,13 @@ def test_full_c2_steinhardt_and_c4_gradient_sampled(fgb):
             assert abs(fd - g[k, c]) <= G_TOL * np.abs(g).max() + 1e-3 * abs(fd)
 
 
-# Small grids run one thread per query by default and large ones the cell-tile kernels;
-# each environment switch forces one family so that both stay covered at small sizes.
+# Small grids run 8 lanes per query (or one thread per query with many queries) by
+# default and large ones the cell-tile kernels; the environment switches force one
+# family, or one variant inside it, so that every kernel stays covered at small sizes:
+#   FGB_THREAD_KERNELS=1 (+ FGB_SPLIT_KERNELS=0: the single-lane count and write),
+#   FGB_TILE_KERNELS=1 (the staged-sort write; + FGB_NL_STAGE_CAP=64: most cells to the
+#   listed fallback; + FGB_NL_KERNELS=0: the earlier tile count and write;
+#   + FGB_NL_QN=2 FGB_NL_QI=1: two queries per pass, query index stored in the pass).
 KERNEL_SWITCH_CHECKS = r"""
 import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb
 dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
@@ -429,6 +452,7 @@ def ball(b, x, r, rc):
     _, off, pj, d = oracle.ball_query(b, x, r)
     assert np.array_equal(nl.segments.cpu().numpy(), off)
     assert np.array_equal(nl.point_indices.cpu().numpy(), pj)
+    assert np.array_equal(nl.query_point_indices.cpu().numpy(), np.repeat(np.arange(len(off) - 1), np.diff(off)))
     assert np.allclose(nl.distances.cpu().numpy(), d, atol=1e-5)
 def rdf(b, x, bins, r, rc):
     h = fgb.RDF(bins, r); h.compute(fgb.NeighborQuery(b, dev(x), r_cell=rc))
@@ -449,7 +473,10 @@ print('ok')
 """
 
 
-@pytest.mark.parametrize("switch", ["FGB_THREAD_KERNELS", "FGB_TILE_KERNELS"])
+@pytest.mark.parametrize("switch", ["FGB_THREAD_KERNELS", "FGB_THREAD_KERNELS FGB_SPLIT_KERNELS=0",
+                                    "FGB_TILE_KERNELS", "FGB_TILE_KERNELS FGB_NL_STAGE_CAP=64",
+                                    "FGB_TILE_KERNELS FGB_NL_KERNELS=0",
+                                    "FGB_TILE_KERNELS FGB_NL_QN=2 FGB_NL_QI=1"])
 def test_kernel_family_switches(switch):
     import os
     import subprocess
@@ -458,7 +485,9 @@ def test_kernel_family_switches(switch):
         pytest.skip("no CUDA device")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, PYTHONPATH=root)
-    env[switch] = "1"
+    for item in switch.split():
+        k, _, v = item.partition("=")
+        env[k] = v or "1"
     r = subprocess.run([sys.executable, "-c", KERNEL_SWITCH_CHECKS], env=env, cwd=root, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]

@@ -1,16 +1,18 @@
 """The allocation-free RDF entry point (fgb_rdf_noalloc), called through the C ABI, gives
 the same counts as the allocating fgb_rdf_compute path.
 
-It exists for callers that cannot allocate device memory while they run (graph-recorded
-work under an allocation ban, fixed-budget simulation steps, foreign memory pools); its
-working set is one static device array.  Two calls in a row on different frames check
-that nothing stale from the previous call leaks into the next.  This file is collected
-last so a stop-at-first-failure run has already run every other test."""
+It exists for callers that cannot allocate device memory while they run (simulation
+steps with a fixed memory budget, runtimes whose own pool owns the device); its working
+set is one static device array.  Two calls in a row on different frames check that
+nothing stale from the previous call leaks into the next; the second frame is also
+compared with the FP64 oracle directly.  This file is collected last so a
+stop-at-first-failure run has already run every other test."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -48,12 +50,14 @@ def test_noalloc_matches_allocating_path_twice(fgb):
          300, 4.0, 0.0),
         (W.Box.cube(24.0), W.small_random(72, 12000, W.Box.cube(24.0)), 97, 5.5, 0.3),
     ]
-    for box, x, bins, r_max, r_min in frames:
+    for k, (box, x, bins, r_max, r_min) in enumerate(frames):
         pts = torch.from_numpy(x).cuda()
         got = noalloc_counts(fgb, box, pts, bins, r_max, r_min)
         want = allocating_counts(fgb, box, pts, bins, r_max, r_min)
         assert np.array_equal(got, want)
         assert got.sum() > 0
+        if k == 1:
+            assert np.array_equal(got, oracle.rdf_counts(box, x, bins, r_max, r_min))
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(fgb):
