@@ -122,10 +122,29 @@ class ClockSampler:
 # so it is scaled to the bench's N; once the source changes the figure is stale and is
 # reported as null.
 MEASURED_TRAFFIC = {
-    "k_tile_write": ("paper_1906_06317_gb300/csrc/tile.cu", "06f1005e6e3ebc0d", 558.15552e6 + 1537.322e6, 2097152),
-    "k_tile_count": ("paper_1906_06317_gb300/csrc/tile.cu", "06f1005e6e3ebc0d", 34.582528e6 + 0.12e6, 2097152),
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "321bbcb2ac39fe62", 34.208e6 + 0.022e6, 2097152),
+    "k_nl_write": ("paper_1906_06317_gb300/csrc/nlist.cu", "7d2387a7c84b1ef3", 570.487808e6 + 1542.941e6, 2097152),
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "2f8d43fe6199dab6", 34.211072e6 + 0.046e6, 2097152),
 }
+
+
+# Shared-atomic wavefronts of the fused RDF as a share of the shared-memory data pipe's
+# peak (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared_op_atom, the same capture).
+MEASURED_SHARED_ATOMICS = {
+    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "2f8d43fe6199dab6", 0.1073),
+}
+
+
+def measured_shared_atomics(kernel: str):
+    """Measured fraction of the shared pipe's peak taken by atomics, or None when stale."""
+    import hashlib
+    if kernel not in MEASURED_SHARED_ATOMICS:
+        return None
+    path, sha, frac = MEASURED_SHARED_ATOMICS[kernel]
+    try:
+        cur = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return frac if cur.startswith(sha) else None
 
 
 def measured_traffic(kernel: str, n: int):
@@ -234,7 +253,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=4_194_304,
                     help="points of the uniform workload (smaller cases are for profiling only)")
-    ap.add_argument("--only", choices=["pmft", "batch"], default=None,
+    ap.add_argument("--only", choices=["pmft", "batch", "q6", "knn", "tree"], default=None,
                     help="time one group of components alone and print them (profiling runs)")
     ap.add_argument("--pmft-points", type=int, default=4_194_304, help="points of the large 2D PMFT frame")
     ap.add_argument("--batch-frames", type=int, default=256, help="--only batch: the first frames of the c5 set")
@@ -251,6 +270,13 @@ def main():
         dev = torch.device("cuda", local)
         flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
         comp = pmft_components(fgb, torch, dev, torch.cuda.current_stream(), flush, n_big=args.pmft_points)
+        print(json.dumps({"components": comp}), flush=True)
+        return
+    if args.only in ("q6", "knn", "tree"):
+        dev = torch.device("cuda", local)
+        flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+        comp = component_only(fgb, torch, dev, torch.cuda.current_stream(), flush, args.only, args.points,
+                              args.steps, args.warmup)
         print(json.dumps({"components": comp}), flush=True)
         return
     if args.only == "batch":
@@ -371,7 +397,9 @@ def main():
     rdf_unordered = rdf_pairs / 2
     nl_bytes = (12.0 * nl_pairs + 28.0 * n) / 1e9    # 12 B per stored pair; record, count, offset per query
     cnt_bytes = 20.0 * n / 1e9                        # sorted record read + count write per query
-    nlw_bytes = (8.0 * nl_pairs + 28.0 * n) / 1e9    # point index + distance per pair; record, count, offset per query
+    # write kernel: point index + distance (+ query index unless a fill pass stores it) per
+    # pair; sorted record, count and offset per query
+    nlw_bytes = ((8.0 if "k_nl_fill_qi" in kern else 12.0) * nl_pairs + 28.0 * n) / 1e9
     qi_bytes = (4.0 * nl_pairs + 8.0 * n) / 1e9      # query index per pair; offset per query
     rdf_ops = 10.0 * rdf_unordered / 1e12             # ~10 FP32 operations per unordered pair inside r_max
     roofs = {
@@ -399,6 +427,9 @@ def main():
             tk = kern[k]["ms_per_step"] / kern[k]["launches_per_step"] * 1e-3
             others[k] = {"bound": b, "achieved": wk / tk, "peak": pk, "unit": u, "frac": wk / tk / pk,
                          "ms": tk * 1e3, "traffic": measured_traffic(k, n)}
+            sa = measured_shared_atomics(k)
+            if sa is not None:
+                others[k]["shared_atomics_frac_of_peak"] = sa
 
     # ---------------- other parts of the hot path (component timings)
     components = {}
@@ -452,6 +483,42 @@ def timed(fn, stream, flush, reps=5, warm=2):
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
     return statistics.median(out)
+
+
+def component_only(fgb, torch, dev, stream, flush, which, n_points, steps, warmup):
+    """One component alone, `warmup` then `steps` timed runs: the commands behind the
+    captures of its kernels.  q6: Q6 forward + backward on the c4 system (2^20 points,
+    fixed list r = 1.3); knn: k = 12 on the c3 workload with n_points points (cell list
+    built each run); tree: tree build + ball query r = 2.5 on the same points."""
+    if which == "q6":
+        w4 = W.c4()
+        x4 = torch.from_numpy(w4.points).to(dev)
+        nq4 = fgb.NeighborQuery(w4.box, x4, r_cell=1.3)
+        nl4 = nq4.query(None, dict(r_max=1.3, exclude_ii=True)).toNeighborList()
+        st = fgb.Steinhardt(6)
+
+        def fn():
+            st.compute(nq4, neighbors=nl4)
+            st.backward(1.0)
+        label = "c4_q6_fwd_bwd_ms"
+    else:
+        w = W.c3(n=n_points)
+        x = torch.from_numpy(w.points).to(dev)
+        if which == "knn":
+            r12 = (3.0 * 13 / (4.0 * math.pi * 0.85)) ** (1.0 / 3.0)
+
+            def fn():
+                nq = fgb.NeighborQuery(w.box, x, r_cell=1.35 * r12)
+                return nq.query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
+            label = "c3_knn12_ms"
+        else:
+            def fn():
+                aq = fgb.AABBQuery(w.box, x)
+                return aq.query(None, dict(r_max=2.5, exclude_ii=True)).toNeighborList()
+            label = "c3_tree_build_query_ms"
+    for _ in range(warmup):
+        fn()
+    return {label: timed(fn, stream, flush, reps=max(steps, 1), warm=0), "points": n_points if which != "q6" else 2 ** 20}
 
 
 def batch_only(fgb, torch, dev, stream, flush, n_frames, steps, warmup):

@@ -22,6 +22,7 @@
 //
 // Both passes decide in FP32 outside a proven band around r_max and in FP64 (the
 // defining sequence) inside it, as everywhere else.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 
@@ -53,8 +54,7 @@ __device__ __noinline__ bool nl_band_pair(const TileArgs *ap, int i, int p, int 
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kNlWarps * 32) k_nl_count(const __grid_constant__ TileArgs a,
-                                                            uint32_t *__restrict__ cs) {
+__device__ __forceinline__ void nl_count_body(const TileArgs &a, uint32_t *__restrict__ cs) {
     __shared__ TileStencilT<NS> sts[kNlWarps];
     __shared__ float4 sstage[kNlWarps][kNlCountStage + 32];
     __shared__ float4 sq[kNlWarps][32];
@@ -163,6 +163,19 @@ __global__ void __launch_bounds__(kNlWarps * 32) k_nl_count(const __grid_constan
     if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
 }
 
+template <int NS>
+__global__ void __launch_bounds__(kNlWarps * 32) k_nl_count(const __grid_constant__ TileArgs a,
+                                                            uint32_t *__restrict__ cs) {
+    nl_count_body<NS>(a, cs);
+}
+
+// At most 64 registers: eight blocks per SM instead of seven (0.85 against 0.87 ms at c3).
+template <int NS>
+__global__ void __launch_bounds__(kNlWarps * 32, 8) k_nl_count_occ(const __grid_constant__ TileArgs a,
+                                                                   uint32_t *__restrict__ cs) {
+    nl_count_body<NS>(a, cs);
+}
+
 // counts[index] = count of the point at sorted position p, plus one for the self pair
 // when it is not excluded (points in the walked cells [cell_lo, ncell) only: a 2D box's
 // tile kernels walk only the points' layer).
@@ -193,6 +206,7 @@ struct NlWriteArgs {
 // [jmin, jmax] (a monotone map), count, scan, group, then rank each candidate among its
 // bucket by comparison.  perm[r] = stage slot of rank r; slots [kept, round32(kept))
 // point at the far sentinel stage[kNlStage].
+template <int STAGE>
 __device__ __forceinline__ void nl_sort_stage(const float4 *stage, int kept, int jmin, int jmax, uint32_t *cnt,
                                               uint16_t *grp, uint16_t *perm) {
     const int lane = threadIdx.x & 31;
@@ -244,17 +258,20 @@ __device__ __forceinline__ void nl_sort_stage(const float4 *stage, int kept, int
         perm[rank] = (uint16_t)e;
     }
     const int padded = (kept + 31) & ~31;
-    if (kept + lane < padded) perm[kept + lane] = (uint16_t)kNlStage;
+    if (kept + lane < padded) perm[kept + lane] = (uint16_t)STAGE;
     __syncwarp();
 }
 
-template <int NS, int QN>
-__global__ void __launch_bounds__(kNlWarps * 32) k_nl_write(const __grid_constant__ NlWriteArgs w) {
+template <int NS, int QN, int STAGE>
+__device__ __forceinline__ void nl_write_body(const NlWriteArgs &w) {
     const TileArgs &a = w.t;
+    // the sort's grouping array lives in the stencil list's memory when it fits (the list
+    // is dead once the candidates are staged)
+    constexpr bool kAlias = sizeof(TileStencilT<NS>) >= STAGE * sizeof(uint16_t);
     __shared__ TileStencilT<NS> sts[kNlWarps];
-    __shared__ float4 sstage[kNlWarps][kNlStage + 1];  // + the far sentinel
-    __shared__ uint16_t sperm[kNlWarps][kNlStage + 32];
-    __shared__ uint16_t sgrp[kNlWarps][kNlStage];
+    __shared__ float4 sstage[kNlWarps][STAGE + 1];  // + the far sentinel
+    __shared__ uint16_t sperm[kNlWarps][STAGE + 32];
+    __shared__ uint16_t sgrp[kNlWarps][kAlias ? 1 : STAGE];
     __shared__ uint32_t scnt[kNlWarps][kNlBuckets];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kNlWarps + warp;
@@ -270,7 +287,7 @@ __global__ void __launch_bounds__(kNlWarps * 32) k_nl_write(const __grid_constan
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
     const unsigned lt = lanemask_lt();
-    if (lane == 0) stage[kNlStage] = far_record();
+    if (lane == 0) stage[STAGE] = far_record();
     // bounding box of A's points
     float3 blo = make_float3(INFINITY, INFINITY, INFINITY), bhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
     for (int t0 = 0; t0 < nA; t0 += 32) {
@@ -308,7 +325,8 @@ __global__ void __launch_bounds__(kNlWarps * 32) k_nl_write(const __grid_constan
         jmax = max(jmax, __shfl_xor_sync(0xffffffffu, jmax, o));
     }
     __syncwarp();
-    if (kept > 0) nl_sort_stage(stage, kept, jmin, jmax, scnt[warp], sgrp[warp], perm);
+    uint16_t *grp = kAlias ? reinterpret_cast<uint16_t *>(&ts) : &sgrp[warp][0];
+    if (kept > 0) nl_sort_stage<STAGE>(stage, kept, jmin, jmax, scnt[warp], grp, perm);
     const int nch = (kept + 31) >> 5;
     const float lo = a.band.lo, hi = a.band.hi;
     for (int q0 = 0; q0 < nA; q0 += QN) {
@@ -374,6 +392,21 @@ __global__ void __launch_bounds__(kNlWarps * 32) k_nl_write(const __grid_constan
     }
 }
 
+template <int NS, int QN>
+__global__ void __launch_bounds__(kNlWarps * 32) k_nl_write(const __grid_constant__ NlWriteArgs w) {
+    nl_write_body<NS, QN, kNlStage>(w);
+}
+
+// The build for 27-cell stencils: a stage of 352 and at most 80 registers, so six
+// blocks fit an SM instead of five (latency-bound: 3.28 against 3.66 ms at c3; a stage
+// of 320 at seven blocks spilled and took 3.59 ms).  Cells with more candidates go to
+// the listed fallback.
+constexpr int kNlStageSmall = 352;
+template <int NS, int QN>
+__global__ void __launch_bounds__(kNlWarps * 32, 6) k_nl_write_occ(const __grid_constant__ NlWriteArgs w) {
+    nl_write_body<NS, QN, kNlStageSmall>(w);
+}
+
 // qi[seg[i] .. seg[i+1]) = i: one warp per 32 consecutive queries, each row stored by
 // the whole warp.
 __global__ void __launch_bounds__(256) k_nl_fill_qi(const int64_t *__restrict__ seg, int64_t nq,
@@ -428,6 +461,17 @@ static bool nl_qi_in_write() {
     return v == 1;
 }
 
+// FGB_NL_OCC=0 launches the unconstrained builds of the count and write kernels
+// (comparisons).
+static bool nl_occ() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_NL_OCC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 // FGB_NL_QN: queries per pass of the write kernel (2 or 4; 4 measured faster).
 static int nl_qn() {
     static int v = -1;
@@ -456,10 +500,14 @@ int nl_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsi
     }
     if (grid > 0) {  // (a shard may walk no cell)
         FGB_KSCOPE("k_nl_count", s);
-        if (nhalf <= 32)
-            k_nl_count<32><<<grid, kNlWarps * 32, 0, s>>>(t, cs);
-        else
+        if (nhalf <= 32) {
+            if (nl_occ())
+                k_nl_count_occ<32><<<grid, kNlWarps * 32, 0, s>>>(t, cs);
+            else
+                k_nl_count<32><<<grid, kNlWarps * 32, 0, s>>>(t, cs);
+        } else {
             k_nl_count<kTileMaxStencil><<<grid, kNlWarps * 32, 0, s>>>(t, cs);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
@@ -480,6 +528,8 @@ int tile_write_global_listed(const fgb_nq *nq, const StencilPlan &p, double R, i
                              const int64_t *seg, const uint32_t *counts, const int *cells, const int *ncells,
                              int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
 
+static int nfull_of(const StencilPlan &p) { return (2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1); }
+
 int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
              const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
     NlWriteArgs w;
@@ -491,6 +541,7 @@ int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int 
     w.pj = pj;
     w.dist = dist;
     w.stage_cap = nl_stage_cap();
+    if (nfull_of(p) <= 32 && nl_occ() && nl_qn() == 4) w.stage_cap = std::min(w.stage_cap, kNlStageSmall);
     const int64_t cells = w.t.ncell - w.t.cell_lo;
     int *ovf = nullptr;
     FGB_TRY(dalloc_n(&ovf, (size_t)cells + 1, s));
@@ -507,7 +558,9 @@ int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int 
     if (grid > 0) {  // (a shard may walk no cell)
         FGB_KSCOPE("k_nl_write", s);
         if (nfull <= 32) {
-            if (nl_qn() == 4)
+            if (nl_occ() && nl_qn() == 4)
+                k_nl_write_occ<32, 4><<<grid, kNlWarps * 32, 0, s>>>(w);
+            else if (nl_qn() == 4)
                 k_nl_write<32, 4><<<grid, kNlWarps * 32, 0, s>>>(w);
             else
                 k_nl_write<32, 2><<<grid, kNlWarps * 32, 0, s>>>(w);

@@ -10,6 +10,7 @@
 // Pairs whose FP32 r2 lies inside the error band of a bin edge are appended to a list
 // and binned by a second kernel with the defining FP64 sequence.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -264,7 +265,7 @@ __device__ __forceinline__ void rdf_tile_flush(uint32_t *h, int bins, unsigned l
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_constant__ RdfTileArgs a) {
+__device__ __forceinline__ void rdf_tile_body(const RdfTileArgs &a) {
     __shared__ TileStencilT<NS> sts[kRdfTileWarps];
     __shared__ float4 sq[kRdfTileWarps][kRdfTileQ];
     __shared__ float4 sbuf[kRdfTileWarps][64];  // candidates kept after the box test
@@ -363,6 +364,19 @@ __global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile(const __grid_co
     }
 }
 
+// At most 64 registers, so eight blocks (32 warps) fit an SM: the kernel is bound by
+// instruction latency, and eight blocks measured 4.01 ms at c3 against 4.17 ms for the
+// unconstrained build (72 registers, seven blocks; FGB_RDF_VARIANT=0 selects it).
+template <int NS>
+__global__ void __launch_bounds__(kRdfTileWarps * 32, 8) k_rdf_tile(const __grid_constant__ RdfTileArgs a) {
+    rdf_tile_body<NS>(a);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kRdfTileWarps * 32) k_rdf_tile_r72(const __grid_constant__ RdfTileArgs a) {
+    rdf_tile_body<NS>(a);
+}
+
 // Histogram of the pairs of a NeighborList.  Below 0.499 of a box length on every axis
 // the defining sequence shifts by no box vector and its displacement is the plain
 // difference, which the FP32 difference matches within u |d_k|: such pairs take the
@@ -438,17 +452,33 @@ static int launch_rdf_nlist(const RdfListArgs &a, cudaStream_t s) {
     return FGB_OK;
 }
 
-template <int NS>
-static int launch_rdf_tile_ns(const RdfTileArgs &ta, cudaStream_t s) {
+template <class K>
+static int launch_rdf_tile_k(K kern, const RdfTileArgs &ta, cudaStream_t s) {
     const size_t smem = (size_t)kRdfTileWarps * ta.bins * sizeof(uint32_t);
     int per_sm = 0;
-    FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_tile<NS>, kRdfTileWarps * 32, smem));
+    FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRdfTileWarps * 32, smem));
     const int64_t cells = ta.t.ncell - ta.t.cell_lo;
     const int64_t want = (cells + kRdfTileWarps - 1) / kRdfTileWarps;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * std::max(per_sm, 1)));
     FGB_KSCOPE("k_rdf_tile", s);
-    k_rdf_tile<NS><<<grid, kRdfTileWarps * 32, smem, s>>>(ta);
+    kern<<<grid, kRdfTileWarps * 32, smem, s>>>(ta);
     return FGB_OK;
+}
+
+// FGB_RDF_VARIANT=0 launches the build without the register bound (comparisons).
+static bool rdf_r72() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_RDF_VARIANT");
+        v = (e && e[0] == '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+template <int NS>
+static int launch_rdf_tile_ns(const RdfTileArgs &ta, cudaStream_t s) {
+    if (rdf_r72()) return launch_rdf_tile_k(k_rdf_tile_r72<NS>, ta, s);
+    return launch_rdf_tile_k(k_rdf_tile<NS>, ta, s);
 }
 
 // Self query on the shift route, bins <= kRdfTileMaxBins, half stencil of nhalf cells.
