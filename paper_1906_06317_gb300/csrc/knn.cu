@@ -306,12 +306,76 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(KnnArgs a) {
     }
 }
 
-// Exact ranking for flagged queries: candidates whose FP32 r2 is within the threshold
-// get their FP64 r2 and are ranked by (r2, j) in double precision.
+// Exact ranking for flagged queries (near ties in FP32): candidates whose FP32 r2 is
+// within the threshold get their FP64 r2 and are ranked by (r2, j) in double precision.
+// A warp per flagged query: the lanes split the stencil's cells,
+// list every candidate inside the threshold with its FP64 r2 in shared memory, and each
+// listed candidate's rank by (r2, j) is counted against the others; ranks below m are
+// written.  A query with more than kExactCap such candidates keeps the serial walk.
+constexpr int kExactCap = 128;
+constexpr int kExactWarps = 4;
+
 template <int KT>
-__global__ void __launch_bounds__(64) k_knn_exact(KnnArgs a) {
+__device__ __noinline__ void knn_exact_serial(const KnnArgs &a, int64_t t, int s, float thr) {
+    const float4 q = a.qs[t];
+    const int i = __float_as_int(q.w);
+    int cx, cy, cz;
+    cell_coords(a.qcell[t], a.nc, cx, cy, cz);
+    const int excl = a.exclude ? i : -1;
+    const int m = a.counts[i];
+    bool all_full;
+    const Stencil S = knn_stencil(a, s, all_full);
+    double br[KT];
+    int bj[KT];
+#pragma unroll
+    for (int q2 = 0; q2 < KT; ++q2) {
+        br[q2] = INFINITY;
+        bj[q2] = 0x7fffffff;
+    }
+    for_stencil(S, cx, cy, cz, make_float3(q.x, q.y, q.z), false, [&](int cell, float qx, float qy, float qz, bool) {
+        const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
+        for (uint32_t p = beg; p < end; ++p) {
+            const float4 c = __ldg(a.pts + p);
+            const int j = __float_as_int(c.w);
+            if (j == excl) continue;
+            const float3 d = cand_disp(S, a.bf, c, qx, qy, qz);
+            const float r2 = r2_f32(d.x, d.y, d.z);
+            if (r2 > thr) continue;
+            const double e = exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j);
+            if (e < br[KT - 1] || (e == br[KT - 1] && j < bj[KT - 1])) {
+                double cr = e;
+                int cj = j;
+#pragma unroll
+                for (int q2 = 0; q2 < KT; ++q2) {
+                    const bool less = cr < br[q2] || (cr == br[q2] && cj < bj[q2]);
+                    const double tr = less ? br[q2] : cr;
+                    const int tj = less ? bj[q2] : cj;
+                    br[q2] = less ? cr : br[q2];
+                    bj[q2] = less ? cj : bj[q2];
+                    cr = tr;
+                    cj = tj;
+                }
+            }
+        }
+    });
+    const int64_t row = (int64_t)i * a.stride;
+#pragma unroll
+    for (int q2 = 0; q2 < KT; ++q2)
+        if (q2 < m) {
+            a.qi_out[row + q2] = i;
+            a.pj_out[row + q2] = bj[q2];
+            a.d_out[row + q2] = (float)sqrt(br[q2]);
+        }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kExactWarps * 32) k_knn_exact_warp(KnnArgs a) {
+    __shared__ double se[kExactWarps][kExactCap];
+    __shared__ int sj[kExactWarps][kExactCap];
+    __shared__ int scnt[kExactWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nflag = min(*a.flag_count, a.flag_cap);
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nflag; f += gridDim.x * blockDim.x) {
+    for (int f = blockIdx.x * kExactWarps + warp; f < nflag; f += gridDim.x * kExactWarps) {
         const int4 fl = a.flags[f];
         const int64_t t = fl.x;
         const int s = fl.y;
@@ -324,47 +388,70 @@ __global__ void __launch_bounds__(64) k_knn_exact(KnnArgs a) {
         const int m = a.counts[i];
         bool all_full;
         const Stencil S = knn_stencil(a, s, all_full);
-        double br[KT];
-        int bj[KT];
-#pragma unroll
-        for (int q2 = 0; q2 < KT; ++q2) {
-            br[q2] = INFINITY;
-            bj[q2] = 0x7fffffff;
+        // the stencil's offsets as a box [lo, hi] per axis (for_stencil's enumeration)
+        int lo[3], hi[3];
+        const int cc[3] = {cx, cy, cz};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = (S.mode != 0 && S.full[k]) ? -cc[k] : -S.s[k];
+            hi[k] = (S.mode != 0 && S.full[k]) ? S.nc[k] - 1 - cc[k] : S.s[k];
         }
-        for_stencil(S, cx, cy, cz, make_float3(q.x, q.y, q.z), false, [&](int cell, float qx, float qy, float qz, bool) {
+        const int wx = hi[0] - lo[0] + 1, wy = hi[1] - lo[1] + 1, wz = hi[2] - lo[2] + 1;
+        if (lane == 0) scnt[warp] = 0;
+        __syncwarp();
+        for (int o = lane; o < wx * wy * wz; o += 32) {
+            const int ox = o % wx + lo[0], oy = (o / wx) % wy + lo[1], oz = o / (wx * wy) + lo[2];
+            const int xx = wrap_cell(cx + ox, S.nc[0]), yy = wrap_cell(cy + oy, S.nc[1]),
+                      zz = wrap_cell(cz + oz, S.nc[2]);
+            const int cell = (zz * S.nc[1] + yy) * S.nc[0] + xx;
+            float qx, qy, qz;
+            if (S.mode == 0) {
+                const int twx = 2 * S.ts[0] + 1, twy = 2 * S.ts[1] + 1;
+                const float4 of = __ldg(S.off + ((oz + S.ts[2]) * twy + (oy + S.ts[1])) * twx + (ox + S.ts[0]));
+                qx = q.x - of.x;
+                qy = q.y - of.y;
+                qz = q.z - of.z;
+            } else {
+                const float fx = (float)ox, fy = (float)oy, fz = (float)oz;
+                qx = q.x - fmaf(fz, S.step[2].x, fmaf(fy, S.step[1].x, fx * S.step[0].x));
+                qy = q.y - fmaf(fz, S.step[2].y, fy * S.step[1].y);
+                qz = q.z - fz * S.step[2].z;
+            }
             const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
             for (uint32_t p = beg; p < end; ++p) {
                 const float4 c = __ldg(a.pts + p);
                 const int j = __float_as_int(c.w);
                 if (j == excl) continue;
                 const float3 d = cand_disp(S, a.bf, c, qx, qy, qz);
-                const float r2 = r2_f32(d.x, d.y, d.z);
-                if (r2 > thr) continue;
-                const double e = exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j);
-                if (e < br[KT - 1] || (e == br[KT - 1] && j < bj[KT - 1])) {
-                    double cr = e;
-                    int cj = j;
-#pragma unroll
-                    for (int q2 = 0; q2 < KT; ++q2) {
-                        const bool less = cr < br[q2] || (cr == br[q2] && cj < bj[q2]);
-                        const double tr = less ? br[q2] : cr;
-                        const int tj = less ? bj[q2] : cj;
-                        br[q2] = less ? cr : br[q2];
-                        bj[q2] = less ? cj : bj[q2];
-                        cr = tr;
-                        cj = tj;
-                    }
+                if (r2_f32(d.x, d.y, d.z) > thr) continue;
+                const int slot = atomicAdd(&scnt[warp], 1);
+                if (slot < kExactCap) {
+                    se[warp][slot] = exact_r2_idx(a.bd, a.q_orig, i, a.p_orig, j);
+                    sj[warp][slot] = j;
                 }
             }
-        });
-        const int64_t row = (int64_t)i * a.stride;
-#pragma unroll
-        for (int q2 = 0; q2 < KT; ++q2)
-            if (q2 < m) {
-                a.qi_out[row + q2] = i;
-                a.pj_out[row + q2] = bj[q2];
-                a.d_out[row + q2] = (float)sqrt(br[q2]);
+        }
+        __syncwarp();
+        const int n = scnt[warp];
+        if (n > kExactCap) {
+            if (lane == 0) knn_exact_serial<KT>(a, t, s, thr);
+        } else {
+            const int64_t row = (int64_t)i * a.stride;
+            for (int e = lane; e < n; e += 32) {
+                const double me = se[warp][e];
+                const int mj = sj[warp][e];
+                int rank = 0;
+                for (int k = 0; k < n; ++k) {
+                    const double oe = se[warp][k];
+                    rank += (oe < me || (oe == me && sj[warp][k] < mj)) ? 1 : 0;
+                }
+                if (rank < m) {
+                    a.qi_out[row + rank] = i;
+                    a.pj_out[row + rank] = mj;
+                    a.d_out[row + rank] = (float)sqrt(me);
+                }
             }
+        }
+        __syncwarp();
     }
 }
 
@@ -399,7 +486,7 @@ static void launch_knn(const KnnArgs &a, cudaStream_t s) {
     }
     {
         FGB_KSCOPE("k_knn_exact", s);
-        k_knn_exact<KT><<<num_sms() * 2, 64, 0, s>>>(a);
+        k_knn_exact_warp<KT><<<num_sms() * 4, kExactWarps * 32, 0, s>>>(a);
     }
 }
 
