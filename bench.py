@@ -38,7 +38,9 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 L2_BYTES = 129 * 2 ** 20
-ORACLE_SAMPLE = 65536  # queries of the workload the CPU oracle times per step
+ORACLE_SAMPLE = 1 << 20  # queries of the workload the CPU oracle times (cpu_baseline)
+ORACLE_BLOCKS = 4        # ... in this many equal blocks spread over the query indices
+REFERENCE_SAMPLE = 1 << 18  # queries per step of --impl reference
 
 
 def env_rank():
@@ -193,9 +195,17 @@ def measured_peaks():
 # ------------------------------------------------------------------------ oracle arm
 
 
-def oracle_rate(w, sample: int, threads: int):
-    """Pairs per second of the CPU oracle on queries [0, sample), with the O(N) cell-list
-    builds charged in proportion (sample / N)."""
+def oracle_blocks(n: int, sample: int, blocks: int):
+    """`blocks` equal ranges of query indices, `sample` queries in all, spread evenly over
+    [0, n) (the points are i.i.d., so each range is a uniform spatial sample)."""
+    blocks = max(1, min(blocks, sample))
+    size = sample // blocks
+    return [(k * n // blocks, k * n // blocks + size) for k in range(blocks)]
+
+
+def oracle_rate(w, sample: int, threads: int, blocks: int = 1):
+    """Pairs per second of the CPU oracle on `sample` queries (in `blocks` spread ranges),
+    with the O(N) cell-list builds charged in proportion (sample / N)."""
     import oracle
     p = w.params
     n = len(w.points)
@@ -204,14 +214,18 @@ def oracle_rate(w, sample: int, threads: int):
     c_rdf = oracle.Cells(w.box, w.points, p["rdf_r_max"])
     t_cells = time.perf_counter() - t0
     del c_nl, c_rdf
+    rg = oracle_blocks(n, sample, blocks)
+    pairs = 0
     t1 = time.perf_counter()
-    counts, _, _, _ = oracle.ball_query(w.box, w.points, p["r_max"], queries=(0, sample), threads=threads)
-    h = oracle.rdf_counts(w.box, w.points, p["rdf_bins"], p["rdf_r_max"], queries=(0, sample), threads=threads)
+    for q in rg:
+        counts, _, _, _ = oracle.ball_query(w.box, w.points, p["r_max"], queries=q, threads=threads)
+        h = oracle.rdf_counts(w.box, w.points, p["rdf_bins"], p["rdf_r_max"], queries=q, threads=threads)
+        pairs += int(counts.sum()) + int(h.sum())
     t_q = time.perf_counter() - t1
-    pairs = int(counts.sum()) + int(h.sum())
-    # each oracle call builds its own cell list over all N points; charge those builds
-    # only in proportion to the fraction of the workload the sample covers
-    t = t_q - 2 * t_cells * (1.0 - sample / n)
+    done = sum(b - a for a, b in rg)
+    # each oracle call builds its own cell list over all N points (two per block); charge
+    # those builds only in proportion to the fraction of the workload the sample covers
+    t = t_q - t_cells * (len(rg) - done / n)
     return pairs / t, pairs, t
 
 
@@ -221,14 +235,15 @@ def run_reference(args, rank, world):
     w = W.c3()
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_rate(w, ORACLE_SAMPLE // 8, threads)
+        oracle_rate(w, REFERENCE_SAMPLE // 8, threads)
     rates, times = [], []
     for _ in range(args.steps):
-        r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads)
+        r, pairs, t = oracle_rate(w, REFERENCE_SAMPLE, threads)
         rates.append(r)
         times.append(t)
     v = statistics.median(rates)
-    sample = f"queries [0, {ORACLE_SAMPLE}) of {len(w.points)} (ball r=2.5 + RDF 500 bins [0,5]); cell builds charged pro rata"
+    sample = (f"queries [0, {REFERENCE_SAMPLE}) of {len(w.points)} per step (ball r=2.5 + RDF 500 bins [0,5]); "
+              "cell builds charged pro rata")
     line = {"impl": "reference", "metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": v,
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "strong",
@@ -440,13 +455,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads)
-        r1, pairs1, t1 = oracle_rate(w, ORACLE_SAMPLE // 16, 1)
+        r, pairs, t = oracle_rate(w, ORACLE_SAMPLE, threads, ORACLE_BLOCKS)
+        r1, pairs1, t1 = oracle_rate(w, ORACLE_SAMPLE // 128, 1)
+        blocks = ", ".join(f"[{a}, {b})" for a, b in oracle_blocks(n, ORACLE_SAMPLE, ORACLE_BLOCKS))
         cpu = {"value": r, "unit": "pairs/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
-               "sample": f"queries [0, {ORACLE_SAMPLE}) of {n}: {pairs} pairs in {t:.1f} s "
-                         "(cell builds charged pro rata)",
+               "sample": f"queries {blocks} of {n}: {pairs} pairs in {t:.1f} s (cell builds charged pro rata)",
                "single_thread": {"value": r1, "unit": "pairs/s", "cores": 1,
-                                 "sample": f"queries [0, {ORACLE_SAMPLE // 16}) of {n}: {pairs1} pairs in {t1:.1f} s"}}
+                                 "sample": f"queries [0, {ORACLE_SAMPLE // 128}) of {n}: {pairs1} pairs in "
+                                           f"{t1:.1f} s"}}
 
     if rank == 0:
         line = {"metric": "neighbor pairs/s (cell-list query+RDF) at N=4M", "value": value, "unit": "pairs/s",
