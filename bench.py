@@ -320,15 +320,15 @@ def main():
 
     def step(x):
         nq = fgb.NeighborQuery(w.box, x, r_cell=p["r_max"])
+        # the RDF is asynchronous and the list query waits for its count pass to size the
+        # list: issuing the RDF first keeps the GPU busy through that wait
         if world > 1:
             # one frame split across the ranks by ranges of query cells; the counts and
             # the histogram are summed over NCCL
-            nl = shard.sharded_ball_query(nq, p["r_max"], rank, world, all_reduce=dist.all_reduce)
             shard.sharded_rdf(rdf, nq, rank, world, all_reduce=dist.all_reduce)
-            return nl
-        nl = nq.query(None, dict(r_max=p["r_max"], exclude_ii=True)).toNeighborList()
+            return shard.sharded_ball_query(nq, p["r_max"], rank, world, all_reduce=dist.all_reduce)
         rdf.compute(nq, reset=True)
-        return nl
+        return nq.query(None, dict(r_max=p["r_max"], exclude_ii=True)).toNeighborList()
 
     for _ in range(max(3, args.warmup)):
         nl = step(pts)

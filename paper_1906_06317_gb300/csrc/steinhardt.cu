@@ -16,6 +16,7 @@
 // times the gradient at u.
 // Spherical-harmonic helpers: fgb_ylm.cuh.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fgb_ball.cuh"
@@ -98,6 +99,70 @@ __global__ void __launch_bounds__(128) k_st_bwd_gather(BoxF b, const float *__re
     grad[k] = make_float3(scale * gx, scale * gy, scale * gz);
 }
 
+// The same gradient with the next neighbour's data (its index, Q_lm, q and bond count)
+// loaded before the current bond is computed, so the gathers of consecutive bonds
+// overlap instead of each waiting on the last.
+template <int L>
+__global__ void __launch_bounds__(128) k_st_bwd_gather_pf(BoxF b, const float *__restrict__ x,
+                                                          const int64_t *__restrict__ seg,
+                                                          const int32_t *__restrict__ pj, int64_t n,
+                                                          const float *__restrict__ q, const float2 *__restrict__ Q,
+                                                          const int32_t *__restrict__ nn, float scale,
+                                                          float3 *__restrict__ grad) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float pref = 4.f * (float)M_PI / (2 * L + 1);
+    const float qk = q[k];
+    const int nk = nn[k];
+    const float ck = (qk > 0.f && nk > 0) ? pref / (qk * (float)nk) : 0.f;
+    const float sgn = (L & 1) ? 1.f : -1.f;  // (-1)^(L-1)
+    float2 Qk[L + 1];
+#pragma unroll
+    for (int m = 0; m <= L; ++m) Qk[m] = Q[k * (L + 1) + m];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    const int64_t beg = seg[k], end = seg[k + 1];
+    int j = beg < end ? pj[beg] : 0;
+    float2 Qj[L + 1];
+    float qj = 0.f;
+    int nj = 0;
+    if (beg < end) {
+#pragma unroll
+        for (int m = 0; m <= L; ++m) Qj[m] = Q[(int64_t)j * (L + 1) + m];
+        qj = q[j];
+        nj = nn[j];
+    }
+    for (int64_t e = beg; e < end; ++e) {
+        const int jc = j;
+        float2 Qc[L + 1];
+#pragma unroll
+        for (int m = 0; m <= L; ++m) Qc[m] = Qj[m];
+        const float qc = qj;
+        const int nc = nj;
+        if (e + 1 < end) {  // the next neighbour's data, in flight during this bond
+            j = pj[e + 1];
+#pragma unroll
+            for (int m = 0; m <= L; ++m) Qj[m] = Q[(int64_t)j * (L + 1) + m];
+            qj = q[j];
+            nj = nn[j];
+        }
+        const float3 d = bond_f32(b, x, k, jc);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (!(r2 > 0.f)) continue;
+        const float inv = rsqrtf(r2);
+        const float3 u = make_float3(d.x * inv, d.y * inv, d.z * inv);
+        float A[L + 2], wr[L + 1], wi[L + 1];
+        legendre_row<L>(u.z, A);
+        powers<L>(u.x, u.y, wr, wi);
+        const float cj = (qc > 0.f && nc > 0) ? pref / (qc * (float)nc) : 0.f;
+        const float3 own = project(contract_grad<L>(A, wr, wi, Qk), u, inv);
+        const float3 nbr = project(contract_grad<L>(A, wr, wi, Qc), u, inv);
+        gx += sgn * cj * nbr.x - ck * own.x;
+        gy += sgn * cj * nbr.y - ck * own.y;
+        gz += sgn * cj * nbr.z - ck * own.z;
+    }
+    grad[k] = make_float3(scale * gx, scale * gy, scale * gz);
+}
+
 // Gradient, any neighbor list: one thread per pair, float atomics.
 template <int L>
 __global__ void __launch_bounds__(128) k_st_bwd_scatter(BoxF b, const float *__restrict__ x, const int32_t *__restrict__ qi,
@@ -128,6 +193,16 @@ __global__ void __launch_bounds__(128) k_st_bwd_scatter(BoxF b, const float *__r
     atomicAdd(grad + 3 * i + 2, -c * g.z);
 }
 
+// FGB_ST_PREFETCH=0 takes the gradient kernel without the prefetch (comparisons).
+static bool bwd_prefetch() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_ST_PREFETCH");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 template <int L>
 struct StLaunch {
     static void nlist(const BoxF &b, const float *x, const fgb_nlist *nl, float *q, float2 *Q, int32_t *nn,
@@ -147,11 +222,13 @@ struct StLaunch {
     static void bwd(const BoxF &b, const float *x, const fgb_nlist *nl, const float *q, const float2 *Q,
                     const int32_t *nn, float scale, float *grad, cudaStream_t s) {
         if (nl->symmetric) {
-            {
-                FGB_KSCOPE("k_st_bwd_gather", s);
+            FGB_KSCOPE("k_st_bwd_gather", s);
+            if (bwd_prefetch())
+                k_st_bwd_gather_pf<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(
+                    b, x, nl->segments, nl->pj, nl->n_query, q, Q, nn, scale, reinterpret_cast<float3 *>(grad));
+            else
                 k_st_bwd_gather<L><<<(unsigned)((nl->n_query + 127) / 128), 128, 0, s>>>(
                     b, x, nl->segments, nl->pj, nl->n_query, q, Q, nn, scale, reinterpret_cast<float3 *>(grad));
-            }
         } else {
             cudaMemsetAsync(grad, 0, sizeof(float) * 3 * nl->n_points, s);
             if (nl->n_pairs > 0)
