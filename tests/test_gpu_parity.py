@@ -443,7 +443,7 @@ def test_full_c2_steinhardt_and_c4_gradient_sampled(fgb):
 #   FGB_THREAD_KERNELS=1 (+ FGB_SPLIT_KERNELS=0: the single-lane count and write),
 #   FGB_TILE_KERNELS=1 (the staged-sort write; + FGB_NL_STAGE_CAP=64: most cells to the
 #   listed fallback; + FGB_NL_KERNELS=0: the earlier tile count and write;
-#   + FGB_NL_QN=2 FGB_NL_QI=1: two queries per pass, query index stored in the pass).
+#   + FGB_NL_QN=2 FGB_NL_QI=0: two queries per pass, query index filled by its own pass).
 KERNEL_SWITCH_CHECKS = r"""
 import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb
 dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
@@ -476,7 +476,7 @@ print('ok')
 @pytest.mark.parametrize("switch", ["FGB_THREAD_KERNELS", "FGB_THREAD_KERNELS FGB_SPLIT_KERNELS=0",
                                     "FGB_TILE_KERNELS", "FGB_TILE_KERNELS FGB_NL_STAGE_CAP=64",
                                     "FGB_TILE_KERNELS FGB_NL_KERNELS=0",
-                                    "FGB_TILE_KERNELS FGB_NL_QN=2 FGB_NL_QI=1"])
+                                    "FGB_TILE_KERNELS FGB_NL_QN=2 FGB_NL_QI=0"])
 def test_kernel_family_switches(switch):
     import os
     import subprocess
