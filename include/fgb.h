@@ -175,6 +175,34 @@ int fgb_nq_cells(const fgb_nq *nq, const float **sorted, const uint32_t **sorted
 int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
                  void *stream, fgb_nlist **out);
 
+/*
+ * The self ball query of fgb_nq_query (same Section; query_points = the NeighborQuery's
+ * own points, args->r_max > 0, args->num_neighbors = 0) without a host synchronisation:
+ * the list's arrays are allocated for `capacity` pairs up front (0: an estimate for
+ * uniformly spread points, n(n-1)·ball volume/box volume + 10 % + 8 per point), the
+ * count, scan and write passes are queued on `stream`, and the call returns.  The list
+ * is then pending: fgb_nlist_wait completes it, and every call that reads a list
+ * (fgb_nlist_size, fgb_nlist_arrays, fgb_nlist_escalations and the analyses that take a
+ * NeighborList) waits for it first.  Completing waits for the queued work; when the
+ * list turned out larger than `capacity`, or held a row longer than 128 in a cell whose
+ * candidates exceed the write kernel's stage, the write pass runs again by the
+ * synchronous route into arrays of the exact size (the result is the same list;
+ * fgb_nlist_wait reports that it happened).  The result is identical to fgb_nq_query's.
+ * nq must stay alive and unchanged until the list is completed or destroyed; destroying
+ * a pending list is allowed.  Queries without the cell-tile route (a tree NeighborQuery,
+ * grids with fewer than 2s+1 cells per axis, the thread-per-query kernels) run
+ * fgb_nq_query and return a complete list.  Errors: FGB_ERR_INVALID_ARG (NULL argument,
+ * not a ball query, capacity < 0), FGB_ERR_BOX_TOO_SMALL, FGB_ERR_OOM; errors of the
+ * queued work are reported by the call that completes the list.
+ */
+int fgb_nq_query_async(fgb_nq *nq, const fgb_query_args *args, int64_t capacity, void *stream,
+                       fgb_nlist **out);
+
+/* Completes a pending list (no-op for a complete one).  *rewritten (may be NULL) is set
+ * to 1 when the write pass had to run again (capacity too small, or a long row in a
+ * cell beyond the write kernel's stage), else 0. */
+int fgb_nlist_wait(fgb_nlist *nl, int32_t *rewritten);
+
 /* --------------------------------------------------------------- NeighborList */
 
 int fgb_nlist_size(const fgb_nlist *nl, int64_t *n_pairs, int64_t *n_query);

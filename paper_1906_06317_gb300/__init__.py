@@ -73,6 +73,8 @@ _SIGS = {
     "fgb_nq_dims": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "fgb_nq_cells": (_I32, [_P, _PP, _PP, _PP]),
     "fgb_nq_query": (_I32, [_P, _P, _I64, ctypes.POINTER(fgb_query_args), _P, _PP]),
+    "fgb_nq_query_async": (_I32, [_P, ctypes.POINTER(fgb_query_args), _I64, _P, _PP]),
+    "fgb_nlist_wait": (_I32, [_P, ctypes.POINTER(_I32)]),
     "fgb_nlist_size": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "fgb_nlist_arrays": (_I32, [_P, _PP, _PP, _PP, _PP, _PP]),
     "fgb_nlist_escalations": (_I32, [_P, ctypes.POINTER(_I64)]),
@@ -276,11 +278,42 @@ class Box:
 
 
 class NeighborList:
-    """Query results, sorted by (query index, point index) (ball) or by distance (kNN)."""
+    """Query results, sorted by (query index, point index) (ball) or by distance (kNN).
 
-    def __init__(self, handle, keep):
+    A list from NeighborQuery.query_async is pending until wait() (or the first read of
+    its sizes or arrays, which waits)."""
+
+    _LAZY = frozenset(("n_pairs", "n_query", "query_point_indices", "point_indices", "distances", "segments",
+                       "neighbor_counts", "escalations", "rewritten"))
+
+    def __init__(self, handle, keep, pending=False, on_complete=None):
         self._o = _Owned(handle, "fgb_nlist_destroy", keep)
         self._h = self._o.ptr
+        self._pending = pending
+        self._on_complete = on_complete
+        if not pending:
+            self.rewritten = False
+            self._fill()
+
+    def __getattr__(self, name):
+        if name in NeighborList._LAZY and self.__dict__.get("_pending"):
+            self.wait()
+            return self.__dict__[name]
+        raise AttributeError(name)
+
+    def wait(self) -> "NeighborList":
+        """Completes a pending list (fgb_nlist_wait); no-op for a complete one."""
+        if self.__dict__.get("_pending"):
+            r = _I32()
+            _check(lib().fgb_nlist_wait(self._h, ctypes.byref(r)))
+            self._pending = False
+            self.rewritten = bool(r.value)
+            self._fill()
+            if self._on_complete is not None:
+                self._on_complete(self.n_pairs)
+        return self
+
+    def _fill(self):
         L = lib()
         m, nq = _I64(), _I64()
         _check(L.fgb_nlist_size(self._h, ctypes.byref(m), ctypes.byref(nq)))
@@ -383,6 +416,24 @@ class NeighborQuery:
         h = ctypes.c_void_p()
         _check(lib().fgb_nq_query(self._h, qp, nq, ctypes.byref(qa), _stream(), ctypes.byref(h)))
         return NeighborList(h.value, keep)
+
+    def query_async(self, r_max: float, exclude_ii: bool = True, capacity: int = None) -> NeighborList:
+        """Self ball query queued on the current stream without a host synchronisation
+        (fgb_nq_query_async).  The list is pending until wait() or the first read of its
+        sizes or arrays.  capacity (pairs) defaults to 5 % above the last list of the
+        same r_max from this NeighborQuery, else to the library's estimate for uniformly
+        spread points; a list that does not fit is written again when completed."""
+        key = (float(r_max), bool(exclude_ii))
+        hints = self.__dict__.setdefault("_capacity_hints", {})
+        if capacity is None:
+            capacity = int(hints[key] * 1.05) + 1024 if key in hints else 0
+        qa = fgb_query_args(float(r_max), 0, int(bool(exclude_ii)))
+        h = ctypes.c_void_p()
+        _check(lib().fgb_nq_query_async(self._h, ctypes.byref(qa), int(capacity), _stream(), ctypes.byref(h)))
+
+        def remember(n_pairs, hints=hints, key=key):
+            hints[key] = n_pairs
+        return NeighborList(h.value, [self._o], pending=True, on_complete=remember)
 
 
 class AABBQuery(NeighborQuery):

@@ -1,4 +1,5 @@
 // Ball query (r_max) and the NeighborList handle.  See query.cu for the overview.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -488,9 +489,182 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     return st;
 }
 
+// Pairs of a self ball query on uniformly spread points, n (n - 1) v / V (v the ball's
+// volume, the disc's area in 2D), with a margin of 10 % plus 8 per point.
+static int64_t capacity_estimate(const fgb_nq *nq, double R) {
+    const double n = (double)nq->n;
+    const double v = nq->box.is2d ? M_PI * R * R : 4.0 / 3.0 * M_PI * R * R * R;
+    const double V = nq->box.is2d ? nq->box.p[0] * nq->box.p[1] : nq->box.p[0] * nq->box.p[1] * nq->box.p[2];
+    const double est = n * std::max(n - 1.0, 0.0) * v / V;
+    return (int64_t)std::min(1.1 * est + 8.0 * n + 1024.0, (double)((int64_t)1 << 40));
+}
+
+// The self ball query without host synchronisation: count, scan and write are queued on
+// s into arrays of `capacity` pairs; the status words (list size, longest row, FP64
+// decisions, error flag) are copied to a pinned slot and `done` recorded after them.
+// nlist_ready completes it.  Only the cell-tile route of the NeighborList kernels has
+// this form; the caller runs ball_query otherwise.
+static int ball_query_async(fgb_nq *nq, const fgb_query_args *args, int64_t capacity, cudaStream_t s,
+                            fgb_nlist *nl) {
+    const double R = args->r_max;
+    StencilPlan plan;
+    FGB_TRY(plan_stencil(nq, R, 0, s, &plan));
+    const int64_t n = nq->n;
+    if (capacity <= 0) capacity = capacity_estimate(nq, R);
+    nl->n_query = n;
+    nl->n_points = n;
+    nl->symmetric = 1;
+    nl->kind = 0;
+    nl->src = nq;
+    nl->r_max = R;
+    nl->exclude = args->exclude_ii ? 1 : 0;
+    nl->capacity = capacity;
+    QueryStatus *dst = nullptr;
+    int st = dalloc_n(&dst, 1, s);
+    st = st ? st : pinned_slot(&nl->hstatus);
+    if (st == FGB_OK && cudaEventCreateWithFlags(&nl->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        nl->done = nullptr;
+        st = fail(FGB_ERR_CUDA, "event creation failed");
+    }
+    nl->dstatus = dst;
+    st = st ? st : dalloc_n(&nl->counts, n, s);
+    st = st ? st : dalloc_n(&nl->segments, n + 1, s);
+    st = st ? st : dalloc_n(&nl->qi, capacity, s);
+    st = st ? st : dalloc_n(&nl->pj, capacity, s);
+    st = st ? st : dalloc_n(&nl->dist, capacity, s);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(nl->counts);
+    if (st == FGB_OK && cudaMemsetAsync(dst, 0, sizeof(QueryStatus), s) != cudaSuccess)
+        st = fail(FGB_ERR_CUDA, "memset failed");
+    if (st == FGB_OK && nq->box.is2d && cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s) != cudaSuccess)
+        st = fail(FGB_ERR_CUDA, "memset failed");
+    st = st ? st : nl_count(nq, plan, R, nl->exclude, &dst->esc, &dst->err, counts, s);
+    st = st ? st : scan_u32_i64(counts, nl->segments, n, &dst->maxcount, s);
+    st = st ? st
+            : nl_write(nq, plan, R, nl->exclude, &dst->err, nl->segments, counts, 0, n, nl->qi, nl->pj, nl->dist, s,
+                       capacity);
+    if (st == FGB_OK) {
+        QueryStatus *h = static_cast<QueryStatus *>(nl->hstatus);
+        cudaMemcpyAsync(h, dst, sizeof(QueryStatus), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&h->total, nl->segments + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(nl->done, s);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "asynchronous ball query: %s", cudaGetErrorString(e));
+    }
+    dfree(plan.table, s);
+    if (st == FGB_OK) nl->pending = 1;
+    return st;
+}
+
+// The waiting half: a list that did not fit its capacity, or held a row the
+// asynchronous fallback could not take, is written again by the synchronous route
+// (counts and segments are final by then).
+static int nlist_finish(fgb_nlist *nl) {
+    cudaStream_t s = nl->stream;
+    nl->pending = 0;
+    if (cudaEventSynchronize(nl->done) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        return fail(FGB_ERR_CUDA, "asynchronous ball query failed: %s", cudaGetErrorString(e));
+    }
+    const QueryStatus h = *static_cast<const QueryStatus *>(nl->hstatus);
+    pinned_release(nl->hstatus, nullptr);
+    cudaEventDestroy(nl->done);
+    nl->hstatus = nullptr;
+    nl->done = nullptr;
+    QueryStatus *dst = static_cast<QueryStatus *>(nl->dstatus);
+    int st = FGB_OK;
+    if (h.total >= ((int64_t)1 << 40))
+        st = fail(FGB_ERR_CAPACITY, "neighbor list of %lld pairs is too large", (long long)h.total);
+    const bool grow = h.total > nl->capacity;
+    if (st == FGB_OK && (grow || h.err)) {
+        fgb_nq *nq = nl->src;
+        if (grow) {
+            dfree(nl->qi, s);
+            dfree(nl->pj, s);
+            dfree(nl->dist, s);
+            nl->qi = nl->pj = nullptr;
+            nl->dist = nullptr;
+            st = dalloc_n(&nl->qi, h.total, s);
+            st = st ? st : dalloc_n(&nl->pj, h.total, s);
+            st = st ? st : dalloc_n(&nl->dist, h.total, s);
+            nl->capacity = h.total;
+        }
+        StencilPlan plan;
+        plan.table = nullptr;
+        st = st ? st : plan_stencil(nq, nl->r_max, 0, s, &plan);
+        if (st == FGB_OK && cudaMemsetAsync(&dst->err, 0, sizeof(int), s) != cudaSuccess)
+            st = fail(FGB_ERR_CUDA, "memset failed");
+        const int cap = (int)((h.maxcount + 3) & ~3u);
+        st = st ? st
+                : nl_write(nq, plan, nl->r_max, nl->exclude, &dst->err, nl->segments,
+                           reinterpret_cast<const uint32_t *>(nl->counts), std::max(cap, 4), nl->n_query, nl->qi,
+                           nl->pj, nl->dist, s);
+        int err = 0;
+        if (st == FGB_OK) {
+            cudaMemcpyAsync(&err, &dst->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+            const cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "ball query rewrite failed: %s", cudaGetErrorString(e));
+            else if (err) st = fail(FGB_ERR_CUDA, "ball query: count and write passes disagree (code %d)", err);
+        }
+        dfree(plan.table, s);
+        nl->repaired = 1;
+    }
+    dfree(nl->dstatus, s);
+    nl->dstatus = nullptr;
+    nl->n_pairs = h.total;
+    nl->escalations = (int64_t)h.esc;
+    return st;
+}
+
+int nlist_ready(const fgb_nlist *nl) {
+    if (!nl || !nl->pending) return FGB_OK;
+    return nlist_finish(const_cast<fgb_nlist *>(nl));
+}
+
 }  // namespace fgb
 
 using namespace fgb;
+
+extern "C" int fgb_nq_query_async(fgb_nq *nq, const fgb_query_args *args, int64_t capacity, void *stream,
+                                  fgb_nlist **out) {
+    clear_error();
+    if (!nq || !args || !out) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!(args->r_max > 0.0) || args->num_neighbors > 0 || !std::isfinite(args->r_max))
+        return fail(FGB_ERR_INVALID_ARG, "an asynchronous query is a ball query: r_max > 0, num_neighbors 0");
+    if (capacity < 0) return fail(FGB_ERR_INVALID_ARG, "capacity must be >= 0");
+    if (!(args->r_max < 0.5 * nq->box.wmin * (1.0 - 1e-5)))
+        return fail(FGB_ERR_BOX_TOO_SMALL, "r_max=%g must be below half the smallest box width (%g)", args->r_max,
+                    0.5 * nq->box.wmin);
+    bool async = nq->kind == 0 && nq->n > 0 && !nq->walk_set && nl_kernels_enabled() && tile_worth(nq) &&
+                 !force_thread_kernels();
+    if (async) {
+        StencilPlan plan;
+        FGB_TRY(plan_stencil_host(nq->box, nq->grid, args->r_max, 0, &plan, nullptr));
+        async = tile_ok(plan);
+    }
+    if (!async) return fgb_nq_query(nq, nullptr, 0, args, stream, out);
+    cudaStream_t s = as_stream(stream);
+    fgb_nlist *nl = new fgb_nlist();
+    memset(nl, 0, sizeof(*nl));
+    nl->stream = s;
+    const int st = ball_query_async(nq, args, capacity, s, nl);
+    if (st != FGB_OK) {
+        if (nl->done) cudaEventSynchronize(nl->done);
+        fgb_nlist_destroy(nl);
+        return st;
+    }
+    *out = nl;
+    return FGB_OK;
+}
+
+extern "C" int fgb_nlist_wait(fgb_nlist *nl, int32_t *rewritten) {
+    clear_error();
+    if (!nl) return fail(FGB_ERR_INVALID_ARG, "nlist is NULL");
+    FGB_TRY(nlist_ready(nl));
+    if (rewritten) *rewritten = nl->repaired;
+    return FGB_OK;
+}
 
 extern "C" int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_query, const fgb_query_args *args,
                             void *stream, fgb_nlist **out) {
@@ -532,6 +706,7 @@ extern "C" int fgb_nq_query(fgb_nq *nq, const float *query_points, int64_t n_que
 
 extern "C" int fgb_nlist_size(const fgb_nlist *nl, int64_t *n_pairs, int64_t *n_query) {
     if (!nl) return fail(FGB_ERR_INVALID_ARG, "nlist is NULL");
+    FGB_TRY(nlist_ready(nl));
     if (n_pairs) *n_pairs = nl->n_pairs;
     if (n_query) *n_query = nl->n_query;
     return FGB_OK;
@@ -540,6 +715,7 @@ extern "C" int fgb_nlist_size(const fgb_nlist *nl, int64_t *n_pairs, int64_t *n_
 extern "C" int fgb_nlist_arrays(const fgb_nlist *nl, const int32_t **qi, const int32_t **pj, const float **dist,
                                 const int64_t **segments, const int32_t **counts) {
     if (!nl) return fail(FGB_ERR_INVALID_ARG, "nlist is NULL");
+    FGB_TRY(nlist_ready(nl));
     if (qi) *qi = nl->qi;
     if (pj) *pj = nl->pj;
     if (dist) *dist = nl->dist;
@@ -550,6 +726,7 @@ extern "C" int fgb_nlist_arrays(const fgb_nlist *nl, const int32_t **qi, const i
 
 extern "C" int fgb_nlist_escalations(const fgb_nlist *nl, int64_t *n) {
     if (!nl || !n) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nl));
     *n = nl->escalations;
     return FGB_OK;
 }
@@ -626,6 +803,11 @@ extern "C" int fgb_nlist_from_arrays(int64_t n_query, int64_t n_points, const in
 
 extern "C" void fgb_nlist_destroy(fgb_nlist *nl) {
     if (!nl) return;
+    // a list still in flight: its status slot is reused once its copies have completed
+    // (the arrays' frees are ordered on the stream behind the kernels)
+    if (nl->hstatus) pinned_release(nl->hstatus, nl->done);
+    else if (nl->done) cudaEventDestroy(nl->done);
+    dfree(nl->dstatus, nl->stream);
     dfree(nl->qi, nl->stream);
     dfree(nl->pj, nl->stream);
     dfree(nl->dist, nl->stream);

@@ -170,6 +170,46 @@ void dfree(void *p, cudaStream_t s) {
     cudaFreeAsync(p, s);
 }
 
+// Pinned host slots (64 bytes each) that asynchronous calls copy their status words
+// into.  A released slot is handed out again once the event recorded after its last copy
+// has completed (the event is the slot's to destroy).
+namespace {
+std::mutex g_pmu;
+constexpr size_t kPinnedSlot = 64, kPinnedChunk = 64;
+struct PinnedFree {
+    void *p;
+    cudaEvent_t after;
+};
+std::vector<PinnedFree> g_pinned_free;
+}  // namespace
+
+int pinned_slot(void **p) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (size_t k = 0; k < g_pinned_free.size(); ++k) {
+        const PinnedFree f = g_pinned_free[k];
+        if (f.after && cudaEventQuery(f.after) != cudaSuccess) continue;
+        if (f.after) cudaEventDestroy(f.after);
+        g_pinned_free.erase(g_pinned_free.begin() + k);
+        *p = f.p;
+        return FGB_OK;
+    }
+    void *chunk = nullptr;
+    if (cudaHostAlloc(&chunk, kPinnedSlot * kPinnedChunk, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FGB_ERR_OOM, "pinned host allocation failed");
+    }
+    for (size_t k = 1; k < kPinnedChunk; ++k)
+        g_pinned_free.push_back(PinnedFree{static_cast<char *>(chunk) + k * kPinnedSlot, nullptr});
+    *p = chunk;
+    return FGB_OK;
+}
+
+void pinned_release(void *p, cudaEvent_t after) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_pinned_free.push_back(PinnedFree{p, after});
+}
+
 int set_memory_cache(size_t bytes) {
     std::lock_guard<std::mutex> lk(g_amu);
     g_cache_limit = bytes;

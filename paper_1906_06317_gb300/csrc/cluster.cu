@@ -254,6 +254,7 @@ extern "C" int fgb_cluster_compute(int64_t n, const fgb_nlist *nlist, const uint
                                    fgb_clusters **out) {
     clear_error();
     if (!out || !nlist) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     *out = nullptr;
     if (n < 0 || n >= ((int64_t)1 << 31) - 1) return fail(FGB_ERR_INVALID_ARG, "n out of range");
     if (nlist->n_query > n || nlist->n_points > n)

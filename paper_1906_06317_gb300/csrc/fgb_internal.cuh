@@ -38,6 +38,11 @@ int dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 int trim_memory();
 int set_memory_cache(size_t bytes);
+// A pinned host slot of 64 bytes for status words copied back by asynchronous calls;
+// pinned_release hands it back, to be reused once `after` (nullable, then owned) has
+// completed.
+int pinned_slot(void **p);
+void pinned_release(void *p, cudaEvent_t after);
 template <class T>
 int dalloc_n(T **p, size_t n, cudaStream_t s) {
     return dalloc(reinterpret_cast<void **>(p), n * sizeof(T), s);
@@ -167,7 +172,23 @@ struct fgb_nlist {
     int symmetric;
     int kind;  // 0 ball, 1 knn, 2 user arrays
     cudaStream_t stream;
+    // asynchronous ball query (fgb_nq_query_async) in flight until fgb_nlist_wait: the
+    // arrays hold `capacity` pairs; status words come back to `hstatus` (pinned) and
+    // `done` follows their copy
+    int pending, repaired;
+    fgb_nq *src;
+    double r_max;
+    int exclude;
+    int64_t capacity;
+    void *dstatus, *hstatus;
+    cudaEvent_t done;
 };
+
+namespace fgb {
+// Completes an asynchronous list (waits, checks, rewrites it when it did not fit); every
+// call that reads a list goes through it.  No-op for a complete list.
+int nlist_ready(const fgb_nlist *nl);
+}  // namespace fgb
 
 namespace fgb {
 
@@ -254,8 +275,12 @@ int tile_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, in
 bool nl_kernels_enabled();
 int nl_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,
              uint32_t *counts, cudaStream_t s);
+// capacity >= 0: the asynchronous form: cap (the longest row) is not known and the arrays
+// hold capacity pairs; nothing is written if seg[nqq] > capacity, and a row the stage
+// fallback cannot hold sets *err = 1 (the caller rewrites the list synchronously).
 int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
-             const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s);
+             const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s,
+             int64_t capacity = -1);
 
 // RDF bin parameters for an error bound G2 on r^2 (rdf.cu).
 struct BinParams;

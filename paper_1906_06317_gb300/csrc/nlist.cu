@@ -34,6 +34,7 @@ constexpr int kNlWarps = 4;
 constexpr int kNlCountStage = 256;  // other-cell candidates per staged batch (count)
 constexpr int kNlStage = 384;       // pruned full-stencil candidates of one cell (write)
 constexpr int kNlBuckets = 256;     // buckets of the per-cell index sort
+constexpr int kNlAsyncRowCap = 128; // longest row of the asynchronous form's fallback
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -200,6 +201,10 @@ struct NlWriteArgs {
     int *ovf_cells;  // cells whose pruned stencil exceeds the stage
     int *ovf_count;
     int stage_cap;   // <= kNlStage
+    // asynchronous query: nothing is written when the list (*total pairs) exceeds the
+    // arrays' capacity (total NULL: no limit)
+    const int64_t *total;
+    int64_t capacity;
 };
 
 // Exact ranks of the staged candidates by point index: bucket by the index's place in
@@ -276,6 +281,7 @@ __device__ __forceinline__ void nl_write_body(const NlWriteArgs &w) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kNlWarps + warp;
     if (A >= a.ncell) return;
+    if (w.total && __ldg(w.total) > w.capacity) return;  // (no cell is listed either)
     const int begA = (int)__ldg(a.cell_start + A);
     const int nA = (int)__ldg(a.cell_start + A + 1) - begA;
     if (nA == 0) return;
@@ -408,12 +414,12 @@ __global__ void __launch_bounds__(kNlWarps * 32, 6) k_nl_write_occ(const __grid_
 }
 
 // qi[seg[i] .. seg[i+1]) = i: one warp per 32 consecutive queries, each row stored by
-// the whole warp.
-__global__ void __launch_bounds__(256) k_nl_fill_qi(const int64_t *__restrict__ seg, int64_t nq,
+// the whole warp.  Nothing is stored when the list (seg[nq]) exceeds capacity.
+__global__ void __launch_bounds__(256) k_nl_fill_qi(const int64_t *__restrict__ seg, int64_t nq, int64_t capacity,
                                                     int32_t *__restrict__ qi) {
     const int lane = threadIdx.x & 31;
     const int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-    if (i0 >= nq) return;
+    if (i0 >= nq || __ldg(seg + nq) > capacity) return;
     const int m = (int)(nq - i0 < 32 ? nq - i0 : 32);
     const int64_t myseg = __ldg(seg + i0 + min(lane, m));  // lane r: start of row r
     const int64_t last = __ldg(seg + i0 + m);              // end of the warp's last row
@@ -531,7 +537,14 @@ int tile_write_global_listed(const fgb_nq *nq, const StencilPlan &p, double R, i
 static int nfull_of(const StencilPlan &p) { return (2 * p.s[0] + 1) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1); }
 
 int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int *err, const int64_t *seg,
-             const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
+             const uint32_t *counts, int cap, int64_t nqq, int32_t *qi, int32_t *pj, float *dist, cudaStream_t s,
+             int64_t capacity) {
+    // capacity >= 0: the asynchronous form (list size and longest row unknown on the host)
+    const bool async = capacity >= 0;
+    if (async) {
+        cap = kNlAsyncRowCap;
+        if (tile_write_smem(cap) > 160 * 1024) return fail(FGB_ERR_UNSUPPORTED, "asynchronous write: no fallback");
+    }
     NlWriteArgs w;
     w.t = tile_args(nq, p, R, exclude);
     w.t.err = err;
@@ -540,6 +553,8 @@ int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int 
     w.qi = nl_qi_in_write() ? qi : nullptr;
     w.pj = pj;
     w.dist = dist;
+    w.total = async ? seg + nqq : nullptr;
+    w.capacity = async ? capacity : INT64_MAX;
     w.stage_cap = nl_stage_cap();
     if (nfull_of(p) <= 32 && nl_occ() && nl_qn() == 4) w.stage_cap = std::min(w.stage_cap, kNlStageSmall);
     const int64_t cells = w.t.ncell - w.t.cell_lo;
@@ -577,12 +592,15 @@ int nl_write(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, int 
     if (st == FGB_OK && !w.qi && nqq > 0) {
         FGB_KSCOPE("k_nl_fill_qi", s);
         const int64_t warps = (nqq + 31) / 32;
-        k_nl_fill_qi<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(seg, nqq, qi);
+        k_nl_fill_qi<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(seg, nqq, w.capacity, qi);
         e = cudaGetLastError();
         if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "query index fill failed: %s", cudaGetErrorString(e));
     }
     // cells with more candidates than the stage: the earlier kernels, over the list
-    // (the row sort of the long-row route reads each row's query index, filled above)
+    // (the row sort of the long-row route reads each row's query index, filled above).
+    // The asynchronous form takes the shared-row kernel with rows of up to
+    // kNlAsyncRowCap entries; a longer row there is skipped and flagged (err = 1), and the
+    // waiting call rewrites the list by the synchronous route.
     if (st == FGB_OK && cap <= 128 && tile_write_smem(cap) <= 160 * 1024) {
         st = tile_write_listed(nq, p, R, exclude, err, seg, counts, cap, w.ovf_cells, w.ovf_count, qi, pj, dist, s);
     } else if (st == FGB_OK) {

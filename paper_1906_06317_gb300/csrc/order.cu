@@ -301,6 +301,7 @@ extern "C" int fgb_steinhardt_wl(fgb_steinhardt *st, int32_t normalize, float *w
 extern "C" int fgb_steinhardt_average(fgb_steinhardt *st, const fgb_nlist *nlist, float *q_out, void *stream) {
     clear_error();
     if (!st || !nlist) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     if (!st->Q) return fail(FGB_ERR_INVALID_ARG, "call fgb_steinhardt_compute first");
     if (nlist->n_query != st->n || nlist->n_points != st->n)
         return fail(FGB_ERR_INVALID_ARG, "the averaging needs a self neighbor list over the same points");
@@ -321,6 +322,7 @@ extern "C" int fgb_local_descriptors(const fgb_box *box, const float *points, co
                                      void *stream) {
     clear_error();
     if (!box || !points || !nlist) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     if (l_max < 0 || l_max > kLMax) return fail(FGB_ERR_INVALID_ARG, "l_max must be in [0, %d]", kLMax);
     if (nlist->n_pairs > 0 && !out) return fail(FGB_ERR_INVALID_ARG, "out is NULL");
     BoxHost b;

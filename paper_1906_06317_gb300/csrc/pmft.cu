@@ -547,6 +547,7 @@ extern "C" int fgb_pmftxy_compute(fgb_pmft *P, fgb_nq *nq, const float *query_po
                                   int64_t n_query, const fgb_nlist *nlist, int32_t reset, void *stream) {
     clear_error();
     if (!P || !nq) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     if (!nq->box.is2d) return fail(FGB_ERR_INVALID_ARG, "PMFT(x, y) needs a 2D box (Lz = 0)");
     if (n_query < 0 || (!query_points && n_query != nq->n))
         return fail(FGB_ERR_INVALID_ARG, "n_query must be the point count when query_points is NULL");

@@ -558,6 +558,7 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                                const fgb_nlist *nlist, int32_t reset, void *stream) {
     clear_error();
     if (!r || !nq) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     if (nq->kind != 0 && !nlist)
         return fail(FGB_ERR_UNSUPPORTED, "the fused RDF walks a cell list; pass a NeighborList from the tree query");
     cudaStream_t s = as_stream(stream);

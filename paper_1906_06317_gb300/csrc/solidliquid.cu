@@ -434,6 +434,7 @@ extern "C" int fgb_solid_liquid(const fgb_box *box, const float *points, const f
                                 int32_t *num_connections, void *stream, fgb_clusters **clusters_out) {
     clear_error();
     if (!box || !nlist || !clusters_out) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     *clusters_out = nullptr;
     if (l < 0 || l > kSlLMax) return fail(FGB_ERR_INVALID_ARG, "l must be in [0, %d]", kSlLMax);
     if (nlist->n_query != nlist->n_points) return fail(FGB_ERR_INVALID_ARG, "needs a self neighbor list");

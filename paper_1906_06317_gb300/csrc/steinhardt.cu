@@ -319,6 +319,7 @@ extern "C" int fgb_steinhardt_compute(fgb_steinhardt *st, fgb_nq *nq, const fgb_
                                       const fgb_query_args *qargs, float *q_out, void *stream) {
     clear_error();
     if (!st || !nq || (nq->n > 0 && !q_out)) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     cudaStream_t s = as_stream(stream);
     FGB_TRY(st_ensure(st, nq->n, s));
     st->last_nlist = nlist;
@@ -377,6 +378,7 @@ extern "C" int fgb_steinhardt_backward(fgb_steinhardt *st, fgb_nq *nq, const fgb
                                        float upstream, float *grad_out, void *stream) {
     clear_error();
     if (!st || !nq || !nlist || (nq->n > 0 && (!q || !grad_out))) return fail(FGB_ERR_INVALID_ARG, "NULL argument");
+    FGB_TRY(nlist_ready(nlist));
     if (!st->Q || st->n != nq->n) return fail(FGB_ERR_INVALID_ARG, "call fgb_steinhardt_compute first");
     if (st->averaged) return fail(FGB_ERR_UNSUPPORTED, "the backward pass is for q_l, not the averaged q_l");
     if (nlist->n_query != nq->n || nlist->n_points != nq->n)
