@@ -24,6 +24,7 @@
 namespace fgb {
 
 constexpr int kBtW = kBatchTileWarps;
+constexpr int kBtOwnCap = 512;  // candidates of a stencil with an owner table
 constexpr unsigned kFull = 0xffffffffu;
 
 // Copies a frame's arguments into the warp's shared slot.
@@ -135,7 +136,8 @@ __device__ __forceinline__ void bt_guard(const BatchTileArgs &a, const FrameTile
 // points carry their limit (k - qb) in `lim`.
 template <int NS>
 __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameTile &fr, int A, TileStencilT<NS> &ts,
-                                            float4 *qs, float4 *buf, int *lim, uint32_t *h, uint64_t &tests) {
+                                            uint8_t *ownbuf, float4 *qs, float4 *buf, int *lim, uint32_t *h,
+                                            uint64_t &tests) {
     const TileArgs &t = fr.r;
     const int lane = threadIdx.x & 31;
     const int begA = (int)__ldg(t.cell_start + A);
@@ -146,6 +148,11 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
     __syncwarp();
     const int n = tile_stencil(t, cx, cy, cz, true, ts);
     const int total = ts.pre[n];
+    const uint8_t *own = nullptr;
+    if (total <= kBtOwnCap) {
+        tile_owners(ts, n, ownbuf);
+        own = ownbuf;
+    }
     const unsigned lt = lanemask_lt();
     // a candidate farther than this from the queries' bounding box reaches none of them
     const float reach2 = fr.P.rmax_hi * (1.0f + 1e-5f);
@@ -162,7 +169,7 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
         int cnt = 0;
         for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
-            const TileCand c = tile_load(t, ts, n, total, k);
+            const TileCand c = tile_load_own(t, ts, own, n, total, k);
             const bool keep = k < total && (k < nA || box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2);
             const unsigned m = __ballot_sync(kFull, keep);
             if (keep) {
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
     __shared__ float4 sq[kBtW][32];
     __shared__ float4 sbuf[kBtW][64];  // kept candidates
     __shared__ int slim[kBtW][64];     // their query limits
+    __shared__ uint8_t sown[kBtW][kBtOwnCap];
     extern __shared__ uint32_t shist[];  // kBtW * bins
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *h = shist + warp * a.bins;
@@ -218,7 +226,8 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
             bt_load_frame(a.ft + w.x, &fr);
             cur = w.x;
         }
-        for (int c = w.y; c < w.z; ++c) bt_rdf_cell<NS>(a, fr, c, sts[warp], sq[warp], sbuf[warp], slim[warp], h, tests);
+        for (int c = w.y; c < w.z; ++c)
+            bt_rdf_cell<NS>(a, fr, c, sts[warp], sown[warp], sq[warp], sbuf[warp], slim[warp], h, tests);
     }
     if (cur >= 0) bt_flush(h, a.bins, a.counts + (int64_t)fr.f * a.bins);
 }
@@ -248,8 +257,10 @@ __device__ __forceinline__ void bt_drain(int n, const float4 *bond, float *acc) 
     const int prev = __shfl_up_sync(kFull, s, 1), next = __shfl_down_sync(kFull, s, 1);
     const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != s);
     const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of the run
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    // steps beyond the longest run of bonds add nothing to a row: stop there (same sums,
+    // same order; the lanes without a bond form a run of their own that no row takes)
+    const int longest = (int)__reduce_max_sync(kFull, have ? (unsigned)(lane - start + 1) : 1u);
+    for (int d = 1; d < longest; d <<= 1) {
         const bool take = lane - d >= start;
 #pragma unroll
         for (int m = 0; m <= L; ++m) {
@@ -284,7 +295,8 @@ __device__ __forceinline__ void bt_drain(int n, const float4 *bond, float *acc) 
 
 template <int L, int NS>
 __device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTile &fr, int A, TileStencilT<NS> &ts,
-                                          float4 *qs, float4 *buf, float4 *bond, float *acc, int *snn, int &nesc) {
+                                          uint8_t *ownbuf, float4 *qs, float4 *buf, float4 *bond, float *acc, int *snn,
+                                          int &nesc) {
     constexpr int NC = 2 * (L + 1);
     const TileArgs &t = fr.b;
     const int lane = threadIdx.x & 31;
@@ -296,6 +308,11 @@ __device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTil
     __syncwarp();
     const int n = tile_stencil(t, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
+    const uint8_t *own = nullptr;
+    if (total <= kBtOwnCap) {
+        tile_owners(ts, n, ownbuf);
+        own = ownbuf;
+    }
     const float lo = t.band.lo, hi = t.band.hi;
     const float reach2 = hi * (1.0f + 1e-5f);
     const unsigned lt = lanemask_lt();
@@ -314,7 +331,7 @@ __device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTil
         int kept = 0, qn = 0;
         for (int base = 0; base < total || kept > 0; base += 32) {
             if (base < total) {
-                const TileCand c = tile_load(t, ts, n, total, base + lane);
+                const TileCand c = tile_load_own(t, ts, own, n, total, base + lane);
                 const bool keep = base + lane < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
                 const unsigned m = __ballot_sync(kFull, keep);
                 if (keep) buf[kept + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
@@ -381,6 +398,7 @@ __global__ void __launch_bounds__(kBtW * 32) k_batch_qtile(const __grid_constant
     __shared__ float4 sbond[kBtW][64];  // queued bonds: displacement, query slot
     __shared__ int snn[kBtW][32];
     __shared__ float sacc[kBtW][32 * 2 * (L + 1)];  // per query: sums of Re, Im Y~_Lm
+    __shared__ uint8_t sown[kBtW][kBtOwnCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FrameTile &fr = sfr[warp];
     int cur = -1, nesc = 0;
@@ -391,7 +409,8 @@ __global__ void __launch_bounds__(kBtW * 32) k_batch_qtile(const __grid_constant
             cur = w.x;
         }
         for (int c = w.y; c < w.z; ++c)
-            bt_q_cell<L, NS>(a, fr, c, sts[warp], sq[warp], sbuf[warp], sbond[warp], sacc[warp], snn[warp], nesc);
+            bt_q_cell<L, NS>(a, fr, c, sts[warp], sown[warp], sq[warp], sbuf[warp], sbond[warp], sacc[warp], snn[warp],
+                             nesc);
     }
     nesc = __reduce_add_sync(kFull, nesc);
     if (lane == 0 && nesc) atomicAdd(a.qesc, (unsigned long long)nesc);

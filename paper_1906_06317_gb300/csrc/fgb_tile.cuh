@@ -133,6 +133,46 @@ __device__ __forceinline__ TileCand tile_load(const TileArgs &a, const TS &ts, i
     return c;
 }
 
+// Owner table of a stencil list: own[k] = the stencil cell that holds candidate k, one
+// byte each (at most kTileMaxStencil cells), for k < pre[n].  Built once per query cell,
+// it turns each candidate's lookup into a table read instead of a binary search over the
+// prefix sums.
+template <class TS>
+__device__ __forceinline__ void tile_owners(const TS &ts, int n, uint8_t *own) {
+    const int lane = threadIdx.x & 31;
+    for (int o = lane; o < n; o += 32) {
+        const int b = ts.pre[o], e = ts.pre[o + 1];
+        for (int k = b; k < e; ++k) own[k] = (uint8_t)o;
+    }
+    __syncwarp();
+}
+
+// tile_load with the owner table (own == nullptr: the binary search).
+template <class TS>
+__device__ __forceinline__ TileCand tile_load_own(const TileArgs &a, const TS &ts, const uint8_t *own, int n, int total,
+                                                  int k) {
+    if (!own) return tile_load(a, ts, n, total, k);
+    TileCand c;
+    if (k < total) {
+        const int o = own[k];
+        const int p = ts.beg[o] + (k - ts.pre[o]);
+        const float4 r = __ldg(a.pts + p);
+        const float4 of = ts.off[o];
+        c.x = r.x + of.x;
+        c.y = r.y + of.y;
+        c.z = r.z + of.z;
+        c.j = __float_as_int(r.w);
+        c.p = p;
+        c.o = o;
+    } else {
+        c.x = c.y = c.z = 1e30f;
+        c.j = -1;
+        c.p = 0x7fffffff;
+        c.o = -1;
+    }
+    return c;
+}
+
 // Lanes hold queries, candidates are broadcast: a query block of nq <= 32 queries of the
 // cell is spread over qpl = next power of two >= nq lanes, and the warp's 32/qpl lane
 // groups take different candidates of the staged chunk in each round.

@@ -35,6 +35,7 @@ constexpr int kNlCountStage = 256;  // other-cell candidates per staged batch (c
 constexpr int kNlStage = 384;       // pruned full-stencil candidates of one cell (write)
 constexpr int kNlBuckets = 256;     // buckets of the per-cell index sort
 constexpr int kNlAsyncRowCap = 128; // longest row of the asynchronous form's fallback
+constexpr int kNlOwnCap = 512;      // half-stencil candidates of a cell with an owner table
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -59,6 +60,7 @@ __device__ __forceinline__ void nl_count_body(const TileArgs &a, uint32_t *__res
     __shared__ TileStencilT<NS> sts[kNlWarps];
     __shared__ float4 sstage[kNlWarps][kNlCountStage + 32];
     __shared__ float4 sq[kNlWarps][32];
+    __shared__ uint8_t sown[kNlWarps][kNlOwnCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kNlWarps + warp;
     if (A >= a.ncell) return;
@@ -70,6 +72,11 @@ __device__ __forceinline__ void nl_count_body(const TileArgs &a, uint32_t *__res
     TileStencilT<NS> &ts = sts[warp];
     const int n = tile_stencil(a, cx, cy, cz, true, ts);  // A first, with nA candidates
     const int total = ts.pre[n];
+    const uint8_t *own = nullptr;
+    if (total <= kNlOwnCap) {
+        tile_owners(ts, n, sown[warp]);
+        own = sown[warp];
+    }
     float4 *stage = sstage[warp];
     float4 *qs = sq[warp];
     const float lo = a.band.lo, hi = a.band.hi;
@@ -115,7 +122,7 @@ __device__ __forceinline__ void nl_count_body(const TileArgs &a, uint32_t *__res
             int kept = 0;
             while (base < total && kept <= kNlCountStage - 32) {
                 const int k = base + lane;
-                const TileCand c = tile_load(a, ts, n, total, k);
+                const TileCand c = tile_load_own(a, ts, own, n, total, k);
                 const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep) stage[kept + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.p));
@@ -293,6 +300,13 @@ __device__ __forceinline__ void nl_write_body(const NlWriteArgs &w) {
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
     const unsigned lt = lanemask_lt();
+    // the owner table lives in the order array's memory (the sort writes it after staging)
+    constexpr int kOwn = (STAGE + 32) * (int)sizeof(uint16_t);
+    const uint8_t *own = nullptr;
+    if (total <= kOwn) {
+        tile_owners(ts, n, reinterpret_cast<uint8_t *>(perm));
+        own = reinterpret_cast<const uint8_t *>(perm);
+    }
     if (lane == 0) stage[STAGE] = far_record();
     // bounding box of A's points
     float3 blo = make_float3(INFINITY, INFINITY, INFINITY), bhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
@@ -307,7 +321,7 @@ __device__ __forceinline__ void nl_write_body(const NlWriteArgs &w) {
     const float reach2 = a.band.hi * (1.0f + 1e-5f);
     int kept = 0, jmin = INT_MAX, jmax = -1;
     for (int base = 0; base < total; base += 32) {
-        const TileCand c = tile_load(a, ts, n, total, base + lane);
+        const TileCand c = tile_load_own(a, ts, own, n, total, base + lane);
         const bool keep = base + lane < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (kept + __popc(m) > w.stage_cap) {

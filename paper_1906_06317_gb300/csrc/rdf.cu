@@ -188,6 +188,7 @@ __global__ void k_rdf_escalated(RdfArgs a) {
 
 constexpr int kRdfTileWarps = 4;
 constexpr int kRdfTileQ = 32;          // queries staged per pass
+constexpr int kRdfOwnCap = 1024;       // candidates of a stencil with an owner table
 constexpr int kRdfTileMaxBins = 1024;  // private histogram of every warp
 
 struct RdfTileArgs {
@@ -269,6 +270,7 @@ __device__ __forceinline__ void rdf_tile_body(const RdfTileArgs &a) {
     __shared__ TileStencilT<NS> sts[kRdfTileWarps];
     __shared__ float4 sq[kRdfTileWarps][kRdfTileQ];
     __shared__ float4 sbuf[kRdfTileWarps][64];  // candidates kept after the box test
+    __shared__ uint8_t sown[kRdfTileWarps][kRdfOwnCap];  // owner table of the stencil
     extern __shared__ uint32_t shist[];  // kRdfTileWarps * bins
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *h = shist + warp * a.bins;
@@ -296,6 +298,11 @@ __device__ __forceinline__ void rdf_tile_body(const RdfTileArgs &a) {
         __syncwarp();
         const int n = tile_stencil(a.t, cx, cy, cz, true, ts);
         const int total = ts.pre[n];
+        const uint8_t *own = nullptr;
+        if (total <= kRdfOwnCap) {
+            tile_owners(ts, n, sown[warp]);
+            own = sown[warp];
+        }
         for (int qb = 0; qb < nA; qb += kRdfTileQ) {
             const int nq = min(kRdfTileQ, nA - qb);
             __syncwarp();
@@ -314,7 +321,7 @@ __device__ __forceinline__ void rdf_tile_body(const RdfTileArgs &a) {
                 }
                 tests += 32u * (unsigned)nq;
                 const int k = base + lane;
-                const TileCand c = tile_load(a.t, ts, n, nA, k);
+                const TileCand c = tile_load_own(a.t, ts, own, n, nA, k);
                 rdf_tile_rounds<true>(a, qs, nq, c, k < nA ? k - qb : 0, h);
             }
             // the other cells: candidates out of reach of the whole pass are dropped, the
@@ -322,7 +329,7 @@ __device__ __forceinline__ void rdf_tile_body(const RdfTileArgs &a) {
             int cnt = 0;
             for (int base = nA; base < total; base += 32) {
                 const int k = base + lane;
-                const TileCand c = tile_load(a.t, ts, n, total, k);
+                const TileCand c = tile_load_own(a.t, ts, own, n, total, k);
                 const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep) buf[cnt + __popc(m & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));

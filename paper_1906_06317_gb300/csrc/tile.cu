@@ -796,15 +796,19 @@ int sort_segments(const int64_t *seg, int64_t nq, int cap, int64_t npoints, int3
 
 // ------------------------------------------------------------------ k nearest
 
-// kNN by radius: every candidate within the stencil's covered radius r0 is collected as
-// (r2 bits, index) into a 64-slot row per query, the row is sorted (bitonic network
-// across the warp), and the first m become the answer when the ranking is certain:
-// every gap between neighbours among the first m+1 exceeds 2 delta and, if fewer than
-// m+1 were found, the m-th sits more than 2 delta inside r0^2.  Other queries (too few
-// points within r0, too many for a row, or a near tie) are listed for the
-// thread-per-query kernel.
+// kNN by radius: every candidate within a collection radius rc <= r0 (the stencil's
+// covered radius) is gathered as (r2 bits, index) into a 64-slot row per query, the row
+// is sorted (bitonic network across the warp: one entry per lane up to 32, two up to
+// 64), and the first m become the answer when the ranking is certain: every gap between
+// neighbours among the first m+1 exceeds 2 delta and, if only m were found, the m-th
+// sits more than 2 delta inside rc^2 (everything not gathered lies at rc or beyond, and
+// inside r0 nothing is missed).  rc is set per query cell so that the stencil's mean
+// density puts about m + 12 points inside it.  Other queries (fewer than m within rc,
+// more than 64, or a near tie) are listed for the warp-per-query kernel.
 struct KnnTile {
-    float r0sq;      // collect candidates with FP32 r2 < r0sq (r0 = covered radius)
+    float r0sq;      // the covered radius r0, squared (collection radii stay below it)
+    float cnum;      // rc^dim = cnum / (candidates of the stencil): m + 12 expected inside
+    int dim;         // 3, or 2 for a 2D box (cnum then gives rc^2)
     float delta;     // FP32 error bound on r2 at r0
     int k;
     int stride;      // output row length m
@@ -815,28 +819,112 @@ struct KnnTile {
     int *list_count;
 };
 
-template <int G>
-__device__ __forceinline__ void knn_chunk(const float4 *sp, float4 Q, int excl, float r0sq, int *rowcnt, uint2 *myrow) {
-#pragma unroll 4
-    for (int r = 0; r < 32 / G; ++r) {
-        const float4 c = sp[r * G];
-        const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
-        if (r2 < r0sq) {
-            const int j = __float_as_int(c.w);
-            if (j != excl) {
-                const int pos = atomicAdd(rowcnt, 1);
-                if (pos < 64) myrow[pos] = make_uint2(__float_as_uint(r2), (uint32_t)j);
+// Sorts one gathered row (cnt <= 64 entries of (r2 bits, index) in shared memory) and
+// writes its first m when the ranking is certain (the rule above); else lists the query
+// (sorted position t) for the warp-per-query kernel.
+__device__ __forceinline__ void knn_finish_row(const uint2 *row, int cnt, int m, float rcsq, const KnnTile &K, int iL,
+                                               int t) {
+    const int lane = threadIdx.x & 31;
+    bool ok = cnt >= m && cnt <= 64;
+    const float twod = 2.f * K.delta;
+    if (ok && cnt <= 32) {
+        // one 32-bit key per lane: the r2 bits with the low five replaced by the row slot
+        // (r2 >= 0, so the bits order as the values).  Keys of distinct truncated r2
+        // order as the true r2; equal truncated r2 is flagged as a tie below.
+        uint32_t key = lane < cnt ? ((row[lane].x & ~31u) | (uint32_t)lane) : 0xffffffffu;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+            const bool asc = (lane & kk) == 0;
+#pragma unroll
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                const uint32_t k0 = __shfl_xor_sync(0xffffffffu, key, jj);
+                const bool takemin = ((lane & jj) == 0) == asc;
+                if ((k0 < key) == takemin) key = k0;
             }
         }
+        const uint2 e0 = lane < cnt ? row[key & 31u] : make_uint2(0xffffffffu, 0u);
+        const float f0 = __uint_as_float(e0.x);
+        const float fnext = __shfl_down_sync(0xffffffffu, f0, 1);
+        const uint32_t knext = __shfl_down_sync(0xffffffffu, key, 1);
+        bool amb = lane < m && lane + 1 < cnt && (fnext - f0 <= twod || (knext >> 5) == (key >> 5));
+        const float fm = __shfl_sync(0xffffffffu, f0, m - 1);
+        if (cnt == m && !(fm + twod < rcsq)) amb = true;
+        ok = !__any_sync(0xffffffffu, amb);
+        if (ok) {
+            const int64_t row0 = (int64_t)iL * m;
+            if (lane < m) {
+                K.qi[row0 + lane] = iL;
+                K.pj[row0 + lane] = (int32_t)e0.y;
+                K.dist[row0 + lane] = sqrtf(f0);
+            }
+            if (lane == 0) K.counts[iL] = m;
+        }
+    } else if (ok) {
+        uint2 e0 = 2 * lane < cnt ? row[2 * lane] : make_uint2(0xffffffffu, 0u);
+        uint2 e1 = 2 * lane + 1 < cnt ? row[2 * lane + 1] : make_uint2(0xffffffffu, 0u);
+#pragma unroll
+        for (int kk = 2; kk <= 64; kk <<= 1) {
+            const bool asc = ((2 * lane) & kk) == 0;
+#pragma unroll
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                if (jj == 1) {
+                    const bool sw = ((e0.x > e1.x) || (e0.x == e1.x && e0.y > e1.y)) == asc;
+                    const uint2 t0 = sw ? e1 : e0, t1 = sw ? e0 : e1;
+                    e0 = t0;
+                    e1 = t1;
+                } else {
+                    const int lm = jj >> 1;
+                    const uint32_t k0 = __shfl_xor_sync(0xffffffffu, e0.x, lm);
+                    const uint32_t v0 = __shfl_xor_sync(0xffffffffu, e0.y, lm);
+                    const uint32_t k1 = __shfl_xor_sync(0xffffffffu, e1.x, lm);
+                    const uint32_t v1 = __shfl_xor_sync(0xffffffffu, e1.y, lm);
+                    const bool takemin = ((lane & lm) == 0) == asc;
+                    const bool l0 = k0 < e0.x || (k0 == e0.x && v0 < e0.y);
+                    const bool l1 = k1 < e1.x || (k1 == e1.x && v1 < e1.y);
+                    if (l0 == takemin) e0 = make_uint2(k0, v0);
+                    if (l1 == takemin) e1 = make_uint2(k1, v1);
+                }
+            }
+        }
+        const float f0 = __uint_as_float(e0.x), f1 = __uint_as_float(e1.x);
+        const float fnext = __shfl_down_sync(0xffffffffu, f0, 1);
+        bool amb = false;
+        if (2 * lane < m && 2 * lane + 1 < cnt) amb |= f1 - f0 <= twod;
+        if (2 * lane + 1 < m && 2 * lane + 2 < cnt && lane < 31) amb |= fnext - f1 <= twod;
+        const float fm = __shfl_sync(0xffffffffu, (m - 1) & 1 ? f1 : f0, (m - 1) >> 1);
+        if (cnt == m && !(fm + twod < rcsq)) amb = true;
+        ok = !__any_sync(0xffffffffu, amb);
+        if (ok) {
+            const int64_t row0 = (int64_t)iL * m;
+            if (2 * lane < m) {
+                K.qi[row0 + 2 * lane] = iL;
+                K.pj[row0 + 2 * lane] = (int32_t)e0.y;
+                K.dist[row0 + 2 * lane] = sqrtf(f0);
+            }
+            if (2 * lane + 1 < m) {
+                K.qi[row0 + 2 * lane + 1] = iL;
+                K.pj[row0 + 2 * lane + 1] = (int32_t)e1.y;
+                K.dist[row0 + 2 * lane + 1] = sqrtf(f1);
+            }
+            if (lane == 0) K.counts[iL] = m;
+        }
     }
+    if (!ok && lane == 0) K.list[atomicAdd(K.list_count, 1)] = t;
 }
+
+// One warp per query cell: the cell's candidates within reach (rc) of the bounding box
+// of its points are staged once (at most kKnnStage; a cell with more lists its queries),
+// then each query in turn takes them 32 at a time, its hits packed into the row by
+// ballot positions.
+constexpr int kKnnStage = 384;
+constexpr int kKnnOwnCap = 512;
 
 template <int NS>
 __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, KnnTile K) {
     __shared__ TileStencilT<NS> sts[kTileWarps];
-    __shared__ float4 sstage[kTileWarps][32];
-    __shared__ uint2 srowbuf[kTileWarps][kTileQueries][64];
-    __shared__ int srow[kTileWarps][kTileQueries];
+    __shared__ float4 sstage[kTileWarps][kKnnStage + 32];
+    __shared__ uint2 srowbuf[kTileWarps][64];
+    __shared__ uint8_t sown[kTileWarps][kKnnOwnCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = a.cell_lo + (int64_t)blockIdx.x * kTileWarps + warp;
     if (A >= a.ncell) return;
@@ -847,97 +935,68 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, Knn
     cell_coords((uint32_t)A, a.nc, cx, cy, cz);
     TileStencilT<NS> &ts = sts[warp];
     float4 *stage = sstage[warp];
-    int *rowlen = srow[warp];
+    uint2 *row = srowbuf[warp];
     const int n = tile_stencil(a, cx, cy, cz, false, ts);
     const int total = ts.pre[n];
+    const uint8_t *own = nullptr;
+    if (total <= kKnnOwnCap) {
+        tile_owners(ts, n, sown[warp]);
+        own = sown[warp];
+    }
     const int m = K.stride;
-    // about 4/27 of a 27-cell stencil lies within the covered radius: a stencil this
-    // dense overflows the 64-slot rows, so its queries go to the warp kernel at once
-    if (total > 1024) {
+    float rcsq = K.r0sq;
+    if (total > 0) {
+        const float x = K.cnum / (float)total;
+        const float r2 = K.dim == 3 ? cbrtf(x) * cbrtf(x) : x;
+        rcsq = fminf(rcsq, r2);
+    }
+    float3 blo = make_float3(INFINITY, INFINITY, INFINITY), bhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    for (int t0 = 0; t0 < nA; t0 += 32) {
+        const float4 q = __ldg(a.pts + begA + min(t0 + lane, nA - 1));
+        float3 l, h;
+        warp_box(q.x, q.y, q.z, t0 + lane < nA, l, h);
+        blo = make_float3(fminf(blo.x, l.x), fminf(blo.y, l.y), fminf(blo.z, l.z));
+        bhi = make_float3(fmaxf(bhi.x, h.x), fmaxf(bhi.y, h.y), fmaxf(bhi.z, h.z));
+    }
+    // a candidate farther than this from the box is at FP32 r2 >= rcsq from every query
+    const float reach2 = rcsq * (1.0f + 1e-5f);
+    const unsigned lt = lanemask_lt();
+    int kept = total > 1024 ? -1 : 0;
+    for (int base = 0; kept >= 0 && base < total; base += 32) {
+        const TileCand c = tile_load_own(a, ts, own, n, total, base + lane);
+        const bool keep = base + lane < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        if (kept + __popc(mk) > kKnnStage) {
+            kept = -1;
+            break;
+        }
+        if (keep) stage[kept + __popc(mk & lt)] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
+        kept += __popc(mk);
+    }
+    if (kept < 0) {
         for (int q = lane; q < nA; q += 32) K.list[atomicAdd(K.list_count, 1)] = begA + q;
         return;
     }
-    for (int qb = 0; qb < nA; qb += kTileQueries) {
-        const int nq = min(kTileQueries, nA - qb);
-        const QLayout L = qlayout(nq);
-        const bool qact = L.myq < nq;
-        const float4 Q = qact ? __ldg(a.pts + begA + qb + L.myq) : make_float4(kFar, kFar, kFar, __int_as_float(-1));
-        const int excl = a.exclude ? __float_as_int(Q.w) : -1;
-        if (lane < kTileQueries) rowlen[lane] = 0;
-        __syncwarp();
-        uint2 *myrow = srowbuf[warp][L.myq];
-        int *myrc = rowlen + L.myq;
-        const float4 *sp = stage + L.g;
-        for (int base = 0; base < total; base += 32) {
-            tile_stage(a, ts, n, total, base, stage);
-#define FGB_KN(GV) knn_chunk<GV>(sp, Q, excl, K.r0sq, myrc, myrow)
-            FGB_TILE_DISPATCH_G(L.G, FGB_KN)
-#undef FGB_KN
-            __syncwarp();
+    if (kept + lane < ((kept + 31) & ~31)) stage[kept + lane] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
+    __syncwarp();
+    const int nch = (kept + 31) >> 5;
+    for (int t = 0; t < nA; ++t) {
+        const float4 Q = __ldg(a.pts + begA + t);
+        const int iL = __float_as_int(Q.w);
+        const int excl = a.exclude ? iL : -1;
+        int cnt = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const float4 c = stage[(ch << 5) + lane];
+            const float r2 = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+            const int j = __float_as_int(c.w);
+            const bool hit = r2 < rcsq && j != excl;
+            const unsigned mh = __ballot_sync(0xffffffffu, hit);
+            const int pos = cnt + __popc(mh & lt);
+            if (hit && pos < 64) row[pos] = make_uint2(__float_as_uint(r2), (uint32_t)j);
+            cnt += __popc(mh);
         }
         __syncwarp();
-        for (int q = 0; q < nq; ++q) {
-            const int cnt = rowlen[q];
-            const int t = begA + qb + q;
-            const int iL = __float_as_int(__ldg(a.pts + t).w);
-            bool ok = cnt >= m && cnt <= 64;
-            uint2 e0 = make_uint2(0xffffffffu, 0u), e1 = make_uint2(0xffffffffu, 0u);
-            if (ok) {
-                const uint2 *row = srowbuf[warp][q];
-                if (2 * lane < cnt) e0 = row[2 * lane];
-                if (2 * lane + 1 < cnt) e1 = row[2 * lane + 1];
-#pragma unroll
-                for (int kk = 2; kk <= 64; kk <<= 1) {
-                    const bool asc = ((2 * lane) & kk) == 0;
-#pragma unroll
-                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                        if (jj == 1) {
-                            const bool sw = ((e0.x > e1.x) || (e0.x == e1.x && e0.y > e1.y)) == asc;
-                            const uint2 t0 = sw ? e1 : e0, t1 = sw ? e0 : e1;
-                            e0 = t0;
-                            e1 = t1;
-                        } else {
-                            const int lm = jj >> 1;
-                            const uint32_t k0 = __shfl_xor_sync(0xffffffffu, e0.x, lm);
-                            const uint32_t v0 = __shfl_xor_sync(0xffffffffu, e0.y, lm);
-                            const uint32_t k1 = __shfl_xor_sync(0xffffffffu, e1.x, lm);
-                            const uint32_t v1 = __shfl_xor_sync(0xffffffffu, e1.y, lm);
-                            const bool takemin = ((lane & lm) == 0) == asc;
-                            const bool l0 = k0 < e0.x || (k0 == e0.x && v0 < e0.y);
-                            const bool l1 = k1 < e1.x || (k1 == e1.x && v1 < e1.y);
-                            if (l0 == takemin) e0 = make_uint2(k0, v0);
-                            if (l1 == takemin) e1 = make_uint2(k1, v1);
-                        }
-                    }
-                }
-                // gaps: element e = 2 lane + r against e + 1 (the next lane's first element)
-                const float f0 = __uint_as_float(e0.x), f1 = __uint_as_float(e1.x);
-                const float fnext = __shfl_down_sync(0xffffffffu, f0, 1);
-                const float twod = 2.f * K.delta;
-                bool amb = false;
-                if (2 * lane < m && 2 * lane + 1 < cnt) amb |= f1 - f0 <= twod;
-                if (2 * lane + 1 < m && 2 * lane + 2 < cnt && lane < 31) amb |= fnext - f1 <= twod;
-                const float fm = __shfl_sync(0xffffffffu, (m - 1) & 1 ? f1 : f0, (m - 1) >> 1);
-                if (cnt == m && !(fm + twod < K.r0sq)) amb = true;
-                ok = !__any_sync(0xffffffffu, amb);
-            }
-            if (ok) {
-                const int64_t row0 = (int64_t)iL * m;
-                if (2 * lane < m) {
-                    K.qi[row0 + 2 * lane] = iL;
-                    K.pj[row0 + 2 * lane] = (int32_t)e0.y;
-                    K.dist[row0 + 2 * lane] = sqrtf(__uint_as_float(e0.x));
-                }
-                if (2 * lane + 1 < m) {
-                    K.qi[row0 + 2 * lane + 1] = iL;
-                    K.pj[row0 + 2 * lane + 1] = (int32_t)e1.y;
-                    K.dist[row0 + 2 * lane + 1] = sqrtf(__uint_as_float(e1.x));
-                }
-                if (lane == 0) K.counts[iL] = m;
-            } else if (lane == 0) {
-                K.list[atomicAdd(K.list_count, 1)] = t;
-            }
-        }
+        knn_finish_row(row, cnt, m, rcsq, K, iL, begA + t);
         __syncwarp();
     }
 }
@@ -1042,6 +1101,18 @@ int tile_knn(const fgb_nq *nq, const StencilPlan &p, int k, int m, int exclude, 
     r0 *= 0.99999;
     KnnTile K;
     K.r0sq = (float)(r0 * r0 * (1.0 - 1e-6));
+    // the stencil's 27 cells (9 of them hold points in a 2D box) over the unit ball's
+    // measure, times m + 12: rc^dim for the expected count m + 12 at the stencil's density
+    const GridHost &g = nq->grid;
+    const double area = nq->box.p[0] * nq->box.p[1] / ((double)g.nc[0] * g.nc[1]);
+    const double extra = 12.0;  // under 1 % of uniform queries find fewer than m within rc
+    if (nq->box.is2d) {
+        K.dim = 2;
+        K.cnum = (float)((m + extra) * 9.0 * area / M_PI);
+    } else {
+        K.dim = 3;
+        K.cnum = (float)((m + extra) * 27.0 * area * nq->box.p[2] / g.nc[2] / (4.0 / 3.0 * M_PI));
+    }
     K.delta = (float)r2_error_bound(p, r0);
     K.k = k;
     K.stride = m;
