@@ -47,6 +47,10 @@ __device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, i
     const int wx = 2 * a.s[0] + 1, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
     const int nfull = wx * wy * wz;
     const int owx = 2 * a.ts[0] + 1, owy = 2 * a.ts[1] + 1;
+    // o -> (o mod wx, o / wx mod wy, o / (wx wy)) by float reciprocals: o < 2^8 and
+    // w < 2^8, so (o + 1/2) / w lies at least 1/(2w) > 2^-9 from an integer while the
+    // rounded product is within 2^-14 of it, and truncates to the exact quotient
+    const float iwx = 1.0f / (float)wx, iwxy = 1.0f / (float)(wx * wy);
     int n = 0;
     // offsets in (oz, oy, ox) order; the half stencil keeps (0,0,0) and what follows it
     const int first = half ? (nfull - 1) / 2 : 0;
@@ -55,7 +59,10 @@ __device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, i
         int cnt = 0, beg = 0;
         float4 of = make_float4(0.f, 0.f, 0.f, 0.f);
         if (o < nfull) {
-            const int ox = o % wx - a.s[0], oy = (o / wx) % wy - a.s[1], oz = o / (wx * wy) - a.s[2];
+            const int qz = __float2int_rz(((float)o + 0.5f) * iwxy);
+            const int rxy = o - qz * (wx * wy);
+            const int qy = __float2int_rz(((float)rxy + 0.5f) * iwx);
+            const int ox = rxy - qy * wx - a.s[0], oy = qy - a.s[1], oz = qz - a.s[2];
             const int xx = wrap_cell(cx + ox, a.nc[0]), yy = wrap_cell(cy + oy, a.nc[1]),
                       zz = wrap_cell(cz + oz, a.nc[2]);
             const int cell = (zz * a.nc[1] + yy) * a.nc[0] + xx;
