@@ -536,6 +536,11 @@ typedef struct fgb_batch_params {
     int32_t hist_copies; /* its shared histogram copies per block: 1, 2 or 4; 0 = autotune */
     int32_t tile_cells;  /* largest work item of the cell-tile kernels, in cells: 1..4096;
                             0 = autotune; -1 = every frame on the per-point kernel */
+    int32_t cells_per_warp; /* query cells per warp of the q_l cell-tile kernel (x-adjacent
+                               cells of a row walked together over the union of their
+                               stencils): 1, 2 or 4, i.e. 1, 1/2 or 1/4 warp per query
+                               cell; a frame whose grid is too narrow takes fewer;
+                               0 = autotune */
 } fgb_batch_params;
 
 /*
@@ -562,8 +567,9 @@ int fgb_batch_run(fgb_batch *b, const float *points, void *stream);
  * pointer (recaptured when it changes). */
 int fgb_batch_run_graph(fgb_batch *b, const float *points, void *stream);
 
-/* Times the candidate (cell_div, tile_cells, block, hist_copies) settings on `points` and
- * keeps the fastest (the parameters set to 0 at create).  Synchronises `stream`. */
+/* Times the candidate (cell_div, tile_cells, cells_per_warp, block, hist_copies) settings
+ * on `points` and keeps the fastest (the parameters set to 0 at create).  Synchronises
+ * `stream`. */
 int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, fgb_batch_params *chosen);
 
 /* Device outputs: RDF counts uint64 (n_frames, bins), q_l float32 (total points, in

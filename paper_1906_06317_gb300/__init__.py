@@ -54,7 +54,8 @@ class fgb_query_args(ctypes.Structure):
 
 class fgb_batch_params(ctypes.Structure):
     _fields_ = [("r_max", _D), ("l", _I32), ("rdf_bins", _I32), ("rdf_r_max", _D), ("rdf_r_min", _D),
-                ("cell_div", _I32), ("block", _I32), ("hist_copies", _I32), ("tile_cells", _I32)]
+                ("cell_div", _I32), ("block", _I32), ("hist_copies", _I32), ("tile_cells", _I32),
+                ("cells_per_warp", _I32)]
 
 
 _SIGS = {
@@ -798,13 +799,13 @@ class Batch:
     particle), replayable from a CUDA graph."""
 
     def __init__(self, frame_sizes, boxes, r_max=1.5, l=6, rdf_bins=200, rdf_r_max=3.0, rdf_r_min=0.0,
-                 cell_div=0, block=0, hist_copies=0, tile_cells=0):
+                 cell_div=0, block=0, hist_copies=0, tile_cells=0, cells_per_warp=0):
         sizes = np.asarray(frame_sizes, dtype=np.int64)
         self.offsets = np.zeros(len(sizes) + 1, dtype=np.int64)
         np.cumsum(sizes, out=self.offsets[1:])
         bx = (fgb_box * len(sizes))(*[Box.from_box(b)._c() for b in boxes])
         self.params = fgb_batch_params(r_max, l, rdf_bins, rdf_r_max, rdf_r_min, cell_div, block, hist_copies,
-                                       tile_cells)
+                                       tile_cells, cells_per_warp)
         h = ctypes.c_void_p()
         _check(lib().fgb_batch_create(len(sizes), self.offsets.ctypes.data, bx, ctypes.byref(self.params), _stream(),
                                       ctypes.byref(h)))
@@ -825,7 +826,7 @@ class Batch:
         chosen = fgb_batch_params()
         _check(lib().fgb_batch_tune(self._h, p.data_ptr(), _stream(), ctypes.byref(chosen)))
         return dict(cell_div=chosen.cell_div, block=chosen.block, hist_copies=chosen.hist_copies,
-                    tile_cells=chosen.tile_cells)
+                    tile_cells=chosen.tile_cells, cells_per_warp=chosen.cells_per_warp)
 
     def routes(self):
         """Frames on the cell-tile kernels and on the per-point kernel (current settings)."""

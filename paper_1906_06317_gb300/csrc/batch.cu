@@ -229,8 +229,8 @@ struct fgb_batch {
     std::vector<fgb_box> boxes;
     fgb_batch_params prm;
     int64_t total;
-    int cell_div, block, copies, tile_cells;
-    bool tune_div, tune_block, tune_copies, tune_tile;
+    int cell_div, block, copies, tile_cells, qbw;
+    bool tune_div, tune_block, tune_copies, tune_tile, tune_qb;
     // configuration-dependent device state
     FrameDev *frames_d;
     float2 *origin_d;
@@ -242,7 +242,8 @@ struct fgb_batch {
     int4 *titems_d;       // their work items
     int ntitems;
     int ntile_frames;
-    bool small_r, small_q;  // every tile frame's RDF half stencil <= 64 cells, ball stencil <= 32
+    bool small_r;           // every tile frame's RDF half stencil <= 64 cells
+    int q_ns;               // q_l stencil capacity every tile frame fits (32, 64, 128)
     uint32_t *cell_start;
     int64_t ncell_total;
     // fixed device state
@@ -301,9 +302,10 @@ static void drop_graph(fgb_batch *b) {
 constexpr int kBatchTileMaxBins = 1024;
 
 // Builds every per-frame table for a cell division, a block size of the per-point kernel
-// and the largest work item of the tile kernels (tile_cells < 0: no tile route);
-// synchronises.
-static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cudaStream_t s) {
+// and the largest work item of the tile kernels (tile_cells < 0: no tile route), and
+// the query cells per warp of the q_l tile kernel (qbw: 1, 2 or 4; a frame takes the
+// largest power of two up to qbw that its grid allows); synchronises.
+static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, int qbw, cudaStream_t s) {
     drop_graph(b);
     free_config(b, s);
     const int F = b->nframes;
@@ -319,7 +321,8 @@ static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cuda
     std::vector<Fix> fix(F);
     std::vector<FrameTile> tiles;
     std::vector<int64_t> tile_lo, tile_hi;  // query cells of each tile frame
-    bool small_r = true, small_q = true;
+    bool small_r = true;
+    int q_cells = 0;  // largest ball stencil (or block union) of the tile frames
     int64_t cell_base = 0;
     for (int f = 0; f < F; ++f) {
         BoxHost box;
@@ -348,7 +351,51 @@ static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cuda
         StencilPlan pq, pr;
         std::vector<float4> tq, tr;
         FGB_TRY(plan_stencil_host(box, g, rq, 0, &pq, &tq));
+        // a block of qb cells along x walks the union of their ball stencils: x offsets
+        // -s .. s + qb - 1 (distinct cells while qb + 2s <= nc_x; the offset table reaches
+        // s + qb - 1 when nc_x >= 2s + 2qb - 1)
+        auto qb_cells = [](const StencilPlan &p, int q) {
+            return (q + 2 * p.s[0]) * (2 * p.s[1] + 1) * (2 * p.s[2] + 1);
+        };
+        int qb_f = 1;
+        if (qbw > 1 && pq.mode == 0) {
+            for (int q = qbw; q > 1 && qb_f == 1; q >>= 1)
+                if (g.nc[0] >= 2 * pq.s[0] + 2 * q - 1 && qb_cells(pq, q) <= kTileMaxStencil) qb_f = q;
+            if (qb_f > 1) {
+                StencilPlan wide;
+                std::vector<float4> tw;
+                FGB_TRY(plan_stencil_host(box, g, rq, pq.s[0] + qb_f - 1, &wide, &tw));
+                if (wide.mode == 0 && wide.ts[0] >= wide.s[0] + qb_f - 1) {
+                    pq = wide;
+                    tq.swap(tw);
+                } else {
+                    qb_f = 1;
+                }
+            }
+        }
         FGB_TRY(plan_stencil_host(box, g, rr, 0, &pr, &tr));
+        // the same for the RDF's half stencil: a block's union lists the cells after each
+        // of its cells in (z, y, x) order
+        auto qbr_cells = [](const StencilPlan &p, int q) {
+            const int wxq = q + 2 * p.s[0];
+            return wxq * (2 * p.s[1] + 1) * p.s[2] + wxq * p.s[1] + q + p.s[0];
+        };
+        int qbr_f = 1;
+        if (qbw > 1 && pr.mode == 0) {
+            for (int q = qbw; q > 1 && qbr_f == 1; q >>= 1)
+                if (g.nc[0] >= 2 * pr.s[0] + 2 * q - 1 && qbr_cells(pr, q) <= kTileMaxStencil) qbr_f = q;
+            if (qbr_f > 1) {
+                StencilPlan wide;
+                std::vector<float4> tw;
+                FGB_TRY(plan_stencil_host(box, g, rr, pr.s[0] + qbr_f - 1, &wide, &tw));
+                if (wide.mode == 0 && wide.ts[0] >= wide.s[0] + qbr_f - 1) {
+                    pr = wide;
+                    tr.swap(tw);
+                } else {
+                    qbr_f = 1;
+                }
+            }
+        }
         fix[f].offq = offs.size();
         offs.insert(offs.end(), tq.begin(), tq.end());
         fix[f].offr = offs.size();
@@ -401,9 +448,11 @@ static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cuda
             ft.b.band = ba.band;
             ft.P = d.P;
             ft.f = f;
+            ft.qb = qb_f;
+            ft.qbr = qbr_f;
             tiles.push_back(ft);
-            small_r = small_r && (cells(pr) + 1) / 2 <= 64;
-            small_q = small_q && cells(pq) <= 32;
+            small_r = small_r && qbr_cells(pr, qbr_f) <= 64;
+            q_cells = std::max(q_cells, qb_cells(pq, qb_f));
             // a 2D frame's points all lie in the middle one of its three z layers
             const int64_t layer = (int64_t)g.nc[0] * g.nc[1];
             tile_lo.push_back(box.is2d ? layer : 0);
@@ -437,7 +486,7 @@ static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cuda
     b->ntitems = (int)titems.size();
     b->ntile_frames = (int)tiles.size();
     b->small_r = small_r;
-    b->small_q = small_q;
+    b->q_ns = q_cells <= 32 ? 32 : q_cells <= 64 ? 64 : kTileMaxStencil;
     int st = FGB_OK;
     st = st ? st : dalloc_n(&b->frames_d, F, s);
     st = st ? st : dalloc_n(&b->origin_d, std::max<size_t>(org.size(), 1), s);
@@ -494,6 +543,7 @@ static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, cuda
     b->cell_div = cell_div;
     b->block = block;
     b->tile_cells = tile_cells;
+    b->qbw = qbw;
     return FGB_OK;
 }
 
@@ -597,7 +647,7 @@ static int enqueue(fgb_batch *b, const float *pts, cudaStream_t s) {
         t.Q = b->Q;
         t.nn = b->nn;
         t.qesc = b->qesc;
-        FGB_TRY(batch_tile_run(t, b->prm.l, b->tl, b->small_r, b->small_q, s));
+        FGB_TRY(batch_tile_run(t, b->prm.l, b->tl, b->small_r, b->q_ns, s));
     }
     {
         FGB_KSCOPE("k_batch_escalated", s);
@@ -618,7 +668,8 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
         p.rdf_r_min < 0.0)
         return fail(FGB_ERR_INVALID_ARG, "invalid batch parameters");
     if (p.cell_div < 0 || p.cell_div > 2 || p.block < 0 || p.block > 512 || (p.block && p.block % 32) ||
-        p.hist_copies < 0 || p.hist_copies > 4 || p.tile_cells < -1 || p.tile_cells > 4096)
+        p.hist_copies < 0 || p.hist_copies > 4 || p.tile_cells < -1 || p.tile_cells > 4096 ||
+        (p.cells_per_warp != 0 && p.cells_per_warp != 1 && p.cells_per_warp != 2 && p.cells_per_warp != 4))
         return fail(FGB_ERR_INVALID_ARG, "invalid tuning parameters");
     if (frame_offsets[0] != 0) return fail(FGB_ERR_INVALID_ARG, "frame_offsets[0] must be 0");
     for (int f = 0; f < n_frames; ++f)
@@ -635,6 +686,7 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
     b->tune_block = p.block == 0;
     b->tune_copies = p.hist_copies == 0;
     b->tune_tile = p.tile_cells == 0;
+    b->tune_qb = p.cells_per_warp == 0;
     b->copies = p.hist_copies ? p.hist_copies : 2;
     b->stream = s;
     const int bins = p.rdf_bins;
@@ -666,7 +718,8 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
         cudaMemcpyAsync(b->off_d, frame_offsets, sizeof(int64_t) * (n_frames + 1), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(b->T_d, b->T_h.data(), sizeof(double) * (bins + 1), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(b->qesc, 0, 2 * sizeof(unsigned long long), s);
-        st = configure(b, p.cell_div ? p.cell_div : 1, p.block ? p.block : 128, p.tile_cells ? p.tile_cells : 64, s);
+        st = configure(b, p.cell_div ? p.cell_div : 1, p.block ? p.block : 128, p.tile_cells ? p.tile_cells : 64,
+                       p.cells_per_warp ? p.cells_per_warp : 1, s);
     }
     if (st != FGB_OK) {
         fgb_batch_destroy(b);
@@ -738,20 +791,23 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
     std::vector<int> tiles = b->tune_tile ? std::vector<int>{16, 64} : std::vector<int>{b->tile_cells};
     std::vector<int> blocks = b->tune_block ? std::vector<int>{64, 128, 256} : std::vector<int>{b->block};
     std::vector<int> copies = b->tune_copies ? std::vector<int>{1, 2, 4} : std::vector<int>{b->copies};
+    std::vector<int> qbs = b->tune_qb && b->prm.l >= 0 ? std::vector<int>{1, 2, 4} : std::vector<int>{b->qbw};
     cudaEvent_t e0, e1;
     FGB_CUDA(cudaEventCreate(&e0));
     FGB_CUDA(cudaEventCreate(&e1));
     float best = INFINITY;
-    int bd = b->cell_div, bt = b->tile_cells, bb = b->block, bc = b->copies;
+    int bd = b->cell_div, bt = b->tile_cells, bb = b->block, bc = b->copies, bq = b->qbw;
     int st = FGB_OK;
     for (int dv : divs) {
         for (int tc : tiles) {
             for (int bl : blocks) {
-                st = configure(b, dv, bl, tc, s);
+              for (int qb : qbs) {
+                st = configure(b, dv, bl, tc, qb, s);
                 if (st) break;
                 // settings of a kernel with no work in this division are timed once
-                if (b->ntitems == 0 && tc != tiles[0]) break;
+                if (b->ntitems == 0 && (tc != tiles[0] || qb != qbs[0])) break;
                 if (b->nitems == 0 && bl != blocks[0]) break;
+                if (b->nitems > 0 && b->ntitems > 0 && qb != qbs[0] && bl != blocks[0]) break;
                 for (int cp : copies) {
                     if (cp * 32 > bl) continue;
                     if (b->nitems == 0 && cp != copies[0]) break;
@@ -774,9 +830,12 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
                         bt = tc;
                         bb = bl;
                         bc = cp;
+                        bq = qb;
                     }
                 }
                 if (st) break;
+              }
+              if (st) break;
             }
             if (st) break;
         }
@@ -786,13 +845,14 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
     cudaEventDestroy(e1);
     FGB_TRY(st);
     b->copies = bc;
-    FGB_TRY(configure(b, bd, bb, bt, s));
+    FGB_TRY(configure(b, bd, bb, bt, bq, s));
     if (chosen) {
         *chosen = b->prm;
         chosen->cell_div = bd;
         chosen->block = bb;
         chosen->hist_copies = bc;
         chosen->tile_cells = bt;
+        chosen->cells_per_warp = bq;
     }
     return FGB_OK;
 }

@@ -95,20 +95,23 @@ __device__ __noinline__ void bt_rdf_slow(const BatchTileArgs *ap, const FrameTil
     if (be >= 0) atomicAdd(a.counts + (int64_t)fr->f * a.bins + be, 2ull);
 }
 
-// One candidate per lane against the queries [0, nq) of the pass, valid only for
-// queries tl < lim (a point of the cell itself pairs only with earlier queries; other
-// candidates carry no limit).  The fast test is the single-frame one: bin floor(x) when
-// x = (r - r_min)/Delta is further than the error bound from both edges.
+// One candidate per lane against the queries [0, nq) of the pass, valid only for the
+// queries lo <= tl < hi (lim = lo | hi << 8): the queries of the block cells whose half
+// stencil holds the candidate's cell, and of its own cell only those before it (so each
+// unordered pair is binned once, with weight 2).  The fast test is the single-frame one:
+// bin floor(x) when x = (r - r_min)/Delta is further than the error bound from both
+// edges.
 __device__ __forceinline__ void bt_rdf_rounds(const BatchTileArgs &a, const FrameTile &fr, const float4 *qs, int nq,
                                               float cx, float cy, float cz, int cj, int lim, uint32_t *h) {
     const BinParams &P = fr.P;
     const float rhi = P.rmax_hi, rlo = P.rmin_lo;
     const float invd = P.invdelta, rmid = P.rmin_invdelta, g2h = P.g2h, eps = P.eps, r2f = P.r2_fast;
+    const int llo = lim & 0xff, lhi = lim >> 8;
 #pragma unroll 4
     for (int tl = 0; tl < nq; ++tl) {
         const float4 q = qs[tl];
         const float r2 = r2_f32(cx - q.x, cy - q.y, cz - q.z);
-        if (r2 < rhi && r2 >= rlo && tl < lim) {
+        if (r2 < rhi && r2 >= rlo && tl < lhi && tl >= llo) {
             const float inv = rsqrt_ftz(r2);
             const float x = fmaf(r2 * inv, invd, -rmid);
             const float fb = floorf(x);
@@ -131,22 +134,41 @@ __device__ __forceinline__ void bt_guard(const BatchTileArgs &a, const FrameTile
     tests += 32u * (unsigned)nq;
 }
 
-// The candidates of the cell's half stencil (its own points first) are packed into full
-// chunks of 32, dropping those out of reach of the pass's bounding box; the cell's own
-// points carry their limit (k - qb) in `lim`.
+// Query i of block cell b (sorted position p) in the frame of cell A: shifted by the
+// table offset of (b, 0, 0), as the candidates are shifted by theirs.  qst[b] = start of
+// block cell b's queries relative to the block's first point.
+__device__ __forceinline__ float4 bt_block_query(const TileArgs &t, const int *qst, int len, int p, int rel) {
+    float4 q = __ldg(t.pts + p);
+    int b = 0;
+    for (int c = 1; c < len; ++c) b += rel >= qst[c] ? 1 : 0;
+    if (b > 0) {
+        const int owx = 2 * t.ts[0] + 1, owy = 2 * t.ts[1] + 1;
+        const float4 of = __ldg(t.off + (t.ts[2] * owy + t.ts[1]) * owx + (b + t.ts[0]));
+        q.x += of.x;
+        q.y += of.y;
+        q.z += of.z;
+    }
+    return q;
+}
+
+// The queries of `len` x-adjacent cells A, A+1, ... of one row (contiguous in sorted
+// order) against the union of their half stencils; each candidate keeps the range of
+// query slots it pairs with.  The candidates are packed into full chunks of 32, dropping
+// those out of reach of the pass's bounding box.
 template <int NS>
-__device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameTile &fr, int A, TileStencilT<NS> &ts,
-                                            uint8_t *ownbuf, float4 *qs, float4 *buf, int *lim, uint32_t *h,
-                                            uint64_t &tests) {
+__device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameTile &fr, int A, int len,
+                                            TileStencilT<NS> &ts, uint8_t *ownbuf, int *qst, float4 *qs, float4 *buf,
+                                            int *lim, uint32_t *h, uint64_t &tests) {
     const TileArgs &t = fr.r;
     const int lane = threadIdx.x & 31;
     const int begA = (int)__ldg(t.cell_start + A);
-    const int nA = (int)__ldg(t.cell_start + A + 1) - begA;
+    const int nA = (int)__ldg(t.cell_start + A + len) - begA;
     if (nA == 0) return;
     int cx, cy, cz;
     cell_coords((uint32_t)A, t.nc, cx, cy, cz);
     __syncwarp();
-    const int n = tile_stencil(t, cx, cy, cz, true, ts);
+    if (lane <= len) qst[lane] = (int)__ldg(t.cell_start + A + lane) - begA;
+    const int n = tile_stencil(t, cx, cy, cz, true, ts, len);
     const int total = ts.pre[n];
     const uint8_t *own = nullptr;
     if (total <= kBtOwnCap) {
@@ -159,7 +181,7 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
     for (int qb = 0; qb < nA; qb += 32) {
         const int nq = min(32, nA - qb);
         __syncwarp();
-        if (lane < nq) qs[lane] = __ldg(t.pts + begA + qb + lane);
+        if (lane < nq) qs[lane] = bt_block_query(t, qst, len, begA + qb + lane, qb + lane);
         __syncwarp();
         float3 blo, bhi;
         {
@@ -170,12 +192,16 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
         for (int base = 0; base < total; base += 32) {
             const int k = base + lane;
             const TileCand c = tile_load_own(t, ts, own, n, total, k);
-            const bool keep = k < total && (k < nA || box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2);
+            const bool keep = k < total && box_dist2(blo, bhi, c.x, c.y, c.z) <= reach2;
             const unsigned m = __ballot_sync(kFull, keep);
             if (keep) {
+                const int rg = __float_as_int(ts.off[c.o].w);
+                const int b0 = rg & 0xff, b1 = (rg >> 8) & 0xff;
+                const int shi = (rg >> 16) ? c.p - begA : qst[b1 + 1];  // own cell: queries before it
+                const int lo = min(max(qst[b0] - qb, 0), 32), hi = min(max(shi - qb, 0), 32);
                 const int slot = cnt + __popc(m & lt);
                 buf[slot] = make_float4(c.x, c.y, c.z, __int_as_float(c.j));
-                lim[slot] = k < nA ? k - qb : 0x7fffffff;
+                lim[slot] = lo | (hi << 8);
             }
             cnt += __popc(m);
             if (cnt >= 32) {
@@ -211,6 +237,7 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
     __shared__ float4 sbuf[kBtW][64];  // kept candidates
     __shared__ int slim[kBtW][64];     // their query limits
     __shared__ uint8_t sown[kBtW][kBtOwnCap];
+    __shared__ int sqst[kBtW][8];      // query starts of the block's cells
     extern __shared__ uint32_t shist[];  // kBtW * bins
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *h = shist + warp * a.bins;
@@ -226,8 +253,13 @@ __global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_const
             bt_load_frame(a.ft + w.x, &fr);
             cur = w.x;
         }
-        for (int c = w.y; c < w.z; ++c)
-            bt_rdf_cell<NS>(a, fr, c, sts[warp], sown[warp], sq[warp], sbuf[warp], slim[warp], h, tests);
+        for (int c = w.y; c < w.z;) {
+            // a block of up to qbr cells, within one x row and the work item
+            const int len = min(min(fr.qbr, fr.r.nc[0] - c % fr.r.nc[0]), w.z - c);
+            bt_rdf_cell<NS>(a, fr, c, len, sts[warp], sown[warp], sqst[warp], sq[warp], sbuf[warp], slim[warp], h,
+                            tests);
+            c += len;
+        }
     }
     if (cur >= 0) bt_flush(h, a.bins, a.counts + (int64_t)fr.f * a.bins);
 }
@@ -293,20 +325,24 @@ __device__ __forceinline__ void bt_drain(int n, const float4 *bond, float *acc) 
     }
 }
 
+// The queries of `len` x-adjacent cells A, A+1, ... of one row (contiguous in sorted
+// order) against the union of their ball stencils: a candidate outside a query's own
+// stencil is farther than r_max from it (the stencil covers the ball), so testing it
+// changes nothing.
 template <int L, int NS>
-__device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTile &fr, int A, TileStencilT<NS> &ts,
-                                          uint8_t *ownbuf, float4 *qs, float4 *buf, float4 *bond, float *acc, int *snn,
-                                          int &nesc) {
+__device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTile &fr, int A, int len,
+                                          TileStencilT<NS> &ts, uint8_t *ownbuf, float4 *qs, float4 *buf, float4 *bond,
+                                          float *acc, int *snn, int &nesc) {
     constexpr int NC = 2 * (L + 1);
     const TileArgs &t = fr.b;
     const int lane = threadIdx.x & 31;
     const int begA = (int)__ldg(t.cell_start + A);
-    const int nA = (int)__ldg(t.cell_start + A + 1) - begA;
+    const int nA = (int)__ldg(t.cell_start + A + len) - begA;
     if (nA == 0) return;
     int cx, cy, cz;
     cell_coords((uint32_t)A, t.nc, cx, cy, cz);
     __syncwarp();
-    const int n = tile_stencil(t, cx, cy, cz, false, ts);
+    const int n = tile_stencil(t, cx, cy, cz, false, ts, len);
     const int total = ts.pre[n];
     const uint8_t *own = nullptr;
     if (total <= kBtOwnCap) {
@@ -319,7 +355,22 @@ __device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTil
     for (int qb = 0; qb < nA; qb += 32) {
         const int nq = min(32, nA - qb);
         __syncwarp();
-        if (lane < nq) qs[lane] = __ldg(t.pts + begA + qb + lane);
+        if (lane < nq) {
+            // a query of block cell b is local to that cell: shift it into cell A's frame
+            // by the table offset of (b, 0, 0), as the candidates are shifted by theirs
+            const int p = begA + qb + lane;
+            float4 q = __ldg(t.pts + p);
+            int b = 0;
+            for (int c = 1; c < len; ++c) b += p >= (int)__ldg(t.cell_start + A + c) ? 1 : 0;
+            if (b > 0) {
+                const int owx = 2 * t.ts[0] + 1, owy = 2 * t.ts[1] + 1;
+                const float4 of = __ldg(t.off + (t.ts[2] * owy + t.ts[1]) * owx + (b + t.ts[0]));
+                q.x += of.x;
+                q.y += of.y;
+                q.z += of.z;
+            }
+            qs[lane] = q;
+        }
         snn[lane] = 0;
         for (int k = lane; k < 32 * NC; k += 32) acc[k] = 0.f;
         __syncwarp();
@@ -390,7 +441,7 @@ __device__ __forceinline__ void bt_q_cell(const BatchTileArgs &a, const FrameTil
 }
 
 template <int L, int NS>
-__global__ void __launch_bounds__(kBtW * 32) k_batch_qtile(const __grid_constant__ BatchTileArgs a) {
+__global__ void __launch_bounds__(kBtW * 32, 7) k_batch_qtile(const __grid_constant__ BatchTileArgs a) {
     __shared__ FrameTile sfr[kBtW];
     __shared__ TileStencilT<NS> sts[kBtW];
     __shared__ float4 sq[kBtW][32];
@@ -408,9 +459,14 @@ __global__ void __launch_bounds__(kBtW * 32) k_batch_qtile(const __grid_constant
             bt_load_frame(a.ft + w.x, &fr);
             cur = w.x;
         }
-        for (int c = w.y; c < w.z; ++c)
-            bt_q_cell<L, NS>(a, fr, c, sts[warp], sown[warp], sq[warp], sbuf[warp], sbond[warp], sacc[warp], snn[warp],
-                             nesc);
+        for (int c = w.y; c < w.z;) {
+            // a block of up to qb cells, within one x row and the work item
+            const int cx = c % fr.b.nc[0];
+            const int len = min(min(fr.qb, fr.b.nc[0] - cx), w.z - c);
+            bt_q_cell<L, NS>(a, fr, c, len, sts[warp], sown[warp], sq[warp], sbuf[warp], sbond[warp], sacc[warp],
+                             snn[warp], nesc);
+            c += len;
+        }
     }
     nesc = __reduce_add_sync(kFull, nesc);
     if (lane == 0 && nesc) atomicAdd(a.qesc, (unsigned long long)nesc);
@@ -423,14 +479,17 @@ struct QTileKernel {
         FGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_qtile<L, NS>, kBtW * 32, 0));
         return FGB_OK;
     }
-    static int init(int *per_sm_small, int *per_sm_large) {
-        FGB_TRY(occupancy<32>(per_sm_small));
-        return occupancy<kTileMaxStencil>(per_sm_large);
+    static int init(int *per_sm) {
+        FGB_TRY(occupancy<32>(per_sm));
+        FGB_TRY(occupancy<64>(per_sm + 1));
+        return occupancy<kTileMaxStencil>(per_sm + 2);
     }
-    static void launch(const BatchTileArgs &a, bool small, unsigned grid, cudaStream_t s) {
+    static void launch(const BatchTileArgs &a, int ns, unsigned grid, cudaStream_t s) {
         FGB_KSCOPE("k_batch_qtile", s);
-        if (small)
+        if (ns <= 32)
             k_batch_qtile<L, 32><<<grid, kBtW * 32, 0, s>>>(a);
+        else if (ns <= 64)
+            k_batch_qtile<L, 64><<<grid, kBtW * 32, 0, s>>>(a);
         else
             k_batch_qtile<L, kTileMaxStencil><<<grid, kBtW * 32, 0, s>>>(a);
     }
@@ -467,17 +526,15 @@ int batch_tile_init(int bins, int l, BatchTileLaunch *out) {
     g.warps = (int)g.grid_r[0] * kBtW;
     if (l >= 0) {
         FGB_TRY(ensure_consts());
-        int q0 = 0, q1 = 0;
-        FGB_TRY(dispatch_qtile(l, [&](auto k) { return k.init(&q0, &q1); }));
-        g.grid_q[0] = (unsigned)(num_sms() * std::max(q0, 1));
-        g.grid_q[1] = (unsigned)(num_sms() * std::max(q1, 1));
+        int q[3] = {0, 0, 0};
+        FGB_TRY(dispatch_qtile(l, [&](auto k) { return k.init(q); }));
+        for (int i = 0; i < 3; ++i) g.grid_q[i] = (unsigned)(num_sms() * std::max(q[i], 1));
     }
     *out = g;
     return FGB_OK;
 }
 
-int batch_tile_run(const BatchTileArgs &a, int l, const BatchTileLaunch &g, bool small_r, bool small_q,
-                   cudaStream_t s) {
+int batch_tile_run(const BatchTileArgs &a, int l, const BatchTileLaunch &g, bool small_r, int q_ns, cudaStream_t s) {
     if (a.nitems <= 0) return FGB_OK;
     const unsigned want = (unsigned)((a.nitems + kBtW - 1) / kBtW);
     {
@@ -490,7 +547,7 @@ int batch_tile_run(const BatchTileArgs &a, int l, const BatchTileLaunch &g, bool
     }
     if (l >= 0)
         FGB_TRY(dispatch_qtile(l, [&](auto k) {
-            k.launch(a, small_q, std::min(g.grid_q[small_q ? 0 : 1], want), s);
+            k.launch(a, q_ns, std::min(g.grid_q[q_ns <= 32 ? 0 : q_ns <= 64 ? 1 : 2], want), s);
             return FGB_OK;
         }));
     FGB_LAUNCH_CHECK();

@@ -40,11 +40,17 @@ struct TileStencilT {
 using TileStencil = TileStencilT<kTileMaxStencil>;
 
 // Builds the (half) stencil list of cell A in `ts` (one warp), returns the number of
-// stencil cells; pre[n] holds the total number of candidates.
+// stencil cells; pre[n] holds the total number of candidates.  span > 1: the union of
+// the (half) stencils of the span cells A, A+1, ... along x (offsets in x from -s to
+// s + span - 1; the offset table must reach that far).  For a half stencil, off[].w of
+// each listed cell holds (as int bits) the block cells b whose half stencil holds it,
+// blo | bhi << 8, plus 1 << 16 when it is block cell bhi itself (then only points after
+// the query in sorted order pair with it).
 template <class TS>
-__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TS &ts) {
+__device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, int cz, bool half, TS &ts,
+                                            int span = 1) {
     const int lane = threadIdx.x & 31;
-    const int wx = 2 * a.s[0] + 1, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
+    const int wx = 2 * a.s[0] + span, wy = 2 * a.s[1] + 1, wz = 2 * a.s[2] + 1;
     const int nfull = wx * wy * wz;
     const int owx = 2 * a.ts[0] + 1, owy = 2 * a.ts[1] + 1;
     // o -> (o mod wx, o / wx mod wy, o / (wx wy)) by float reciprocals: o < 2^8 and
@@ -53,7 +59,7 @@ __device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, i
     const float iwx = 1.0f / (float)wx, iwxy = 1.0f / (float)(wx * wy);
     int n = 0;
     // offsets in (oz, oy, ox) order; the half stencil keeps (0,0,0) and what follows it
-    const int first = half ? (nfull - 1) / 2 : 0;
+    const int first = half ? (a.s[2] * wy + a.s[1]) * wx + a.s[0] : 0;
     for (int b = first; b < nfull; b += 32) {
         const int o = b + lane;
         int cnt = 0, beg = 0;
@@ -69,6 +75,11 @@ __device__ __forceinline__ int tile_stencil(const TileArgs &a, int cx, int cy, i
             beg = (int)__ldg(a.cell_start + cell);
             cnt = (int)__ldg(a.cell_start + cell + 1) - beg;
             of = __ldg(a.off + ((oz + a.ts[2]) * owy + (oy + a.ts[1])) * owx + (ox + a.ts[0]));
+            if (half) {
+                const bool row = oz == 0 && oy == 0;  // the query cells' own row: ox >= 0
+                const int blo = max(0, ox - a.s[0]), bhi = min(span - 1, row ? ox : ox + a.s[0]);
+                of.w = __int_as_float(blo | (bhi << 8) | ((row && ox < span) ? (1 << 16) : 0));
+            }
         }
         // inclusive scan of counts across the warp
         int inc = cnt;

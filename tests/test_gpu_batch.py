@@ -43,18 +43,21 @@ def check(b, fr, refs):
         assert np.array_equal(nn[off[k]:off[k + 1]], nn_ref)
 
 
-# (cell_div, block, hist_copies, tile_cells, route): tile_cells -1 puts every frame on the
-# per-point kernel; cell_div 2 makes the RDF half stencil too wide for the tile kernels;
-# tile_cells 1 gives one-cell work items
-@pytest.mark.parametrize("cell_div,block,copies,tile,route", [
-    (1, 128, 2, -1, "per_point"), (2, 64, 1, 0, "per_point"), (1, 256, 4, 0, "tile"), (1, 128, 2, 1, "tile")])
-def test_batch_matches_oracle(fgb, frames, cell_div, block, copies, tile, route):
+# (cell_div, block, hist_copies, tile_cells, cells_per_warp, route): tile_cells -1 puts
+# every frame on the per-point kernel; cell_div 2 makes the RDF half stencil too wide for
+# the tile kernels; tile_cells 1 gives one-cell work items; cells_per_warp 2 and 4 walk
+# blocks of x-adjacent query cells (shortened at row and work-item ends; frames too narrow
+# take smaller blocks)
+@pytest.mark.parametrize("cell_div,block,copies,tile,qb,route", [
+    (1, 128, 2, -1, 1, "per_point"), (2, 64, 1, 0, 1, "per_point"), (1, 256, 4, 0, 1, "tile"),
+    (1, 128, 2, 1, 1, "tile"), (1, 128, 2, 0, 2, "tile"), (1, 128, 2, 0, 4, "tile"), (1, 128, 2, 3, 4, "tile")])
+def test_batch_matches_oracle(fgb, frames, cell_div, block, copies, tile, qb, route):
     fr, refs = frames
     P = W.C5_PARAMS
     pts = torch.from_numpy(np.concatenate([f.points for f in fr])).cuda()
     b = fgb.Batch([len(f.points) for f in fr], [f.box for f in fr], r_max=P["r_max"], l=P["l"],
                   rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"], cell_div=cell_div, block=block,
-                  hist_copies=copies, tile_cells=tile)
+                  hist_copies=copies, tile_cells=tile, cells_per_warp=qb)
     assert b.routes()[route] == len(fr)
     b.run(pts)
     torch.cuda.synchronize()
@@ -78,10 +81,11 @@ def test_batch_routes_agree(fgb, frames):
     assert np.all(np.abs(q0 - q1) <= 1e-5 * np.maximum(np.abs(q0), 1e-2))
 
 
-@pytest.mark.parametrize("l", [4, 12])
-def test_batch_crowded_cells(fgb, l):
-    # about 40 points per cell (several query passes per cell in the tile kernels), one
-    # cubic and one triclinic frame, l with two partial sums (4) and with one (12)
+@pytest.mark.parametrize("l,qb", [(4, 1), (12, 1), (6, 2)])
+def test_batch_crowded_cells(fgb, l, qb):
+    # about 40 points per cell (several query passes per cell in the tile kernels; blocks
+    # of two cells: about 80 queries), one cubic and one triclinic frame, l with two
+    # partial sums (4) and with one (12)
     rng = np.random.default_rng(21 + l)
     boxes = [W.Box.cube(8.0), W.Box(8.2, 8.0, 8.4, 0.1, -0.05, 0.08)]
     xs = [W.uniform_points(rng, boxes[0], 5000), W.uniform_points(rng, boxes[1], 5400)]
@@ -93,7 +97,7 @@ def test_batch_crowded_cells(fgb, l):
         refs.append((counts, oracle.steinhardt(box, x, off, pj, l), np.diff(off)))
     pts = torch.from_numpy(np.concatenate(xs)).cuda()
     b = fgb.Batch([len(x) for x in xs], boxes, r_max=P["r_max"], l=l, rdf_bins=P["rdf_bins"],
-                  rdf_r_max=P["rdf_r_max"], cell_div=1)
+                  rdf_r_max=P["rdf_r_max"], cell_div=1, cells_per_warp=qb)
     assert b.routes()["tile"] == 2
     b.run(pts)
     torch.cuda.synchronize()
@@ -108,6 +112,7 @@ def test_batch_graph_replay_and_tune(fgb, frames):
                   rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"])
     chosen = b.tune(pts)
     assert chosen["cell_div"] in (1, 2) and chosen["block"] in (64, 128, 256) and chosen["tile_cells"] in (16, 64)
+    assert chosen["cells_per_warp"] in (1, 2, 4)
     for _ in range(3):
         b.run(pts, graph=True)
     torch.cuda.synchronize()
