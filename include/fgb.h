@@ -536,10 +536,11 @@ typedef struct fgb_batch_params {
     int32_t hist_copies; /* its shared histogram copies per block: 1, 2 or 4; 0 = autotune */
     int32_t tile_cells;  /* largest work item of the cell-tile kernels, in cells: 1..4096;
                             0 = autotune; -1 = every frame on the per-point kernel */
-    int32_t cells_per_warp; /* query cells per warp of the q_l cell-tile kernel (x-adjacent
+    int32_t cells_per_warp; /* query cells per warp of the cell-tile kernels (x-adjacent
                                cells of a row walked together over the union of their
-                               stencils): 1, 2 or 4, i.e. 1, 1/2 or 1/4 warp per query
-                               cell; a frame whose grid is too narrow takes fewer;
+                               stencils): 1, 2, 4 or 8, i.e. 1 to 1/8 warp per query
+                               cell; a frame whose grid is too narrow, or whose block
+                               union would exceed 128 stencil cells, takes fewer;
                                0 = autotune */
 } fgb_batch_params;
 

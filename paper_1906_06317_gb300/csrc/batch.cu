@@ -303,7 +303,7 @@ constexpr int kBatchTileMaxBins = 1024;
 
 // Builds every per-frame table for a cell division, a block size of the per-point kernel
 // and the largest work item of the tile kernels (tile_cells < 0: no tile route), and
-// the query cells per warp of the q_l tile kernel (qbw: 1, 2 or 4; a frame takes the
+// the query cells per warp of the tile kernels (qbw: 1, 2, 4 or 8; a frame takes the
 // largest power of two up to qbw that its grid allows); synchronises.
 static int configure(fgb_batch *b, int cell_div, int block, int tile_cells, int qbw, cudaStream_t s) {
     drop_graph(b);
@@ -669,7 +669,8 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
         return fail(FGB_ERR_INVALID_ARG, "invalid batch parameters");
     if (p.cell_div < 0 || p.cell_div > 2 || p.block < 0 || p.block > 512 || (p.block && p.block % 32) ||
         p.hist_copies < 0 || p.hist_copies > 4 || p.tile_cells < -1 || p.tile_cells > 4096 ||
-        (p.cells_per_warp != 0 && p.cells_per_warp != 1 && p.cells_per_warp != 2 && p.cells_per_warp != 4))
+        (p.cells_per_warp != 0 && p.cells_per_warp != 1 && p.cells_per_warp != 2 && p.cells_per_warp != 4 &&
+         p.cells_per_warp != 8))
         return fail(FGB_ERR_INVALID_ARG, "invalid tuning parameters");
     if (frame_offsets[0] != 0) return fail(FGB_ERR_INVALID_ARG, "frame_offsets[0] must be 0");
     for (int f = 0; f < n_frames; ++f)
@@ -791,7 +792,7 @@ extern "C" int fgb_batch_tune(fgb_batch *b, const float *points, void *stream, f
     std::vector<int> tiles = b->tune_tile ? std::vector<int>{16, 64} : std::vector<int>{b->tile_cells};
     std::vector<int> blocks = b->tune_block ? std::vector<int>{64, 128, 256} : std::vector<int>{b->block};
     std::vector<int> copies = b->tune_copies ? std::vector<int>{1, 2, 4} : std::vector<int>{b->copies};
-    std::vector<int> qbs = b->tune_qb && b->prm.l >= 0 ? std::vector<int>{1, 2, 4} : std::vector<int>{b->qbw};
+    std::vector<int> qbs = b->tune_qb ? std::vector<int>{1, 2, 4, 8} : std::vector<int>{b->qbw};
     cudaEvent_t e0, e1;
     FGB_CUDA(cudaEventCreate(&e0));
     FGB_CUDA(cudaEventCreate(&e1));

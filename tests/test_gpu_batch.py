@@ -45,12 +45,13 @@ def check(b, fr, refs):
 
 # (cell_div, block, hist_copies, tile_cells, cells_per_warp, route): tile_cells -1 puts
 # every frame on the per-point kernel; cell_div 2 makes the RDF half stencil too wide for
-# the tile kernels; tile_cells 1 gives one-cell work items; cells_per_warp 2 and 4 walk
+# the tile kernels; tile_cells 1 gives one-cell work items; cells_per_warp 2, 4 and 8 walk
 # blocks of x-adjacent query cells (shortened at row and work-item ends; frames too narrow
 # take smaller blocks)
 @pytest.mark.parametrize("cell_div,block,copies,tile,qb,route", [
     (1, 128, 2, -1, 1, "per_point"), (2, 64, 1, 0, 1, "per_point"), (1, 256, 4, 0, 1, "tile"),
-    (1, 128, 2, 1, 1, "tile"), (1, 128, 2, 0, 2, "tile"), (1, 128, 2, 0, 4, "tile"), (1, 128, 2, 3, 4, "tile")])
+    (1, 128, 2, 1, 1, "tile"), (1, 128, 2, 0, 2, "tile"), (1, 128, 2, 0, 4, "tile"), (1, 128, 2, 3, 4, "tile"),
+    (1, 128, 2, 0, 8, "tile")])
 def test_batch_matches_oracle(fgb, frames, cell_div, block, copies, tile, qb, route):
     fr, refs = frames
     P = W.C5_PARAMS
@@ -112,7 +113,7 @@ def test_batch_graph_replay_and_tune(fgb, frames):
                   rdf_bins=P["rdf_bins"], rdf_r_max=P["rdf_r_max"])
     chosen = b.tune(pts)
     assert chosen["cell_div"] in (1, 2) and chosen["block"] in (64, 128, 256) and chosen["tile_cells"] in (16, 64)
-    assert chosen["cells_per_warp"] in (1, 2, 4)
+    assert chosen["cells_per_warp"] in (1, 2, 4, 8)
     for _ in range(3):
         b.run(pts, graph=True)
     torch.cuda.synchronize()

@@ -73,7 +73,7 @@ def test_host_side_argument_checks(lib):
     off = np.array([0, 10], np.int64)
     boxes = (fgb.fgb_box * 1)(fgb.fgb_box(10.0, 10.0, 10.0, 0, 0, 0))
     for bad in (dict(tile_cells=-2), dict(tile_cells=5000), dict(cell_div=3), dict(block=48),
-                dict(hist_copies=5), dict(cells_per_warp=3), dict(cells_per_warp=8)):
+                dict(hist_copies=5), dict(cells_per_warp=3), dict(cells_per_warp=16)):
         prm = fgb.fgb_batch_params(1.5, 6, 200, 3.0, 0.0, bad.get("cell_div", 0), bad.get("block", 0),
                                    bad.get("hist_copies", 0), bad.get("tile_cells", 0),
                                    bad.get("cells_per_warp", 0))
