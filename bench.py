@@ -120,30 +120,41 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the top kernels from one ncu capture of the
 # c3 workload at 2,097,152 points (profiles/k_*_c3_2M.md), with the sha256 prefix of the
-# source file of the captured build.  Traffic grows in proportion to N at fixed density,
-# so it is scaled to the bench's N; once the source changes the figure is stale and is
-# reported as null.
+# captured build's sources (the kernel's file, then the tile header it inlines).
+# Traffic grows in proportion to N at fixed density, so it is scaled to the bench's N;
+# once a source changes the figure is stale and is reported as null.
+_NL = ("paper_1906_06317_gb300/csrc/nlist.cu", "paper_1906_06317_gb300/csrc/fgb_tile.cuh")
+_RDF = ("paper_1906_06317_gb300/csrc/rdf.cu", "paper_1906_06317_gb300/csrc/fgb_tile.cuh")
 MEASURED_TRAFFIC = {
-    "k_nl_write": ("paper_1906_06317_gb300/csrc/nlist.cu", "7d2387a7c84b1ef3", 570.487808e6 + 1542.941e6, 2097152),
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "2f8d43fe6199dab6", 34.211072e6 + 0.046e6, 2097152),
+    "k_nl_write": (_NL, "6793fdff82cf7609", 576.290560e6 + 1544.660e6, 2097152),
+    "k_nl_count": (_NL, "6793fdff82cf7609", 42.768896e6 + 0.072e6, 2097152),
+    "k_rdf_tile": (_RDF, "ee9c5aa65dddbe7a", 34.213888e6 + 0.039e6, 2097152),
 }
 
 
 # Shared-atomic wavefronts of the fused RDF as a share of the shared-memory data pipe's
 # peak (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared_op_atom, the same capture).
 MEASURED_SHARED_ATOMICS = {
-    "k_rdf_tile": ("paper_1906_06317_gb300/csrc/rdf.cu", "2f8d43fe6199dab6", 0.1073),
+    "k_rdf_tile": (_RDF, "ee9c5aa65dddbe7a", 0.1174),
 }
+
+
+def _sources_sha(paths) -> str:
+    import hashlib
+    d = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            d.update(f.read())
+    return d.hexdigest()
 
 
 def measured_shared_atomics(kernel: str):
     """Measured fraction of the shared pipe's peak taken by atomics, or None when stale."""
-    import hashlib
     if kernel not in MEASURED_SHARED_ATOMICS:
         return None
-    path, sha, frac = MEASURED_SHARED_ATOMICS[kernel]
+    paths, sha, frac = MEASURED_SHARED_ATOMICS[kernel]
     try:
-        cur = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+        cur = _sources_sha(paths)
     except OSError:
         return None
     return frac if cur.startswith(sha) else None
@@ -151,12 +162,11 @@ def measured_shared_atomics(kernel: str):
 
 def measured_traffic(kernel: str, n: int):
     """Scaled DRAM bytes per launch, or None when unmeasured or the source has changed."""
-    import hashlib
     if kernel not in MEASURED_TRAFFIC:
         return None
-    path, sha, nbytes, n0 = MEASURED_TRAFFIC[kernel]
+    paths, sha, nbytes, n0 = MEASURED_TRAFFIC[kernel]
     try:
-        cur = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+        cur = _sources_sha(paths)
     except OSError:
         return None
     return nbytes * n / n0 if cur.startswith(sha) else None
@@ -545,14 +555,15 @@ def component_only(fgb, torch, dev, stream, flush, which, n_points, steps, warmu
 
 def batch_only(fgb, torch, dev, stream, flush, n_frames, steps, warmup):
     """The c5 frames [0, n_frames) in one batch at fixed settings (cell size r_max, tile
-    items of up to 64 cells), `warmup` then `steps` plain runs (no graph, no tuning): the
-    command behind the batch kernels' launch lists and captures."""
+    items of up to 64 cells, 4 query cells per warp), `warmup` then `steps` plain runs
+    (no graph, no tuning): the command behind the batch kernels' launch lists and
+    captures."""
     frames = W.c5()[:n_frames]
     P = W.C5_PARAMS
     sizes = [len(f.points) for f in frames]
     pts = torch.from_numpy(np.concatenate([f.points for f in frames])).to(dev)
     b = fgb.Batch(sizes, [f.box for f in frames], r_max=P["r_max"], l=P["l"], rdf_bins=P["rdf_bins"],
-                  rdf_r_max=P["rdf_r_max"], cell_div=1, block=128, hist_copies=2, tile_cells=64)
+                  rdf_r_max=P["rdf_r_max"], cell_div=1, block=128, hist_copies=2, tile_cells=64, cells_per_warp=4)
     for _ in range(warmup):
         b.run(pts)
     ms = timed(lambda: b.run(pts), stream, flush, reps=max(steps, 1), warm=0)

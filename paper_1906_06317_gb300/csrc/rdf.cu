@@ -91,6 +91,18 @@ __device__ __forceinline__ int exact_bin(const double *T, int bins, double e) {
     return lo;
 }
 
+// The same bin from a guess: the FP32 bin of sqrt(e), then stepped until
+// T[b] <= e < T[b+1] holds in FP64 (T is increasing, so the result is the unique bin of
+// the binary search; the guess is off by at most one in practice).
+__device__ __forceinline__ int exact_bin_near(const double *T, int bins, double e, float rmin, float invdelta) {
+    if (!(e >= T[0]) || !(e < T[bins])) return -1;
+    int b = (int)((sqrtf((float)e) - rmin) * invdelta);
+    b = min(max(b, 0), bins - 1);
+    while (b > 0 && e < T[b]) --b;
+    while (b + 1 < bins && e >= T[b + 1]) ++b;
+    return b;
+}
+
 // HALF: self query with the half stencil; the pair (t, t) is never visited, so no index
 // test is needed.  Otherwise a self query skips j == i explicitly.
 template <bool SHARED, int MODE, bool HALF>
@@ -166,13 +178,43 @@ __global__ void k_band(const double *__restrict__ T, int n, double delta, float2
     if (b < n) out[b] = make_float2(__double2float_rd(__dsub_rd(T[b], delta)), __double2float_ru(__dadd_ru(T[b], delta)));
 }
 
+// FP64 decisions of the listed band pairs.  SHARED: counted in a shared histogram per
+// block and added to the global counts once per block and bin (the pairs crowd a few
+// hundred bins, where one global atomic per pair contends).
+constexpr int kEscSharedBins = 8192;
+
+template <bool SHARED>
 __global__ void k_rdf_escalated(RdfArgs a) {
+    extern __shared__ uint32_t eh[];  // SHARED: bins
+    if (SHARED) {
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x) eh[b] = 0;
+        __syncthreads();
+    }
     const int n = min(*a.esc_count, a.esc_cap);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int2 p = a.esc[e];
-        const int b = exact_bin(a.T, a.bins, exact_r2_idx(a.bd, a.q_orig, p.x, a.p_orig, p.y));
-        if (b >= 0) atomicAdd(a.hist + b, (unsigned long long)a.weight);
+        const int b =
+            exact_bin_near(a.T, a.bins, exact_r2_idx(a.bd, a.q_orig, p.x, a.p_orig, p.y), a.P.rmin, a.P.invdelta);
+        if (b >= 0) {
+            if (SHARED)
+                atomicAdd(eh + b, 1u);
+            else
+                atomicAdd(a.hist + b, (unsigned long long)a.weight);
+        }
     }
+    if (SHARED) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < a.bins; b += blockDim.x)
+            if (eh[b]) atomicAdd(a.hist + b, (unsigned long long)eh[b] * a.weight);
+    }
+}
+
+static void launch_rdf_escalated(const RdfArgs &a, cudaStream_t s) {
+    FGB_KSCOPE("k_rdf_escalated", s);
+    if (a.bins <= kEscSharedBins)
+        k_rdf_escalated<true><<<num_sms() * 2, 256, (size_t)a.bins * sizeof(uint32_t), s>>>(a);
+    else
+        k_rdf_escalated<false><<<num_sms() * 4, 256, 0, s>>>(a);
 }
 
 // ------------------------------------------------------------------ cell-tile RDF
@@ -686,10 +728,7 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                     else
                         launch_rdf<false>(a, grid, 0, s);
                 }
-                {
-                    FGB_KSCOPE("k_rdf_escalated", s);
-                    k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
-                }
+                launch_rdf_escalated(a, s);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) st = fail(FGB_ERR_CUDA, "rdf launch failed: %s", cudaGetErrorString(e));
             }
@@ -931,10 +970,7 @@ extern "C" int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t 
         launch_rdf<true>(a, grid, smem, s);
     else
         launch_rdf<false>(a, grid, 0, s);
-    {
-        FGB_KSCOPE("k_rdf_escalated", s);
-        k_rdf_escalated<<<num_sms() * 4, 256, 0, s>>>(a);
-    }
+    launch_rdf_escalated(a, s);
     FGB_LAUNCH_CHECK();
     return FGB_OK;
 }
