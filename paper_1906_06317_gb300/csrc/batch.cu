@@ -59,16 +59,26 @@ struct BatchArgs {
 __global__ void k_batch_bin(const FrameDev *__restrict__ frames, const int64_t *__restrict__ frame_off, int nframes,
                             const float *__restrict__ pts, int64_t total, uint32_t *__restrict__ keys,
                             uint32_t *__restrict__ vals, float4 *__restrict__ local) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= total) return;
-    int lo = 0, hi = nframes;  // frame_off[lo] <= g < frame_off[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (frame_off[mid] <= g)
-            lo = mid;
-        else
-            hi = mid;
+    // the frame of the block's first point by binary search (one thread), then each
+    // point's by stepping forward from it (a block's 256 points span few frames)
+    __shared__ int sframe;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nframes;  // frame_off[lo] <= g0 < frame_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (frame_off[mid] <= g0)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        sframe = lo;
     }
+    __syncthreads();
+    const int64_t g = g0 + threadIdx.x;
+    if (g >= total) return;
+    int lo = sframe;
+    while (lo + 1 < nframes && __ldg(frame_off + lo + 1) <= g) ++lo;
     const FrameDev &f = frames[lo];
     GridDev gd = {{f.ball.S.nc[0], f.ball.S.nc[1], f.ball.S.nc[2]}};
     uint32_t key;
@@ -192,16 +202,13 @@ __global__ void k_batch_escalated(BatchArgs a) {
     const int n = min(a.ctl[1], a.esc_cap);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int4 x = a.esc[e];
-        const double r2 = exact_r2_idx(a.frames[x.x].ball.bd, a.pts, x.y, a.pts, x.z);
+        const FrameDev &f = a.frames[x.x];
+        const double r2 = exact_r2_idx(f.ball.bd, a.pts, x.y, a.pts, x.z);
         if (!(r2 >= a.T[0]) || !(r2 < a.T[a.bins])) continue;
-        int lo = 0, hi = a.bins;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.T[mid] <= r2)
-                lo = mid;
-            else
-                hi = mid;
-        }
+        // the bin of the FP32 guess, stepped until the FP64 thresholds bracket r2
+        int lo = min(max((int)((sqrtf((float)r2) - f.P.rmin) * f.P.invdelta), 0), a.bins - 1);
+        while (lo > 0 && r2 < a.T[lo]) --lo;
+        while (lo + 1 < a.bins && r2 >= a.T[lo + 1]) ++lo;
         atomicAdd(a.counts + (int64_t)x.x * a.bins + lo, (unsigned long long)x.w);
     }
 }

@@ -230,7 +230,7 @@ __device__ __forceinline__ void bt_rdf_cell(const BatchTileArgs &a, const FrameT
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kBtW * 32, 6) k_batch_rtile(const __grid_constant__ BatchTileArgs a) {
+__global__ void __launch_bounds__(kBtW * 32, 7) k_batch_rtile(const __grid_constant__ BatchTileArgs a) {
     __shared__ FrameTile sfr[kBtW];
     __shared__ TileStencilT<NS> sts[kBtW];
     __shared__ float4 sq[kBtW][32];
