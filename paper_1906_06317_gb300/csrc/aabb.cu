@@ -18,9 +18,10 @@
 // count, scan and write passes give rows in traversal order; a warp per row then sorts
 // it by point index, so the list equals the cell list's bit for bit.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
-#include "fgb_device.cuh"
+#include "fgb_tile.cuh"
 
 namespace fgb {
 
@@ -34,6 +35,11 @@ struct BvhNode {
 };
 
 constexpr int kBvhStack = 64;  // tree depth is at most 30 code bits + 31 position bits
+
+// The point ranges stored after the n - 1 nodes of a tree over n >= 2 points.
+__host__ __device__ inline int2 *bvh_ranges(BvhNode *nodes, int64_t n) {
+    return reinterpret_cast<int2 *>(nodes + (n - 1));
+}
 
 // Bits of a 10-bit integer spread to every third position.
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
@@ -96,9 +102,10 @@ __device__ __forceinline__ int bvh_delta(const uint32_t *__restrict__ k, int n, 
     return 32 + __clz((uint32_t)i ^ (uint32_t)j);
 }
 
-// Internal node i of the radix tree over n >= 2 sorted keys.
+// Internal node i of the radix tree over n >= 2 sorted keys; range[i] = the sorted
+// positions (first, last) of its points.
 __global__ void k_bvh_nodes(const uint32_t *__restrict__ keys, int n, BvhNode *__restrict__ nodes,
-                            int *__restrict__ parent_int, int *__restrict__ parent_leaf) {
+                            int2 *__restrict__ range, int *__restrict__ parent_int, int *__restrict__ parent_leaf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int d = bvh_delta(keys, n, i, i + 1) > bvh_delta(keys, n, i, i - 1) ? 1 : -1;
@@ -122,6 +129,7 @@ __global__ void k_bvh_nodes(const uint32_t *__restrict__ keys, int n, BvhNode *_
     const int right = hi == g + 1 ? ~(g + 1) : g + 1;
     nodes[i].left = left;
     nodes[i].right = right;
+    range[i] = make_int2(lo, hi);
     if (left < 0)
         parent_leaf[~left] = i;
     else
@@ -174,6 +182,7 @@ struct BvhArgs {
     BoxD bd;
     float w[3];                 // perpendicular widths
     const BvhNode *nodes;       // n - 1 internal nodes (root 0) when n >= 2
+    const int2 *range;          // their point ranges (first, last sorted position)
     const float4 *pts;          // wrapped points in Morton order, index bits in w
     int n;
     const float *p_orig;        // (n, 3) caller's points
@@ -183,6 +192,7 @@ struct BvhArgs {
     int exclude;
     float reach2;               // node boxes farther than this (squared) are skipped
     float reach;                // images whose box distance exceeds this are skipped
+    float group_ext;            // group kernels: a group wider than this is halved
     Band band;                  // FP32 band when neither point of a pair was moved by wrapping
     Band band_wide;             // band when one was (the points' flag or the query's own)
     int pts_moved;              // some point was moved by wrapping
@@ -328,6 +338,240 @@ __global__ void __launch_bounds__(128) k_bvh_write(BvhArgs a, const int64_t *__r
         ++k;
     });
     if (k != want) atomicExch(a.err, 2);
+}
+
+// Squared distance between child c's box (a point for a leaf) and the box [blo, bhi]
+// of a group's queries: every query is at least this far from every point of the child.
+__device__ __forceinline__ float bvh_gap2(const BvhArgs &a, int c, float3 blo, float3 bhi) {
+    float3 l, h;
+    if (c < 0) {
+        const float4 p = __ldg(a.pts + ~c);
+        l = h = make_float3(p.x, p.y, p.z);
+    } else {
+        const BvhNode *cn = a.nodes + c;
+        l = make_float3(__ldg(cn->lo), __ldg(cn->lo + 1), __ldg(cn->lo + 2));
+        h = make_float3(__ldg(cn->hi), __ldg(cn->hi + 1), __ldg(cn->hi + 2));
+    }
+    const float dx = fmaxf(fmaxf(l.x - bhi.x, blo.x - h.x), 0.f);
+    const float dy = fmaxf(fmaxf(l.y - bhi.y, blo.y - h.y), 0.f);
+    const float dz = fmaxf(fmaxf(l.z - bhi.z, blo.z - h.z), 0.f);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// One chunk of staged candidates (c on the lanes, valid when c.w >= 0) against the
+// queries of lanes [l0, l1) in qs (w < 0: no query in this image), four queries per step
+// so that their tests overlap.  Lane t keeps query t's count (cnt) and, when writing,
+// its row start (off) and length (want); a hit's place in the row is the count so far
+// plus the hits of lower lanes.
+template <bool WRITE>
+__device__ __forceinline__ void bvh_chunk(const BvhArgs &a, const float4 *qs, int l0, int l1, float4 c, float lo,
+                                          float hi, unsigned lt, uint32_t &cnt, int64_t off, uint32_t want, int &nesc,
+                                          int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
+                                          float *__restrict__ d_out) {
+    const int lane = threadIdx.x & 31;
+    const int j = __float_as_int(c.w);
+    for (int t0 = l0; t0 < l1; t0 += 4) {
+        bool hit[4];
+        float dist[4], r2[4];
+        bool band = false;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 Q = qs[min(t0 + u, 31)];
+            const int qi = __float_as_int(Q.w);
+            const bool valid = t0 + u < l1 && j >= 0 && qi >= 0 && j != (a.exclude ? qi : -1);
+            r2[u] = r2_f32(c.x - Q.x, c.y - Q.y, c.z - Q.z);
+            hit[u] = valid && r2[u] < lo;
+            band |= valid && r2[u] >= lo && r2[u] < hi;
+            dist[u] = r2[u] > 0.f ? r2[u] * rsqrt_ftz(r2[u]) : 0.f;
+        }
+        if (__any_sync(0xffffffffu, band)) {  // pairs inside the FP32 band: the FP64 decision
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int qi = __float_as_int(qs[min(t0 + u, 31)].w);
+                const bool valid = t0 + u < l1 && j >= 0 && qi >= 0 && j != (a.exclude ? qi : -1);
+                if (valid && r2[u] >= lo && r2[u] < hi) {
+                    ++nesc;
+                    const double e = exact_r2_idx(a.bd, a.q_orig, qi, a.p_orig, j);
+                    hit[u] = e < a.T;
+                    dist[u] = (float)sqrt(e);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u;
+            const unsigned m = __ballot_sync(0xffffffffu, hit[u]);
+            if (m == 0) continue;
+            if (WRITE) {
+                const uint32_t base = __shfl_sync(0xffffffffu, cnt, t);
+                const int64_t row = __shfl_sync(0xffffffffu, off, t);
+                const uint32_t rw = __shfl_sync(0xffffffffu, want, t);
+                const uint32_t pos = base + __popc(m & lt);
+                if (hit[u] && pos < rw) {
+                    qi_out[row + pos] = __float_as_int(qs[t].w);
+                    pj_out[row + pos] = j;
+                    d_out[row + pos] = dist[u];
+                }
+            }
+            if (lane == t) cnt += __popc(m);
+        }
+    }
+}
+
+// Self queries, a warp per group of 32 consecutive points in Morton order: the group's
+// queries are walked down the tree together, a node kept when its box lies within reach
+// of the bounding box of the group's queries (in the current periodic image), and a node
+// of at most 32 points (its range of sorted positions) is taken as a bucket: its points
+// staged into chunks of 32, each chunk against the group's queries in turn, one ballot
+// per query.  A group whose box is wider than twice the radius (the Morton curve jumps
+// between distant regions) is halved until it is not.  The pair decisions and images are those of bvh_visit, so the count
+// and write passes give the same rows as the thread-per-query kernels (in another order
+// before the row sort).
+constexpr int kBvhWarps = 4;
+constexpr int kBvhGroupSoft = 1024;                        // batched expansion below this
+constexpr int kBvhGroupStack = kBvhGroupSoft + kBvhStack;  // + one entry per tree level
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kBvhWarps * 32) k_bvh_group(BvhArgs a, uint32_t *__restrict__ counts,
+                                                              const int64_t *__restrict__ seg,
+                                                              int32_t *__restrict__ qi_out,
+                                                              int32_t *__restrict__ pj_out, float *__restrict__ d_out) {
+    __shared__ float4 sq[kBvhWarps][32];  // the group's queries in the current image (w: index, -1 none)
+    __shared__ int sstk[kBvhWarps][kBvhGroupStack];
+    __shared__ float4 sstg[kBvhWarps][64];  // bucket points staged into chunks of 32
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBvhWarps + warp) * 32;
+    if (g0 >= a.n) return;
+    const int nq = (int)min((int64_t)32, (int64_t)a.n - g0);
+    const bool qv = lane < nq;
+    const float4 r = qv ? __ldg(a.pts + g0 + lane) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    const int i = qv ? __float_as_int(r.w) : -1;
+    const float3 qf = frac_of(a.bf, r.x, r.y, r.z);
+    const float lo = a.pts_moved ? a.band_wide.lo : a.band.lo, hi = a.pts_moved ? a.band_wide.hi : a.band.hi;
+    float4 *qs = sq[warp];
+    int *stk = sstk[warp];
+    float4 *stg = sstg[warp];
+    int nst = 0;       // staged points
+    uint32_t cnt = 0;  // lane t: hits of query t so far
+    const int64_t off = WRITE && qv ? seg[i] : 0;
+    const uint32_t want = WRITE && qv ? counts[i] : 0;
+    const unsigned lt = lanemask_lt();
+    int nesc = 0;
+    // subgroups (lane ranges l0 | l1 << 8), depth first
+    int pend[8];
+    int np = 0;
+    pend[np++] = nq << 8;
+    while (np > 0) {
+        const int rg = pend[--np];
+        const int l0 = rg & 0xff, l1 = rg >> 8;
+        const bool in = lane >= l0 && lane < l1;
+        {
+            float3 blo, bhi;
+            warp_box(r.x, r.y, r.z, in, blo, bhi);
+            const float ext = fmaxf(bhi.x - blo.x, fmaxf(bhi.y - blo.y, bhi.z - blo.z));
+            if (ext > a.group_ext && l1 - l0 > 1) {
+                const int mid = (l0 + l1) >> 1;
+                pend[np++] = mid | (l1 << 8);
+                pend[np++] = l0 | (mid << 8);
+                continue;
+            }
+        }
+        for (int im = 0; im < 27; ++im) {
+            const int sx = im % 3 - 1, sy = (im / 3) % 3 - 1, sz = im / 9 - 1;
+            // as in bvh_visit: this image of the query is at least its largest slab
+            // distance away from the box
+            const float gx = qf.x + sx, gy = qf.y + sy, gz = qf.z + sz;
+            const float ex = fmaxf(fmaxf(-gx, gx - 1.f), 0.f) * a.w[0];
+            const float ey = fmaxf(fmaxf(-gy, gy - 1.f), 0.f) * a.w[1];
+            const float ez = fmaxf(fmaxf(-gz, gz - 1.f), 0.f) * a.w[2];
+            const bool on = in && !(fmaxf(ex, fmaxf(ey, ez)) > a.reach);
+            if (!__any_sync(0xffffffffu, on)) continue;
+            const float qx = r.x + (float)sx * a.bf.L[0] + (float)sy * a.bf.a2x + (float)sz * a.bf.a3x;
+            const float qy = r.y + (float)sy * a.bf.L[1] + (float)sz * a.bf.a3y;
+            const float qz = r.z + (float)sz * a.bf.L[2];
+            __syncwarp();
+            qs[lane] = on ? make_float4(qx, qy, qz, __int_as_float(i)) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            float3 blo, bhi;
+            warp_box(qx, qy, qz, on, blo, bhi);
+            // Depth first in batches: the top nodes of the warp's stack (up to 32, one
+            // per lane) are expanded at once, their children within reach of the box
+            // pushed back, nodes of at most 32 points kept as buckets.  Above the soft
+            // capacity one node is expanded at a time, which adds at most one entry per
+            // tree level, so the stack stays within kBvhGroupStack.
+            if (lane == 0) stk[0] = a.n >= 2 ? 0 : ~0;
+            int sp = 1;
+            __syncwarp();
+            for (int64_t steps = 0; sp > 0; ++steps) {
+                if (steps > 2 * (int64_t)a.n + 2 || sp + 2 > kBvhGroupStack) {
+                    if (lane == 0) atomicExch(a.err, steps > 2 * (int64_t)a.n + 2 ? 4 : 3);
+                    break;
+                }
+                const int k = sp + 32 <= kBvhGroupSoft ? min(32, sp) : 1;
+                const int node = lane < k ? stk[sp - k + lane] : 0;
+                sp -= k;
+                __syncwarp();
+                bool bucket = false, t0 = false, t1 = false;
+                int bfirst = 0, bcount = 0, c0 = 0, c1 = 0;
+                if (lane < k) {
+                    if (node < 0) {
+                        bucket = true;
+                        bfirst = ~node;
+                        bcount = 1;
+                    } else {
+                        const int2 rn = __ldg(a.range + node);
+                        bucket = rn.y - rn.x < 32;
+                        bfirst = rn.x;
+                        bcount = rn.y - rn.x + 1;
+                    }
+                    if (!bucket) {
+                        const BvhNode *nd = a.nodes + node;
+                        c0 = __ldg(&nd->left);
+                        c1 = __ldg(&nd->right);
+                        t0 = bvh_gap2(a, c0, blo, bhi) <= a.reach2;
+                        t1 = bvh_gap2(a, c1, blo, bhi) <= a.reach2;
+                    }
+                }
+                const unsigned m0 = __ballot_sync(0xffffffffu, t0), m1 = __ballot_sync(0xffffffffu, t1);
+                if (t0) stk[sp + __popc(m0 & lt)] = c0;
+                if (t1) stk[sp + __popc(m0) + __popc(m1 & lt)] = c1;
+                sp += __popc(m0) + __popc(m1);
+                __syncwarp();
+                for (unsigned mb = __ballot_sync(0xffffffffu, bucket); mb; mb &= mb - 1) {
+                    const int src = __ffs(mb) - 1;
+                    const int bf = __shfl_sync(0xffffffffu, bfirst, src), bc = __shfl_sync(0xffffffffu, bcount, src);
+                    // the bucket's points join the stage; each full chunk of 32 is tested
+                    if (lane < bc) stg[nst + lane] = __ldg(a.pts + bf + lane);
+                    nst += bc;
+                    if (nst >= 32) {
+                        __syncwarp();
+                        bvh_chunk<WRITE>(a, qs, l0, l1, stg[lane], lo, hi, lt, cnt, off, want, nesc, qi_out, pj_out,
+                                         d_out);
+                        const float4 rest = stg[32 + lane];
+                        __syncwarp();
+                        if (lane < nst - 32) stg[lane] = rest;
+                        nst -= 32;
+                        __syncwarp();
+                    }
+                }
+            }
+            if (nst > 0) {  // the image's last, partial chunk
+                __syncwarp();
+                const float4 c = lane < nst ? stg[lane] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                bvh_chunk<WRITE>(a, qs, l0, l1, c, lo, hi, lt, cnt, off, want, nesc, qi_out, pj_out, d_out);
+                nst = 0;
+                __syncwarp();
+            }
+        }
+    }
+    if (qv) {
+        if (WRITE) {
+            if (cnt != want) atomicExch(a.err, 2);
+        } else {
+            counts[i] = cnt;
+        }
+    }
+    nesc = __reduce_add_sync(0xffffffffu, nesc);
+    if (!WRITE && lane == 0 && nesc) atomicAdd(a.esc, (unsigned long long)nesc);
 }
 
 // ------------------------------------------------------------------ k nearest
@@ -547,6 +791,20 @@ __global__ void __launch_bounds__(64) k_bvh_knn_exact(BvhKnn a) {
 
 static int grid1d(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+// Blocks of kBvhWarps warps, one per 32 queries.
+static unsigned group_grid(int64_t nq) { return (unsigned)(((nq + 31) / 32 + kBvhWarps - 1) / kBvhWarps); }
+
+// FGB_BVH_GROUP=0 keeps self queries on the thread-per-query kernels (comparisons, and
+// tests of those kernels).
+static bool group_kernels() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FGB_BVH_GROUP");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 int aabb_build(fgb_nq *nq, cudaStream_t s) {
     const int64_t n = nq->n;
     nq->kind = 1;
@@ -572,7 +830,9 @@ int aabb_build(fgb_nq *nq, cudaStream_t s) {
         st = radix_sort_cells(keys, vals, n, (int64_t)1 << 30, rec, nq->sorted, nq->sorted_cell, ws, s);
     }
     if (st == FGB_OK && n >= 2) {
-        st = dalloc_n(&nodes, n - 1, s);
+        // the n - 1 nodes, then their n - 1 point ranges (int2), in one block
+        static_assert(sizeof(BvhNode) % sizeof(int2) == 0, "ranges follow the nodes");
+        st = dalloc(reinterpret_cast<void **>(&nodes), (size_t)(n - 1) * (sizeof(BvhNode) + sizeof(int2)), s);
         st = st ? st : dalloc_n(&parent_int, n - 1, s);
         st = st ? st : dalloc_n(&parent_leaf, n, s);
         st = st ? st : dalloc_n(&flags, n - 1, s);
@@ -580,7 +840,8 @@ int aabb_build(fgb_nq *nq, cudaStream_t s) {
             FGB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * (n - 1), s));
             {
                 FGB_KSCOPE("k_bvh_nodes", s);
-                k_bvh_nodes<<<grid1d(n - 1, 256), 256, 0, s>>>(nq->sorted_cell, (int)n, nodes, parent_int, parent_leaf);
+                k_bvh_nodes<<<grid1d(n - 1, 256), 256, 0, s>>>(nq->sorted_cell, (int)n, nodes,
+                                                               bvh_ranges(nodes, n), parent_int, parent_leaf);
             }
             {
                 FGB_KSCOPE("k_bvh_refit", s);
@@ -631,6 +892,7 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
     a.bd = b.d;
     for (int k = 0; k < 3; ++k) a.w[k] = (float)b.w[k];
     a.nodes = static_cast<const BvhNode *>(nq->bvh);
+    a.range = nq->n >= 2 ? bvh_ranges(static_cast<BvhNode *>(nq->bvh), nq->n) : nullptr;
     a.pts = nq->sorted;
     a.n = (int)nq->n;
     a.p_orig = nq->points;
@@ -658,6 +920,7 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
     a.pts_moved = nq->bvh_moved;
     a.reach2 = a.band_wide.hi * (1.0f + 1e-5f) + 1e-30f;
     a.reach = (float)(R * (1.0 + 1e-4) + 1e-5 * Lsum);
+    a.group_ext = (float)(2.0 * R);
     struct Status {
         unsigned long long esc;
         int err;
@@ -677,7 +940,10 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
     memset(&hs, 0, sizeof(hs));
     int64_t total = 0;
     if (st == FGB_OK && nqq > 0) {
-        {
+        if (self && group_kernels()) {
+            FGB_KSCOPE("k_bvh_group_count", s);
+            k_bvh_group<false><<<group_grid(nqq), kBvhWarps * 32, 0, s>>>(a, counts, nullptr, nullptr, nullptr, nullptr);
+        } else {
             FGB_KSCOPE("k_bvh_count", s);
             k_bvh_count<<<grid1d(nqq, 128), 128, 0, s>>>(a, counts);
         }
@@ -702,7 +968,11 @@ int aabb_ball_query(fgb_nq *nq, const float *query_points, int64_t n_query, cons
     st = st ? st : dalloc_n(&nl->pj, total, s);
     st = st ? st : dalloc_n(&nl->dist, total, s);
     if (st == FGB_OK && total > 0) {
-        {
+        if (self && group_kernels()) {
+            FGB_KSCOPE("k_bvh_group_write", s);
+            k_bvh_group<true><<<group_grid(nqq), kBvhWarps * 32, 0, s>>>(a, counts, nl->segments, nl->qi, nl->pj,
+                                                                         nl->dist);
+        } else {
             FGB_KSCOPE("k_bvh_write", s);
             k_bvh_write<<<grid1d(nqq, 128), 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
         }

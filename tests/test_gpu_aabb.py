@@ -190,3 +190,32 @@ def test_tree_knn_ties_outside_points_and_query_points(fgb):
     with pytest.raises(fgb.FGBError) as e:  # 5 points spread over the box: a 4th neighbor too far
         fgb.AABBQuery(b3, dev(W.small_random(112, 5, b3))).query(None, dict(num_neighbors=4)).toNeighborList()
     assert e.value.code == fgb.ERR_BOX_TOO_SMALL
+
+
+TREE_THREAD_CHECK = r"""
+import numpy as np, torch, oracle, workloads as W, paper_1906_06317_gb300 as fgb
+b = W.Box(12.0, 10.0, 11.0, -0.2, 0.2, 0.15)
+x = W.small_random(64, 5000, b)
+aq = fgb.AABBQuery(b, torch.from_numpy(x).cuda())
+for r in (0.9, 2.3):
+    for excl in (True, False):
+        nl = aq.query(None, dict(r_max=r, exclude_ii=excl)).toNeighborList()
+        _, off, pj, d = oracle.ball_query(b, x, r, exclude_ii=excl)
+        assert np.array_equal(nl.segments.cpu().numpy(), off)
+        assert np.array_equal(nl.point_indices.cpu().numpy(), pj)
+        assert np.all(np.abs(nl.distances.cpu().numpy() - d) <= 2e-6 * r + 1e-7)
+print("ok")
+"""
+
+
+def test_tree_thread_per_query_kernels(fgb):
+    # self queries take the warp-per-group walk by default; FGB_BVH_GROUP=0 keeps them on
+    # the thread-per-query kernels, which other query sets use
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root, FGB_BVH_GROUP="0")
+    r = subprocess.run([sys.executable, "-c", TREE_THREAD_CHECK], env=env, cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]
