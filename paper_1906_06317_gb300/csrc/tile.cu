@@ -916,11 +916,11 @@ __device__ __forceinline__ void knn_finish_row(const uint2 *row, int cnt, int m,
 // of its points are staged once (at most kKnnStage; a cell with more lists its queries),
 // then each query in turn takes them 32 at a time, its hits packed into the row by
 // ballot positions.
-constexpr int kKnnStage = 384;
+constexpr int kKnnStage = 256;
 constexpr int kKnnOwnCap = 512;
 
 template <int NS>
-__global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, KnnTile K) {
+__global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_knn(TileArgs a, KnnTile K) {
     __shared__ TileStencilT<NS> sts[kTileWarps];
     __shared__ float4 sstage[kTileWarps][kKnnStage + 32];
     __shared__ uint2 srowbuf[kTileWarps][64];
@@ -980,8 +980,10 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_knn(TileArgs a, Knn
     if (kept + lane < ((kept + 31) & ~31)) stage[kept + lane] = make_float4(kFar, kFar, kFar, __int_as_float(-1));
     __syncwarp();
     const int nch = (kept + 31) >> 5;
+    float4 Qn = __ldg(a.pts + begA);  // the next query's record, loaded a query ahead
     for (int t = 0; t < nA; ++t) {
-        const float4 Q = __ldg(a.pts + begA + t);
+        const float4 Q = Qn;
+        if (t + 1 < nA) Qn = __ldg(a.pts + begA + t + 1);
         const int iL = __float_as_int(Q.w);
         const int excl = a.exclude ? iL : -1;
         int cnt = 0;
