@@ -916,11 +916,11 @@ __device__ __forceinline__ void knn_finish_row(const uint2 *row, int cnt, int m,
 // of its points are staged once (at most kKnnStage; a cell with more lists its queries),
 // then each query in turn takes them 32 at a time, its hits packed into the row by
 // ballot positions.
-constexpr int kKnnStage = 256;
+constexpr int kKnnStage = 224;
 constexpr int kKnnOwnCap = 512;
 
 template <int NS>
-__global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_knn(TileArgs a, KnnTile K) {
+__global__ void __launch_bounds__(kTileWarps * 32, 9) k_tile_knn(TileArgs a, KnnTile K) {
     __shared__ TileStencilT<NS> sts[kTileWarps];
     __shared__ float4 sstage[kTileWarps][kKnnStage + 32];
     __shared__ uint2 srowbuf[kTileWarps][64];
