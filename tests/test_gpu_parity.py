@@ -466,6 +466,9 @@ c = W.Box.cube(20.0)
 blob = (np.random.default_rng(7).normal(size=(900, 3)) * 0.3).astype(np.float32)
 xd = np.concatenate([W.small_random(50, 2000, c), blob, blob[:50]]).astype(np.float32)
 ball(c, xd, 1.5, 1.5); rdf(c, xd, 100, 3.0, 3.0)
+g = np.stack(np.meshgrid(*[np.arange(-8, 8)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float32) * 0.5
+rdf(W.Box.cube(16.0), g, 16, 4.0, 2.0)       # thousands of pairs on bin edges
+ball(W.Box.cube(16.0), g, 1.0, 1.0)          # and exactly on r_max
 k = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
 _, kj, _ = oracle.knn(b, x, 12)
 assert np.array_equal(k.point_indices.cpu().numpy().reshape(-1, 12), kj[:, :12])

@@ -70,3 +70,19 @@ def test_noalloc_rejects_sizes_beyond_its_limit(fgb):
     with pytest.raises(fgb.FGBError) as e:
         noalloc_counts(fgb, box, small, 8193, 2.0, 0.0)
     assert e.value.code == fgb.ERR_CAPACITY
+
+
+def test_noalloc_2d_frame_and_general_stencil(fgb):
+    # a 2D frame (its points on the z = 0 layer) and a box too small for the 27-cell
+    # shift stencil (two cells per axis, so the library takes its general stencil
+    # route), each compared with the allocating path and the oracle
+    sq = W.Box.square(30.0, 0.1)
+    x2 = W.small_random(73, 9000, sq)
+    small = W.Box.cube(9.0)
+    xs = W.small_random(74, 2500, small)
+    for box, x, bins, r_max in ((sq, x2, 120, 6.0), (small, xs, 50, 4.0)):
+        pts = torch.from_numpy(x).cuda()
+        got = noalloc_counts(fgb, box, pts, bins, r_max, 0.0)
+        assert np.array_equal(got, allocating_counts(fgb, box, pts, bins, r_max, 0.0))
+        assert np.array_equal(got, oracle.rdf_counts(box, x, bins, r_max, 0.0))
+        assert got.sum() > 0
