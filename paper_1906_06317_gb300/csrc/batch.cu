@@ -56,28 +56,20 @@ struct BatchArgs {
     int32_t *nn;
 };
 
-__global__ void k_batch_bin(const FrameDev *__restrict__ frames, const int64_t *__restrict__ frame_off, int nframes,
-                            const float *__restrict__ pts, int64_t total, uint32_t *__restrict__ keys,
-                            uint32_t *__restrict__ vals, float4 *__restrict__ local) {
-    // the frame of the block's first point by binary search (one thread), then each
-    // point's by stepping forward from it (a block's 256 points span few frames)
-    __shared__ int sframe;
-    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = nframes;  // frame_off[lo] <= g0 < frame_off[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (frame_off[mid] <= g0)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        sframe = lo;
-    }
-    __syncthreads();
-    const int64_t g = g0 + threadIdx.x;
+// Blocks of kBinBlock points; blk_frame[b] is the frame of block b's first point (set
+// at create time), and each point finds its own by stepping forward from it (a block's
+// points span few frames).
+constexpr int kBinBlock = 256;
+
+__global__ void __launch_bounds__(kBinBlock) k_batch_bin(const FrameDev *__restrict__ frames,
+                                                         const int64_t *__restrict__ frame_off,
+                                                         const int32_t *__restrict__ blk_frame, int nframes,
+                                                         const float *__restrict__ pts, int64_t total,
+                                                         uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                         float4 *__restrict__ local) {
+    const int64_t g = (int64_t)blockIdx.x * kBinBlock + threadIdx.x;
     if (g >= total) return;
-    int lo = sframe;
+    int lo = __ldg(blk_frame + blockIdx.x);
     while (lo + 1 < nframes && __ldg(frame_off + lo + 1) <= g) ++lo;
     const FrameDev &f = frames[lo];
     GridDev gd = {{f.ball.S.nc[0], f.ball.S.nc[1], f.ball.S.nc[2]}};
@@ -255,6 +247,8 @@ struct fgb_batch {
     int64_t ncell_total;
     // fixed device state
     int64_t *off_d;
+    int32_t *blk_d;               // frame of the first point of each binning block
+    std::vector<int32_t> blk;
     double *T_d;
     std::vector<double> T_h;
     int *ctl;
@@ -625,8 +619,8 @@ static int enqueue(fgb_batch *b, const float *pts, cudaStream_t s) {
     if (n > 0) {
         {
             FGB_KSCOPE("k_batch_bin", s);
-            k_batch_bin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b->frames_d, b->off_d, F, pts, n, b->keys, b->vals,
-                                                                   b->local);
+            k_batch_bin<<<(unsigned)((n + kBinBlock - 1) / kBinBlock), kBinBlock, 0, s>>>(
+                b->frames_d, b->off_d, b->blk_d, F, pts, n, b->keys, b->vals, b->local);
         }
         FGB_TRY(radix_sort_cells(b->keys, b->vals, n, b->ncell_total, b->local, b->sorted, b->skeys, b->sort_ws, s));
     }
@@ -705,7 +699,15 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
     const int64_t n = b->total;
     const int L = p.l < 0 ? 0 : p.l;
     b->esc_cap = (int)std::min<int64_t>(std::max<int64_t>(n, 1 << 16), 1 << 26);
+    // frame of each binning block's first point: the last frame starting at or before it
+    b->blk.resize((size_t)std::max<int64_t>((n + kBinBlock - 1) / kBinBlock, 1));
+    for (size_t k = 0; k < b->blk.size(); ++k) {
+        const int64_t g0 = (int64_t)k * kBinBlock;
+        b->blk[k] = (int32_t)(std::upper_bound(b->off.begin(), b->off.end(), g0) - b->off.begin() - 1);
+        b->blk[k] = std::min(std::max(b->blk[k], 0), n_frames - 1);
+    }
     int st = dalloc_n(&b->off_d, n_frames + 1, s);
+    st = st ? st : dalloc_n(&b->blk_d, b->blk.size(), s);
     st = st ? st : dalloc_n(&b->T_d, bins + 1, s);
     st = st ? st : dalloc_n(&b->ctl, 4, s);
     st = st ? st : dalloc_n(&b->keys, n, s);
@@ -724,6 +726,7 @@ extern "C" int fgb_batch_create(int32_t n_frames, const int64_t *frame_offsets, 
     if (st == FGB_OK) st = batch_tile_init(std::min(bins, kBatchTileMaxBins), p.l, &b->tl);
     if (st == FGB_OK) {
         cudaMemcpyAsync(b->off_d, frame_offsets, sizeof(int64_t) * (n_frames + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(b->blk_d, b->blk.data(), sizeof(int32_t) * b->blk.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(b->T_d, b->T_h.data(), sizeof(double) * (bins + 1), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(b->qesc, 0, 2 * sizeof(unsigned long long), s);
         st = configure(b, p.cell_div ? p.cell_div : 1, p.block ? p.block : 128, p.tile_cells ? p.tile_cells : 64,
@@ -744,6 +747,7 @@ extern "C" void fgb_batch_destroy(fgb_batch *b) {
     free_config(b, s);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     dfree(b->off_d, s);
+    dfree(b->blk_d, s);
     dfree(b->T_d, s);
     dfree(b->ctl, s);
     dfree(b->keys, s);
