@@ -21,7 +21,7 @@ bool force_thread_kernels() {
 
 // FGB_SPLIT_KERNELS=0 keeps few-query grids on the one-thread-per-query kernels instead
 // of the 8-lanes-per-query ones (so that both stay covered by tests).
-static bool split_kernels_enabled() {
+bool split_kernels_enabled() {
     static int v = -1;
     if (v < 0) {
         const char *e = getenv("FGB_SPLIT_KERNELS");

@@ -256,6 +256,7 @@ bool tile_ok(const StencilPlan &p);
 // few crowded cells runs faster one thread per query).
 bool tile_worth(const fgb_nq *nq);
 bool force_thread_kernels();
+bool split_kernels_enabled();
 // FGB_TILE_KERNELS=1: the cell-tile kernels wherever they apply, however small the grid.
 bool force_tile_kernels();
 int tile_count(const fgb_nq *nq, const StencilPlan &p, double R, int exclude, unsigned long long *esc, int *err,

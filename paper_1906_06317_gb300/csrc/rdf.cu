@@ -104,15 +104,20 @@ __device__ __forceinline__ int exact_bin_near(const double *T, int bins, double 
 }
 
 // HALF: self query with the half stencil; the pair (t, t) is never visited, so no index
-// test is needed.  Otherwise a self query skips j == i explicitly.
-template <bool SHARED, int MODE, bool HALF>
+// test is needed.  Otherwise a self query skips j == i explicitly.  LANES consecutive
+// threads share a query (few queries: a small grid), thread g of the group taking the
+// candidates beg + g, beg + g + LANES, ... of every stencil cell, so each candidate is
+// still tested once.
+template <bool SHARED, int MODE, bool HALF, int LANES>
 __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
     extern __shared__ uint32_t sh[];  // copies * bins
     if (SHARED) {
         for (int b = threadIdx.x; b < a.bins * a.copies; b += blockDim.x) sh[b] = 0;
         __syncthreads();
     }
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = tt / LANES;
+    const uint32_t g = (uint32_t)(tt % LANES);
     uint32_t *my = sh + ((threadIdx.x >> 5) % a.copies) * a.bins;
     if (t < a.nq) {
         const float4 q = a.qs[t];
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
                         const uint32_t end = __ldg(a.cell_start + cell + 1);
                         if (HALF && center) beg = max(beg, (uint32_t)t + 1u);
 #pragma unroll 2
-                        for (uint32_t p = beg; p < end; ++p) {
+                        for (uint32_t p = beg + g; p < end; p += LANES) {
                             const float4 c = __ldg(a.pts + p);
                             const float3 d = cand_disp_m<MODE>(a.bf, c, qx, qy, qz);
                             const float r2 = r2_f32(d.x, d.y, d.z);
@@ -161,15 +166,25 @@ __global__ void __launch_bounds__(256) k_rdf(RdfArgs a) {
     }
 }
 
-template <bool SHARED>
-static void launch_rdf(const RdfArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
-    FGB_KSCOPE("k_rdf", s);
+template <bool SHARED, int LANES>
+static void launch_rdf_lanes(const RdfArgs &a, size_t smem, cudaStream_t s) {
+    const unsigned grid = (unsigned)((a.nq * LANES + 255) / 256);
     if (a.half)
-        k_rdf<SHARED, 0, true><<<grid, 256, smem, s>>>(a);
+        k_rdf<SHARED, 0, true, LANES><<<grid, 256, smem, s>>>(a);
     else if (a.S.mode == 0)
-        k_rdf<SHARED, 0, false><<<grid, 256, smem, s>>>(a);
+        k_rdf<SHARED, 0, false, LANES><<<grid, 256, smem, s>>>(a);
     else
-        k_rdf<SHARED, 1, false><<<grid, 256, smem, s>>>(a);
+        k_rdf<SHARED, 1, false, LANES><<<grid, 256, smem, s>>>(a);
+}
+
+// Fewer than 128 queries per SM: 8 threads per query (FGB_SPLIT_KERNELS=0: one).
+template <bool SHARED>
+static void launch_rdf(const RdfArgs &a, size_t smem, cudaStream_t s) {
+    FGB_KSCOPE("k_rdf", s);
+    if (a.nq < (int64_t)num_sms() * 128 && split_kernels_enabled())
+        launch_rdf_lanes<SHARED, 8>(a, smem, s);
+    else
+        launch_rdf_lanes<SHARED, 1>(a, smem, s);
 }
 
 // Band around each exact edge threshold, rounded outward.
@@ -722,11 +737,10 @@ extern "C" int fgb_rdf_compute(fgb_rdf *r, fgb_nq *nq, const float *query_points
                     while (copies > 1 && (size_t)copies * r->bins * 4 > 32 * 1024) copies >>= 1;
                     const size_t smem = (size_t)copies * r->bins * 4;
                     a.copies = copies;
-                    const unsigned grid = (unsigned)((nqq + block - 1) / block);
                     if (smem <= 48 * 1024)
-                        launch_rdf<true>(a, grid, smem, s);
+                        launch_rdf<true>(a, smem, s);
                     else
-                        launch_rdf<false>(a, grid, 0, s);
+                        launch_rdf<false>(a, 0, s);
                 }
                 launch_rdf_escalated(a, s);
                 cudaError_t e = cudaGetLastError();
@@ -965,11 +979,10 @@ extern "C" int fgb_rdf_noalloc(const fgb_box *box, const float *points, int64_t 
     while (copies > 1 && (size_t)copies * bins * 4 > 32 * 1024) copies >>= 1;
     const size_t smem = (size_t)copies * bins * 4;
     a.copies = copies;
-    const unsigned grid = (unsigned)((n + 255) / 256);
     if (smem <= 48 * 1024)
-        launch_rdf<true>(a, grid, smem, s);
+        launch_rdf<true>(a, smem, s);
     else
-        launch_rdf<false>(a, grid, 0, s);
+        launch_rdf<false>(a, 0, s);
     launch_rdf_escalated(a, s);
     FGB_LAUNCH_CHECK();
     return FGB_OK;
