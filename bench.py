@@ -128,7 +128,7 @@ _RDF = ("paper_1906_06317_gb300/csrc/rdf.cu", "paper_1906_06317_gb300/csrc/fgb_t
 MEASURED_TRAFFIC = {
     "k_nl_write": (_NL, "6793fdff82cf7609", 576.290560e6 + 1544.660e6, 2097152),
     "k_nl_count": (_NL, "6793fdff82cf7609", 42.768896e6 + 0.072e6, 2097152),
-    "k_rdf_tile": (_RDF, "ee9c5aa65dddbe7a", 34.213888e6 + 0.039e6, 2097152),
+    "k_rdf_tile": (_RDF, "3eddbba7d02e9b5d", 34.218496e6 + 0.005888e6, 2097152),
 }
 
 

@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(128) k_ball_write(BallArgs a, const int64_t *_
 // Few queries (a small grid): G consecutive lanes share one query, lane g taking the
 // candidates beg + g, beg + g + G, ... of every stencil cell (coalesced across the
 // group), so the GPU holds G times as many warps.  Pairs are decided exactly as in the
-// single-lane walks.
+// single-lane walks.  G = 8 below 128 queries per SM, a whole warp below 32.
 
 constexpr int kSplitG = 8;
 
-template <int MODE, bool CHECKJ, class F>
+template <int MODE, bool CHECKJ, int G, class F>
 __device__ __forceinline__ void split_walk(const BallArgs &a, float4 q, uint32_t qc, int i, int g, F &&fn) {
     int cx, cy, cz;
     cell_coords(qc, a.S.nc, cx, cy, cz);
@@ -165,7 +165,7 @@ __device__ __forceinline__ void split_walk(const BallArgs &a, float4 q, uint32_t
     for_stencil(a.S, cx, cy, cz, make_float3(q.x, q.y, q.z), false,
                 [&](int cell, float qx, float qy, float qz, bool) {
                     const uint32_t beg = __ldg(a.cell_start + cell), end = __ldg(a.cell_start + cell + 1);
-                    for (uint32_t p = beg + (uint32_t)g; p < end; p += kSplitG) {
+                    for (uint32_t p = beg + (uint32_t)g; p < end; p += G) {
                         const float4 c = __ldg(a.pts + p);
                         const float3 d = cand_disp_m<MODE>(a.bf, c, qx, qy, qz);
                         const float r2 = r2_f32(d.x, d.y, d.z);
@@ -183,40 +183,40 @@ __device__ __forceinline__ void split_walk(const BallArgs &a, float4 q, uint32_t
                 });
 }
 
-// Neighbor count of every query (kSplitG lanes per query).
-template <int MODE>
+// Neighbor count of every query (G lanes per query).
+template <int MODE, int G>
 __global__ void __launch_bounds__(128) k_ball_count_split(BallArgs a, uint32_t *__restrict__ counts) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t qx = t / kSplitG;
-    const int g = (int)(t % kSplitG);
+    const int64_t qx = t / G;
+    const int g = (int)(t % G);
     const bool act = qx < a.nq;
     uint32_t cnt = 0;
     int nesc = 0, i = -1;
     if (act) {
         const float4 q = a.qs[qx];
         i = __float_as_int(q.w);
-        split_walk<MODE, true>(a, q, a.qcell[qx], i, g, [&](int j, int esc) {
+        split_walk<MODE, true, G>(a, q, a.qcell[qx], i, g, [&](int j, int esc) {
             nesc += esc;
             cnt += j >= 0 ? 1u : 0u;
         });
     }
 #pragma unroll
-    for (int o = kSplitG / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    for (int o = G / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (act && g == 0) counts[i] = cnt;
     if (nesc) atomicAdd(a.esc, (unsigned long long)nesc);
 }
 
-// Rows of every query (kSplitG lanes per query), unsorted: each lane counts its share,
+// Rows of every query (G lanes per query), unsorted: each lane counts its share,
 // takes its offset in the row from an exclusive scan over the group, and writes its
 // neighbors there (bounded by the row's count); sort_segments sorts the rows.
-template <int MODE>
+template <int MODE, int G>
 __global__ void __launch_bounds__(128) k_ball_write_split(BallArgs a, const int64_t *__restrict__ seg,
                                                           const uint32_t *__restrict__ counts,
                                                           int32_t *__restrict__ qi_out, int32_t *__restrict__ pj_out,
                                                           float *__restrict__ d_out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t qx = t / kSplitG;
-    const int g = (int)(t % kSplitG);
+    const int64_t qx = t / G;
+    const int g = (int)(t % G);
     const bool act = qx < a.nq;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t qc = 0, mine = 0;
@@ -225,22 +225,22 @@ __global__ void __launch_bounds__(128) k_ball_write_split(BallArgs a, const int6
         q = a.qs[qx];
         qc = a.qcell[qx];
         i = __float_as_int(q.w);
-        split_walk<MODE, true>(a, q, qc, i, g, [&](int j, int) { mine += j >= 0 ? 1u : 0u; });
+        split_walk<MODE, true, G>(a, q, qc, i, g, [&](int j, int) { mine += j >= 0 ? 1u : 0u; });
     }
     uint32_t inc = mine;
 #pragma unroll
-    for (int d = 1; d < kSplitG; d <<= 1) {
+    for (int d = 1; d < G; d <<= 1) {
         const uint32_t u = __shfl_up_sync(0xffffffffu, inc, d);
         if (g >= d) inc += u;
     }
     if (!act) return;
     const int64_t off = seg[i];
     const uint32_t want = counts[i];
-    if (g == kSplitG - 1 && inc != want) atomicExch(a.err, 2);
+    if (g == G - 1 && inc != want) atomicExch(a.err, 2);
     const float xi0 = __ldg(a.q_orig + 3 * (int64_t)i), xi1 = __ldg(a.q_orig + 3 * (int64_t)i + 1),
                 xi2 = __ldg(a.q_orig + 3 * (int64_t)i + 2);
     uint32_t n = inc - mine;
-    split_walk<MODE, true>(a, q, qc, i, g, [&](int j, int) {
+    split_walk<MODE, true, G>(a, q, qc, i, g, [&](int j, int) {
         if (j < 0) return;
         if (n < want) {
             const float3 d = bond_f32v(a.bf, xi0, xi1, xi2, __ldg(a.p_orig + 3 * (int64_t)j),
@@ -364,6 +364,7 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     const bool tile = Q.self && tile_ok(plan) && tile_worth(nq) && (nq->walk_set || !force_thread_kernels());
     // few queries: several lanes per query (the single-lane kernels would leave most SMs idle)
     const bool split = !tile && nqq < (int64_t)num_sms() * 128 && split_kernels_enabled();
+    const int split_g = nqq < (int64_t)num_sms() * 32 ? 32 : kSplitG;
     if (st == FGB_OK && nqq > 0 && tile) {
         // 2D: the tile kernels walk only the points' layer; a point off the plane keeps a
         // count of zero instead of an unwritten one
@@ -377,11 +378,12 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
     } else if (st == FGB_OK && nqq > 0 && split) {
         {
             FGB_KSCOPE("k_ball_count_split", s);
-            const unsigned g2 = (unsigned)((nqq * kSplitG + 127) / 128);
-            if (a.S.mode == 0)
-                k_ball_count_split<0><<<g2, 128, 0, s>>>(a, counts);
+            const unsigned g2 = (unsigned)((nqq * split_g + 127) / 128);
+            if (split_g == 32)
+                (a.S.mode == 0 ? k_ball_count_split<0, 32> : k_ball_count_split<1, 32>)<<<g2, 128, 0, s>>>(a, counts);
             else
-                k_ball_count_split<1><<<g2, 128, 0, s>>>(a, counts);
+                (a.S.mode == 0 ? k_ball_count_split<0, kSplitG>
+                               : k_ball_count_split<1, kSplitG>)<<<g2, 128, 0, s>>>(a, counts);
         }
         st = scan_u32_i64(counts, nl->segments, nqq, &dst->maxcount, s);
     } else if (st == FGB_OK && nqq > 0) {
@@ -431,11 +433,11 @@ static int ball_query(fgb_nq *nq, const QueryPoints &Q, const fgb_query_args *ar
             // row by one warp costs O(row^2) and held c1's 268-entry rows to 128 warps)
             if (split) {
                 FGB_KSCOPE("k_ball_write_split", s);
-                const unsigned g2 = (unsigned)((nqq * kSplitG + 127) / 128);
-                if (a.S.mode == 0)
-                    k_ball_write_split<0><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
-                else
-                    k_ball_write_split<1><<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
+                const unsigned g2 = (unsigned)((nqq * split_g + 127) / 128);
+                auto kern = split_g == 32 ? (a.S.mode == 0 ? k_ball_write_split<0, 32> : k_ball_write_split<1, 32>)
+                                          : (a.S.mode == 0 ? k_ball_write_split<0, kSplitG>
+                                                           : k_ball_write_split<1, kSplitG>);
+                kern<<<g2, 128, 0, s>>>(a, nl->segments, counts, nl->qi, nl->pj, nl->dist);
             } else {
                 FGB_KSCOPE("k_ball_write_rows", s);
                 const unsigned g2 = (unsigned)((nqq + 127) / 128);

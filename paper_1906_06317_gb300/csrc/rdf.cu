@@ -177,11 +177,14 @@ static void launch_rdf_lanes(const RdfArgs &a, size_t smem, cudaStream_t s) {
         k_rdf<SHARED, 1, false, LANES><<<grid, 256, smem, s>>>(a);
 }
 
-// Fewer than 128 queries per SM: 8 threads per query (FGB_SPLIT_KERNELS=0: one).
+// Fewer than 128 queries per SM: 8 threads per query, fewer than 32: a warp per query
+// (FGB_SPLIT_KERNELS=0: one thread).
 template <bool SHARED>
 static void launch_rdf(const RdfArgs &a, size_t smem, cudaStream_t s) {
     FGB_KSCOPE("k_rdf", s);
-    if (a.nq < (int64_t)num_sms() * 128 && split_kernels_enabled())
+    if (a.nq < (int64_t)num_sms() * 32 && split_kernels_enabled())
+        launch_rdf_lanes<SHARED, 32>(a, smem, s);
+    else if (a.nq < (int64_t)num_sms() * 128 && split_kernels_enabled())
         launch_rdf_lanes<SHARED, 8>(a, smem, s);
     else
         launch_rdf_lanes<SHARED, 1>(a, smem, s);
