@@ -135,7 +135,7 @@ MEASURED_TRAFFIC = {
 # Shared-atomic wavefronts of the fused RDF as a share of the shared-memory data pipe's
 # peak (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared_op_atom, the same capture).
 MEASURED_SHARED_ATOMICS = {
-    "k_rdf_tile": (_RDF, "ee9c5aa65dddbe7a", 0.1174),
+    "k_rdf_tile": (_RDF, "3eddbba7d02e9b5d", 0.1174),
 }
 
 

@@ -141,6 +141,14 @@ def test_ball_query_exact_edges(fgb):
         nl = nq.query(None, dict(r_max=r, exclude_ii=True)).toNeighborList()
         assert_ball_equal(nl, oracle.ball_query(b, g, r), r)
         assert nl.escalations > 0
+    # a half-spaced lattice on the cell tiles with r_max one ulp above 1: every pair at
+    # exactly 1 is a neighbor that only the FP64 decision finds
+    h = g * np.float32(0.5)
+    r = float(np.nextafter(1.0, 2.0))
+    nl = fgb.NeighborQuery(b, dev(h), r_cell=r).query(None, dict(r_max=r, exclude_ii=True)).toNeighborList()
+    ref = oracle.ball_query(b, h, r)
+    assert_ball_equal(nl, ref, r)
+    assert nl.escalations > 0 and np.diff(ref[1]).max() >= 18
 
 
 def test_ball_query_degenerate(fgb):
@@ -469,6 +477,8 @@ ball(c, xd, 1.5, 1.5); rdf(c, xd, 100, 3.0, 3.0)
 g = np.stack(np.meshgrid(*[np.arange(-8, 8)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float32) * 0.5
 rdf(W.Box.cube(16.0), g, 16, 4.0, 2.0)       # thousands of pairs on bin edges
 ball(W.Box.cube(16.0), g, 1.0, 1.0)          # and exactly on r_max
+r1 = float(np.nextafter(1.0, 2.0))
+ball(W.Box.cube(16.0), g, r1, r1)            # just inside r_max: found by the FP64 decision
 k = fgb.NeighborQuery(b, dev(x), r_cell=1.0).query(None, dict(num_neighbors=12, exclude_ii=True)).toNeighborList()
 _, kj, _ = oracle.knn(b, x, 12)
 assert np.array_equal(k.point_indices.cpu().numpy().reshape(-1, 12), kj[:, :12])
