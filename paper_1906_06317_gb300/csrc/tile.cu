@@ -712,16 +712,21 @@ __device__ __forceinline__ void store_sorted_packed_sb(const uint2 *row, uint32_
 // fit 23 or 22 bits; longer rows are sorted in shared memory by a bitonic network over
 // the row padded to a power of two (width entries per warp), then stored coalesced.
 // packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
-template <bool WIDE>
-__global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int cap, int width, int packable,
-                                int32_t *__restrict__ qi, int32_t *__restrict__ pj, float *__restrict__ dist) {
+// Only the rows with nmin < length <= cap are sorted by one launch (nmin >= 1), so that
+// rows of different length classes can take buffers of their own size.
+// NET32: the 1,024-entry register network is compiled in (about twice the registers of
+// the build without it, so the launches whose rows cannot use it leave it out).
+template <bool WIDE, bool NET32>
+__global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int nmin, int cap, int width,
+                                int packable, int32_t *__restrict__ qi, int32_t *__restrict__ pj,
+                                float *__restrict__ dist) {
     extern __shared__ uint2 srows[];  // (blockDim / 32) * (WIDE ? width : cap)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (q >= nq) return;
     const int64_t b = seg[q];
     const uint32_t n = (uint32_t)(seg[q + 1] - b);
-    if (n <= 1 || n > (uint32_t)cap) return;
+    if (n <= (uint32_t)nmin || n > (uint32_t)cap) return;
     uint2 *row = srows + (size_t)warp * (WIDE ? width : cap);
     for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
     const int iq = qi[b];
@@ -735,7 +740,7 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
         store_sorted_packed_sb<16, 9>(row, n, iq, b, qi, pj, dist);
         return;
     }
-    if (n <= 1024 && (packable & 4)) {
+    if (NET32 && n <= 1024 && (packable & 4)) {
         __syncwarp();
         store_sorted_packed_sb<32, 10>(row, n, iq, b, qi, pj, dist);
         return;
@@ -767,6 +772,26 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
     }
 }
 
+// One launch over the rows of length in (nmin, cap], each staged in a buffer of `width`
+// entries (WIDE) or `cap` entries.
+static int sort_segments_class(const int64_t *seg, int64_t nq, int nmin, int cap, int width, bool wide, int packable,
+                               int32_t *qi, int32_t *pj, float *dist, cudaStream_t s) {
+    const int stride = wide ? width : cap;
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * stride * sizeof(uint2) > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * stride * sizeof(uint2);
+    if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "more than %d neighbors of one point", 25600);
+    const unsigned grid = (unsigned)((nq + warps - 1) / warps);
+    // the 1,024-entry network only where rows of 513..1,024 entries can reach it
+    const bool net32 = wide && nmin < 1024 && cap > 512;
+    auto kern = !wide ? k_sort_segments<false, false> : net32 ? k_sort_segments<true, true> : k_sort_segments<true, false>;
+    FGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FGB_KSCOPE("k_sort_segments", s);
+    kern<<<grid, 32 * warps, smem, s>>>(seg, nq, nmin, cap, width, packable, qi, pj, dist);
+    FGB_LAUNCH_CHECK();
+    return FGB_OK;
+}
+
 int sort_segments(const int64_t *seg, int64_t nq, int cap, int64_t npoints, int32_t *qi, int32_t *pj, float *dist,
                   cudaStream_t s) {
     if (nq == 0 || cap <= 1) return FGB_OK;
@@ -775,22 +800,17 @@ int sort_segments(const int64_t *seg, int64_t nq, int cap, int64_t npoints, int3
     int width = 256;
     while (width < cap) width <<= 1;
     const bool wide = cap > 128 && (size_t)width * sizeof(uint2) <= 128 * 1024;
-    const int stride = wide ? width : cap;
-    int warps = 4;
-    while (warps > 1 && (size_t)warps * stride * sizeof(uint2) > 96 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * stride * sizeof(uint2);
-    if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "more than %d neighbors of one point", 25600);
-    const unsigned grid = (unsigned)((nq + warps - 1) / warps);
-    if (wide) {
-        FGB_CUDA(cudaFuncSetAttribute(k_sort_segments<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        FGB_KSCOPE("k_sort_segments", s);
-        k_sort_segments<true><<<grid, 32 * warps, smem, s>>>(seg, nq, cap, width, packable, qi, pj, dist);
-    } else {
-        FGB_CUDA(cudaFuncSetAttribute(k_sort_segments<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        FGB_KSCOPE("k_sort_segments", s);
-        k_sort_segments<false><<<grid, 32 * warps, smem, s>>>(seg, nq, cap, width, packable, qi, pj, dist);
+    if (!wide) return sort_segments_class(seg, nq, 1, cap, width, false, packable, qi, pj, dist, s);
+    // long rows by length class (up to 512, up to 1,024, longer), each class with a row
+    // buffer of its own size, so the common shorter rows keep more warps resident
+    int lo = 1;
+    for (const int hi : {512, 1024}) {
+        if (lo >= cap) break;
+        FGB_TRY(sort_segments_class(seg, nq, lo, std::min(cap, hi), std::min(width, hi), true, packable, qi, pj, dist,
+                                    s));
+        lo = hi;
     }
-    FGB_LAUNCH_CHECK();
+    if (cap > lo) FGB_TRY(sort_segments_class(seg, nq, lo, cap, width, true, packable, qi, pj, dist, s));
     return FGB_OK;
 }
 
