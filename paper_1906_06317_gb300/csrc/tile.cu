@@ -705,18 +705,69 @@ __device__ __forceinline__ void store_sorted_packed_sb(const uint2 *row, uint32_
     }
 }
 
+// A row of 513..1,024 entries with point indices below 2^22 (one warp): keys
+// (index << 10 | slot) in kb[0, 1024) (padded with ~0) and distances in db by slot.
+// Each half of 512 keys is sorted by the register network, the two sorted halves are
+// merged (lane l produces outputs 32 l .. 32 l + 31 from the merge-path split of its
+// diagonal), and the merged row is stored coalesced.  Keys are distinct (indices are
+// distinct within a row), so the merge needs no tie rule.
+__device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, uint32_t n, int iq, int64_t b,
+                                                 int32_t *__restrict__ qi, int32_t *__restrict__ pj,
+                                                 float *__restrict__ dist) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = kb[512 * h + 16 * lane + r];
+        bitonic_keys<16>(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) kb[512 * h + 16 * lane + r] = v[r];
+    }
+    __syncwarp();
+    const uint32_t *A = kb, *B = kb + 512;
+    const int d = 32 * lane;
+    int lo = max(0, d - 512), hi = min(d, 512);  // A elements among the first d outputs
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] < B[d - mid - 1])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int ia = lo, ib = d - lo;
+    uint32_t out[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const uint32_t x = ia < 512 ? A[ia] : 0xffffffffu, y = ib < 512 ? B[ib] : 0xffffffffu;
+        const bool ta = x < y;
+        out[r] = ta ? x : y;
+        ia += ta ? 1 : 0;
+        ib += ta ? 0 : 1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) kb[d + r] = out[r];
+    __syncwarp();
+    for (uint32_t k = lane; k < n; k += 32) {
+        const uint32_t key = kb[k];
+        __stcs(qi + b + k, iq);
+        __stcs(pj + b + k, (int32_t)(key >> 10));
+        __stcs(dist + b + k, db[key & 1023u]);
+    }
+}
+
 // Sorts each segment [seg[q], seg[q+1]) of (qi, pj, dist) by point index in place: one
 // warp per segment, staged as (index, distance) in shared memory, then the same network
 // (or ranking) and stores as the write kernels.  WIDE (rows longer than 128): rows of up
-// to 512 or 1,024 entries take a register network on packed keys when the point indices
-// fit 23 or 22 bits; longer rows are sorted in shared memory by a bitonic network over
-// the row padded to a power of two (width entries per warp), then stored coalesced.
-// packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
+// to 512 entries take a register network on packed keys when the point indices fit 23
+// bits; MERGE: rows of 513..1,024 entries (indices below 2^22) take sort_merge_store in
+// the same 8 KB (width 1,024); other rows are sorted in shared memory by a bitonic
+// network over the row padded to a power of two (width entries per warp), then stored
+// coalesced.  packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
 // Only the rows with nmin < length <= cap are sorted by one launch (nmin >= 1), so that
 // rows of different length classes can take buffers of their own size.
-// NET32: the 1,024-entry register network is compiled in (about twice the registers of
-// the build without it, so the launches whose rows cannot use it leave it out).
-template <bool WIDE, bool NET32>
+template <bool WIDE, bool MERGE>
 __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int nmin, int cap, int width,
                                 int packable, int32_t *__restrict__ qi, int32_t *__restrict__ pj,
                                 float *__restrict__ dist) {
@@ -728,6 +779,18 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
     const uint32_t n = (uint32_t)(seg[q + 1] - b);
     if (n <= (uint32_t)nmin || n > (uint32_t)cap) return;
     uint2 *row = srows + (size_t)warp * (WIDE ? width : cap);
+    if (MERGE && n > 512 && n <= 1024 && width >= 1024 && (packable & 4)) {
+        uint32_t *kb = reinterpret_cast<uint32_t *>(row);
+        float *db = reinterpret_cast<float *>(kb + 1024);
+        for (uint32_t k = lane; k < 1024; k += 32) {
+            kb[k] = k < n ? ((uint32_t)pj[b + k] << 10) | k : 0xffffffffu;
+            if (k < n) db[k] = dist[b + k];
+        }
+        const int iq = qi[b];
+        __syncwarp();
+        sort_merge_store(kb, db, n, iq, b, qi, pj, dist);
+        return;
+    }
     for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
     const int iq = qi[b];
     if (!WIDE || n <= 128) {
@@ -738,11 +801,6 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
     if (n <= 512 && (packable & 2)) {
         __syncwarp();
         store_sorted_packed_sb<16, 9>(row, n, iq, b, qi, pj, dist);
-        return;
-    }
-    if (NET32 && n <= 1024 && (packable & 4)) {
-        __syncwarp();
-        store_sorted_packed_sb<32, 10>(row, n, iq, b, qi, pj, dist);
         return;
     }
 
@@ -782,9 +840,9 @@ static int sort_segments_class(const int64_t *seg, int64_t nq, int nmin, int cap
     const size_t smem = (size_t)warps * stride * sizeof(uint2);
     if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "more than %d neighbors of one point", 25600);
     const unsigned grid = (unsigned)((nq + warps - 1) / warps);
-    // the 1,024-entry network only where rows of 513..1,024 entries can reach it
-    const bool net32 = wide && nmin < 1024 && cap > 512;
-    auto kern = !wide ? k_sort_segments<false, false> : net32 ? k_sort_segments<true, true> : k_sort_segments<true, false>;
+    // the merge of two sorted halves where rows of 513..1,024 entries can reach it
+    const bool merge = wide && nmin < 1024 && cap > 512 && width >= 1024;
+    auto kern = !wide ? k_sort_segments<false, false> : merge ? k_sort_segments<true, true> : k_sort_segments<true, false>;
     FGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FGB_KSCOPE("k_sort_segments", s);
     kern<<<grid, 32 * warps, smem, s>>>(seg, nq, nmin, cap, width, packable, qi, pj, dist);
