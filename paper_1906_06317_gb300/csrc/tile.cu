@@ -707,27 +707,37 @@ __device__ __forceinline__ void store_sorted_packed_sb(const uint2 *row, uint32_
 
 // A row of 513..1,024 entries with point indices below 2^22 (one warp): keys
 // (index << 10 | slot) in kb[0, 1024) (padded with ~0) and distances in db by slot.
-// Each half of 512 keys is sorted by the register network, the two sorted halves are
-// merged (lane l produces outputs 32 l .. 32 l + 31 from the merge-path split of its
-// diagonal), and the merged row is stored coalesced.  Keys are distinct (indices are
-// distinct within a row), so the merge needs no tie rule.
+// The first 512 keys and the next 32 * KPLB (256 for rows up to 768) are each sorted by
+// the register network, the two sorted runs are merged (lane l produces outputs from
+// the merge-path split of its diagonal), and the merged row is stored coalesced.  Keys
+// are distinct (indices are distinct within a row), so the merge needs no tie rule.
+template <int KPLB>
 __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, uint32_t n, int iq, int64_t b,
                                                  int32_t *__restrict__ qi, int32_t *__restrict__ pj,
                                                  float *__restrict__ dist) {
+    constexpr int LB = 32 * KPLB;        // length of the second run
+    constexpr int PER = (512 + LB) / 32;  // outputs per lane
     const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
+    {
         uint32_t v[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = kb[512 * h + 16 * lane + r];
+        for (int r = 0; r < 16; ++r) v[r] = kb[16 * lane + r];
         bitonic_keys<16>(v);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) kb[512 * h + 16 * lane + r] = v[r];
+        for (int r = 0; r < 16; ++r) kb[16 * lane + r] = v[r];
+    }
+    {
+        uint32_t v[KPLB];
+#pragma unroll
+        for (int r = 0; r < KPLB; ++r) v[r] = kb[512 + KPLB * lane + r];
+        bitonic_keys<KPLB>(v);
+#pragma unroll
+        for (int r = 0; r < KPLB; ++r) kb[512 + KPLB * lane + r] = v[r];
     }
     __syncwarp();
     const uint32_t *A = kb, *B = kb + 512;
-    const int d = 32 * lane;
-    int lo = max(0, d - 512), hi = min(d, 512);  // A elements among the first d outputs
+    const int d = PER * lane;
+    int lo = max(0, d - LB), hi = min(d, 512);  // A elements among the first d outputs
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (A[mid] < B[d - mid - 1])
@@ -736,10 +746,10 @@ __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, 
             hi = mid;
     }
     int ia = lo, ib = d - lo;
-    uint32_t out[32];
+    uint32_t out[PER];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const uint32_t x = ia < 512 ? A[ia] : 0xffffffffu, y = ib < 512 ? B[ib] : 0xffffffffu;
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t x = ia < 512 ? A[ia] : 0xffffffffu, y = ib < LB ? B[ib] : 0xffffffffu;
         const bool ta = x < y;
         out[r] = ta ? x : y;
         ia += ta ? 1 : 0;
@@ -747,7 +757,7 @@ __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, 
     }
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < 32; ++r) kb[d + r] = out[r];
+    for (int r = 0; r < PER; ++r) kb[d + r] = out[r];
     __syncwarp();
     for (uint32_t k = lane; k < n; k += 32) {
         const uint32_t key = kb[k];
@@ -760,8 +770,8 @@ __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, 
 // Sorts each segment [seg[q], seg[q+1]) of (qi, pj, dist) by point index in place: one
 // warp per segment, staged as (index, distance) in shared memory, then the same network
 // (or ranking) and stores as the write kernels.  WIDE (rows longer than 128): rows of up
-// to 512 entries take a register network on packed keys when the point indices fit 23
-// bits; MERGE: rows of 513..1,024 entries (indices below 2^22) take sort_merge_store in
+// to 256 or 512 entries take a register network on packed keys when the point indices
+// fit 23 bits; MERGE: rows of 513..1,024 entries (indices below 2^22) take sort_merge_store in
 // the same 8 KB (width 1,024); other rows are sorted in shared memory by a bitonic
 // network over the row padded to a power of two (width entries per warp), then stored
 // coalesced.  packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
@@ -788,7 +798,10 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
         }
         const int iq = qi[b];
         __syncwarp();
-        sort_merge_store(kb, db, n, iq, b, qi, pj, dist);
+        if (n <= 768)
+            sort_merge_store<8>(kb, db, n, iq, b, qi, pj, dist);
+        else
+            sort_merge_store<16>(kb, db, n, iq, b, qi, pj, dist);
         return;
     }
     for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
@@ -796,6 +809,11 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
     if (!WIDE || n <= 128) {
         __syncwarp();
         sort_store_row(row, n, iq, b, (packable & 1) != 0, qi, pj, dist);
+        return;
+    }
+    if (n <= 256 && (packable & 2)) {
+        __syncwarp();
+        store_sorted_packed_sb<8, 8>(row, n, iq, b, qi, pj, dist);
         return;
     }
     if (n <= 512 && (packable & 2)) {
