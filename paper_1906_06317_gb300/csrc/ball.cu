@@ -19,8 +19,9 @@ bool force_thread_kernels() {
     return v == 1;
 }
 
-// FGB_SPLIT_KERNELS=0 keeps few-query grids on the one-thread-per-query kernels instead
-// of the 8-lanes-per-query ones (so that both stay covered by tests).
+// FGB_SPLIT_KERNELS=0 keeps few-query grids on the one-thread-per-query kernels (ball
+// count and write, per-point RDF) instead of the ones that give a query 8 lanes or a
+// warp (so that both stay covered by tests).
 bool split_kernels_enabled() {
     static int v = -1;
     if (v < 0) {
