@@ -705,39 +705,39 @@ __device__ __forceinline__ void store_sorted_packed_sb(const uint2 *row, uint32_
     }
 }
 
-// A row of 513..1,024 entries with point indices below 2^22 (one warp): keys
-// (index << 10 | slot) in kb[0, 1024) (padded with ~0) and distances in db by slot.
-// The first 512 keys and the next 32 * KPLB (256 for rows up to 768) are each sorted by
-// the register network, the two sorted runs are merged (lane l produces outputs from
-// the merge-path split of its diagonal), and the merged row is stored coalesced.  Keys
-// are distinct (indices are distinct within a row), so the merge needs no tie rule.
-template <int KPLB>
+// A row of at most 32 (KPLA + KPLB) entries with point indices below 2^22 (one warp):
+// keys (index << 10 | slot) in kb (padded with ~0 to that length) and distances in db
+// by slot.  The first 32 KPLA keys and the next 32 KPLB are each sorted by the register
+// network, the two sorted runs are merged (lane l produces its outputs from the
+// merge-path split of its diagonal), and the merged row is stored coalesced.  Keys are
+// distinct (indices are distinct within a row), so the merge needs no tie rule.
+template <int KPLA, int KPLB>
 __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, uint32_t n, int iq, int64_t b,
                                                  int32_t *__restrict__ qi, int32_t *__restrict__ pj,
                                                  float *__restrict__ dist) {
-    constexpr int LB = 32 * KPLB;        // length of the second run
-    constexpr int PER = (512 + LB) / 32;  // outputs per lane
+    constexpr int LA = 32 * KPLA, LB = 32 * KPLB;  // lengths of the two runs
+    constexpr int PER = KPLA + KPLB;               // outputs per lane
     const int lane = threadIdx.x & 31;
     {
-        uint32_t v[16];
+        uint32_t v[KPLA];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = kb[16 * lane + r];
-        bitonic_keys<16>(v);
+        for (int r = 0; r < KPLA; ++r) v[r] = kb[KPLA * lane + r];
+        bitonic_keys<KPLA>(v);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) kb[16 * lane + r] = v[r];
+        for (int r = 0; r < KPLA; ++r) kb[KPLA * lane + r] = v[r];
     }
     {
         uint32_t v[KPLB];
 #pragma unroll
-        for (int r = 0; r < KPLB; ++r) v[r] = kb[512 + KPLB * lane + r];
+        for (int r = 0; r < KPLB; ++r) v[r] = kb[LA + KPLB * lane + r];
         bitonic_keys<KPLB>(v);
 #pragma unroll
-        for (int r = 0; r < KPLB; ++r) kb[512 + KPLB * lane + r] = v[r];
+        for (int r = 0; r < KPLB; ++r) kb[LA + KPLB * lane + r] = v[r];
     }
     __syncwarp();
-    const uint32_t *A = kb, *B = kb + 512;
+    const uint32_t *A = kb, *B = kb + LA;
     const int d = PER * lane;
-    int lo = max(0, d - LB), hi = min(d, 512);  // A elements among the first d outputs
+    int lo = max(0, d - LB), hi = min(d, LA);  // A elements among the first d outputs
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (A[mid] < B[d - mid - 1])
@@ -749,7 +749,7 @@ __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, 
     uint32_t out[PER];
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const uint32_t x = ia < 512 ? A[ia] : 0xffffffffu, y = ib < LB ? B[ib] : 0xffffffffu;
+        const uint32_t x = ia < LA ? A[ia] : 0xffffffffu, y = ib < LB ? B[ib] : 0xffffffffu;
         const bool ta = x < y;
         out[r] = ta ? x : y;
         ia += ta ? 1 : 0;
@@ -767,17 +767,42 @@ __device__ __forceinline__ void sort_merge_store(uint32_t *kb, const float *db, 
     }
 }
 
+// Rows of 257..MAXN entries (MAXN 512 or 1,024) by two sorted runs and a merge, in the
+// warp's buffer of `width` entries (keys in its first half, distances in the second).
+template <int MAXN>
+__device__ __forceinline__ void sort_merge_row(uint2 *row, int width, uint32_t n, int64_t b, int32_t *__restrict__ qi,
+                                               int32_t *__restrict__ pj, float *__restrict__ dist) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *kb = reinterpret_cast<uint32_t *>(row);
+    float *db = reinterpret_cast<float *>(kb + width);
+    const uint32_t len = n <= 384 ? 384 : n <= 512 ? 512 : n <= 768 ? 768 : 1024;  // padded
+    for (uint32_t k = lane; k < len; k += 32) {
+        kb[k] = k < n ? ((uint32_t)pj[b + k] << 10) | k : 0xffffffffu;
+        if (k < n) db[k] = dist[b + k];
+    }
+    const int iq = qi[b];
+    __syncwarp();
+    if (MAXN > 512 && n > 768)
+        sort_merge_store<16, 16>(kb, db, n, iq, b, qi, pj, dist);
+    else if (MAXN > 512 && n > 512)
+        sort_merge_store<16, 8>(kb, db, n, iq, b, qi, pj, dist);
+    else if (n > 384)
+        sort_merge_store<8, 8>(kb, db, n, iq, b, qi, pj, dist);
+    else
+        sort_merge_store<8, 4>(kb, db, n, iq, b, qi, pj, dist);
+}
+
 // Sorts each segment [seg[q], seg[q+1]) of (qi, pj, dist) by point index in place: one
 // warp per segment, staged as (index, distance) in shared memory, then the same network
 // (or ranking) and stores as the write kernels.  WIDE (rows longer than 128): rows of up
 // to 256 or 512 entries take a register network on packed keys when the point indices
-// fit 23 bits; MERGE: rows of 513..1,024 entries (indices below 2^22) take sort_merge_store in
-// the same 8 KB (width 1,024); other rows are sorted in shared memory by a bitonic
+// fit 23 bits; MERGE: rows of 257..MERGE entries (indices below 2^22) take two sorted
+// runs and a merge (sort_merge_row) in the same buffer; other rows are sorted in shared memory by a bitonic
 // network over the row padded to a power of two (width entries per warp), then stored
 // coalesced.  packable: bit 0 indices below 2^25, bit 1 below 2^23, bit 2 below 2^22.
 // Only the rows with nmin < length <= cap are sorted by one launch (nmin >= 1), so that
 // rows of different length classes can take buffers of their own size.
-template <bool WIDE, bool MERGE>
+template <bool WIDE, int MERGE>
 __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int nmin, int cap, int width,
                                 int packable, int32_t *__restrict__ qi, int32_t *__restrict__ pj,
                                 float *__restrict__ dist) {
@@ -789,19 +814,8 @@ __global__ void k_sort_segments(const int64_t *__restrict__ seg, int64_t nq, int
     const uint32_t n = (uint32_t)(seg[q + 1] - b);
     if (n <= (uint32_t)nmin || n > (uint32_t)cap) return;
     uint2 *row = srows + (size_t)warp * (WIDE ? width : cap);
-    if (MERGE && n > 512 && n <= 1024 && width >= 1024 && (packable & 4)) {
-        uint32_t *kb = reinterpret_cast<uint32_t *>(row);
-        float *db = reinterpret_cast<float *>(kb + 1024);
-        for (uint32_t k = lane; k < 1024; k += 32) {
-            kb[k] = k < n ? ((uint32_t)pj[b + k] << 10) | k : 0xffffffffu;
-            if (k < n) db[k] = dist[b + k];
-        }
-        const int iq = qi[b];
-        __syncwarp();
-        if (n <= 768)
-            sort_merge_store<8>(kb, db, n, iq, b, qi, pj, dist);
-        else
-            sort_merge_store<16>(kb, db, n, iq, b, qi, pj, dist);
+    if (MERGE > 0 && WIDE && n > 256 && n <= (uint32_t)min(MERGE, width) && (packable & 4)) {
+        sort_merge_row<MERGE>(row, width, n, b, qi, pj, dist);
         return;
     }
     for (uint32_t k = lane; k < n; k += 32) row[k] = make_uint2((uint32_t)pj[b + k], __float_as_uint(dist[b + k]));
@@ -858,9 +872,12 @@ static int sort_segments_class(const int64_t *seg, int64_t nq, int nmin, int cap
     const size_t smem = (size_t)warps * stride * sizeof(uint2);
     if (smem > 200 * 1024) return fail(FGB_ERR_UNSUPPORTED, "more than %d neighbors of one point", 25600);
     const unsigned grid = (unsigned)((nq + warps - 1) / warps);
-    // the merge of two sorted halves where rows of 513..1,024 entries can reach it
-    const bool merge = wide && nmin < 1024 && cap > 512 && width >= 1024;
-    auto kern = !wide ? k_sort_segments<false, false> : merge ? k_sort_segments<true, true> : k_sort_segments<true, false>;
+    // the merge of two sorted runs for the rows of 257..1,024 entries that the launch
+    // holds (MERGE: the longest such row; the 1,024 build takes more registers)
+    auto kern = !wide                                  ? k_sort_segments<false, 0>
+                : (cap > 512 && nmin < 1024 && width >= 1024) ? k_sort_segments<true, 1024>
+                : (cap > 256 && nmin < 512 && width >= 512)   ? k_sort_segments<true, 512>
+                                                               : k_sort_segments<true, 0>;
     FGB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FGB_KSCOPE("k_sort_segments", s);
     kern<<<grid, 32 * warps, smem, s>>>(seg, nq, nmin, cap, width, packable, qi, pj, dist);
